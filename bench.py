@@ -1,0 +1,421 @@
+#!/usr/bin/env python3
+"""Benchmark of the bundle-adjustment hot path (one JSON line on stdout).
+
+Workload (default): the driving-sequence BA problem - 1,000 forward-facing
+cameras along a 2 km road, 200k points, ~1.21M observations, Huber 1 px,
+block-Jacobi PCG (tol 1e-6, max 100), 20 LM iterations - solved by the FP32
+path (FP32 residuals / Jacobians / Schur blocks / PCG, FP64 cost sum, gain
+ratio, damping and 3x3 point inverses).  A step is one whole solve (20 LM
+iterations) from the same initial state; inputs are resident in HBM; L2 is
+flushed (256 MB write) between steps inside the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+value = observations x LM iterations / second over the timed steps (all
+ranks).  Also reported: the plain FP64 path on the same problem, the end-to-
+end rate through the C ABI with host buffers, per-kernel device times and the
+roofline of the dominant kernel, SM clocks during the timed region, and the
+FP64 CPU oracle on the host cores as a reported baseline.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "BA obs·iters/s & local-BA p50/p99 ms, FP32-batched vs plain FP64 path"
+UNIT = "obs*iters/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------- workload
+
+def make_workload(name, seed):
+    from paper_2510_15271_b300 import scenes
+    return scenes.make_scene(name, seed=seed)
+
+
+def camera_pairs(s):
+    """Number of 6x6 blocks of S: camera pairs (incl. i = k) sharing a point,
+    and the sum of squared track lengths."""
+    order = np.argsort(s.obs_pt, kind="stable")
+    pt = s.obs_pt[order]
+    cam = s.obs_cam[order].astype(np.int64)
+    L = np.bincount(pt, minlength=s.n_pts)
+    start = np.concatenate([[0], np.cumsum(L)[:-1]])
+    keys = []
+    for l in np.unique(L):
+        sel = np.nonzero(L == l)[0]
+        idx = start[sel][:, None] + np.arange(l)[None, :]
+        c = cam[idx]
+        keys.append((c[:, :, None] * s.n_cams + c[:, None, :]).ravel())
+    keys = np.unique(np.concatenate(keys))
+    return int(keys.size), int(np.sum(L.astype(np.int64) ** 2))
+
+
+def algorithmic_bytes(s, nnzb, kernel, fp32=True, pcg_iters=100):
+    """Compulsory DRAM bytes of one launch of a kernel (each array touched
+    once), from the data layout; see the design notes for the derivation."""
+    N, P, C = s.n_obs, s.n_pts, s.n_cams
+    t = 4 if fp32 else 8
+    w = 18 * t
+    cam_state = C * (9 + 3 + 3) * 8
+    if kernel == "lin_cam":
+        return N * (2 * t + 4 + w) + P * 24 + cam_state + C * 27 * t
+    if kernel == "lin_pt":
+        return N * (2 * t + 4) + P * (24 + 9 * t) + cam_state
+    if kernel == "damp_pt":
+        return P * (9 * t + 48 + 3 * t)
+    if kernel == "schur":
+        return N * (w + 4 + 8) + P * (48 + 3 * t + 8) + nnzb * (36 * t + 4) + C * (42 * t)
+    if kernel == "backsub":
+        return N * (w + 8) + P * (3 * t + 48 + 6 * t + 24 + 24 + 3 * t) + C * 6 * t
+    if kernel in ("cost_trial", "cost_initial", "cost_final"):
+        return N * (2 * t + 8) + P * 24 + cam_state
+    if kernel == "pcg":
+        return pcg_iters * (nnzb * (36 * t + 4) + C * 6 * t * 8)
+    return 0
+
+
+# --------------------------------------------------------------------------- our arm
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2510_15271_b300 import ba
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    s = make_workload(args.workload, args.seed + rank)
+    iters = s.lm_iters
+    work = s.n_obs * iters  # obs*iters per step
+
+    def make_handle(precision, profile):
+        o = ba.options_for_scene(s, precision, device=local_rank, profile=1 if profile else 0)
+        h = ba.ba_create(o, use_torch=True)
+        ba.ba_set_problem(h, torch.tensor(s.cam_qt, device=dev), torch.tensor(s.pts, device=dev),
+                          torch.tensor(s.obs_cam, device=dev), torch.tensor(s.obs_pt, device=dev),
+                          torch.tensor(s.obs_uv, device=dev), s.intrinsics(),
+                          torch.tensor(s.cam_fixed, device=dev))
+        return h
+
+    q0 = torch.tensor(s.cam_qt, device=dev)
+    p0 = torch.tensor(s.pts, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    L = ba.lib()
+
+    def reset(h):
+        st = L.ba_set_state(h.ptr, q0.data_ptr(), p0.data_ptr(), ba.BA_MEM_DEVICE)
+        if st != ba.BA_OK:
+            raise ba.BAError(st, ba.ba_last_error(h.ptr))
+
+    def timed(h, steps, warmup):
+        reps = []
+        for _ in range(warmup):
+            reset(h)
+            flush.fill_(1.0)
+            reps.append(ba.ba_solve(h))
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            reset(h)
+            flush.fill_(1.0)
+            reps.append(ba.ba_solve(h))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+            torch.distributed.barrier()
+        return ms, reps
+
+    # ---- FP32 path (the headline).  The timed handle records a CUDA event
+    # after every kernel inside its graph, so the per-kernel device times come
+    # from the timed steps themselves.
+    h32 = make_handle("fp32", profile=True)
+    clock = ClockSampler(local_rank)
+    clock.start()
+    ms32, reps32 = timed(h32, args.steps, args.warmup)
+    clocks = clock.stop()
+    kstats = ba.ba_kernel_stats(h32)
+    last = reps32[-1]
+    launches_per_step = last["n_kernels"] + (2 if s.precision == "fp32" else 1)  # + state reset
+    h32.close()
+    # the same solve without the event nodes, to show what they cost
+    hp = make_handle("fp32", profile=False)
+    ms_plain, _ = timed(hp, max(1, args.steps // 2), 1)
+    hp.close()
+    ms_plain_per_step = ms_plain / max(1, args.steps // 2)
+
+    # ---- plain FP64 path on the same problem
+    fp64 = None
+    if not args.no_fp64:
+        h64 = make_handle("fp64", profile=False)
+        ms64, reps64 = timed(h64, args.fp64_steps, 1)
+        h64.close()
+        fp64 = {"value": work * args.fp64_steps * world / (ms64 / 1e3), "unit": UNIT,
+                "ms_per_step": ms64 / args.fp64_steps,
+                "final_cost": float(reps64[-1]["costs"][-1]),
+                "rmse_px": float(reps64[-1]["rmse_px"])}
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        qh = np.ascontiguousarray(s.cam_qt)
+        ph = np.ascontiguousarray(s.pts)
+        ch = np.ascontiguousarray(s.obs_cam)
+        jh = np.ascontiguousarray(s.obs_pt)
+        uvh = np.ascontiguousarray(s.obs_uv)
+        fh = np.ascontiguousarray(s.cam_fixed)
+        qo = np.empty_like(qh)
+        po = np.empty_like(ph)
+        o = ba.options_for_scene(s, "fp32", device=local_rank)
+        with ba.ba_create(o, use_torch=True) as h:
+            def one():
+                ba.ba_set_problem(h, qh, ph, ch, jh, uvh, s.intrinsics(), fh)
+                rep = ba.ba_solve(h)
+                L.ba_get_state(h.ptr, qo.ctypes.data, po.ctypes.data, ba.BA_MEM_HOST)
+                return rep
+            one()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            n_e2e = max(1, args.e2e_steps)
+            for _ in range(n_e2e):
+                one()
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+        h2d = qh.nbytes + ph.nbytes + ch.nbytes + jh.nbytes + uvh.nbytes + fh.nbytes
+        d2h = qo.nbytes + po.nbytes + ba.ctypes.sizeof(ba.Report)
+        e2e = {"value": work * n_e2e * world / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": dt / n_e2e * 1e3}
+
+    return dict(s=s, work=work, ms32=ms32, reps=reps32, kstats=kstats, clocks=clocks,
+                launches_per_step=launches_per_step, fp64=fp64, e2e=e2e,
+                ms_plain_per_step=ms_plain_per_step)
+
+
+def cpu_baseline(s, iters, kind="oracle"):
+    """The FP64 oracle, as it stands, for `iters` LM iterations on scene s."""
+    import oracle as O
+    prob = O.Problem.from_arrays(s.intrinsics(), s.obs_cam, s.obs_pt, s.obs_uv, s.cam_fixed,
+                                 s.n_cams, s.n_pts)
+    st = O.state_from_qt(s.cam_qt, s.pts)
+    t0 = time.perf_counter()
+    O.lm_solve(prob, st, O.LMOptions(huber_delta=s.huber_delta, lm_iters=iters, solver=s.solver,
+                                     pcg_tol=s.pcg_tol, pcg_max_iters=s.pcg_max_iters))
+    dt = time.perf_counter() - t0
+    return s.n_obs * iters / dt, dt
+
+
+def roofline(res, peak_gbs, peak_kind):
+    s = res["s"]
+    nnzb, sumL2 = camera_pairs(s)
+    ks = res["kstats"]
+    name, (launches, total_ms) = max(ks.items(), key=lambda kv: kv[1][1])
+    per_launch_ms = total_ms / launches
+    mean_pcg = float(np.mean(res["reps"][-1]["pcg_iters"])) if name == "pcg" else 0
+    nbytes = algorithmic_bytes(s, nnzb, name, True, pcg_iters=mean_pcg)
+    achieved = nbytes / (per_launch_ms / 1e3) / 1e9
+    return {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak_gbs,
+            "unit": "GB/s", "frac": round(achieved / peak_gbs, 4), "traffic": None,
+            "peak_source": peak_kind, "bytes_per_launch": int(nbytes),
+            "launch_ms": round(per_launch_ms, 4), "nnzb": nnzb, "sum_track_len_sq": sumL2}
+
+
+# --------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    """The FP64 CPU oracle, as it stands, on the host cores: each step is one
+    LM iteration on a 300-camera sample of the driving recipe."""
+    from paper_2510_15271_b300 import scenes
+    full = scenes.make_scene(args.workload, seed=args.seed)
+    s = scenes.make_scene(args.workload, seed=args.seed, **_reference_sample(args.workload))
+    for _ in range(args.warmup):
+        cpu_baseline(s, 1)
+    t = 0.0
+    for _ in range(args.steps):
+        _, dt = cpu_baseline(s, 1)
+        t += dt
+    value = s.n_obs * args.steps / t
+    cores = len(os.sched_getaffinity(0))
+    sample = (f"{args.workload} recipe at {s.n_cams} cameras / {s.n_pts} points / {s.n_obs} obs, "
+              "one LM iteration per step")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config(args, full),
+            "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": cores,
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def _reference_sample(name):
+    if name == "driving":
+        return dict(n_cams=300, n_pts=60000, length_m=600.0)
+    if name == "city":
+        return dict(n_cams=1000, n_pts=200000)
+    return {}
+
+
+def _config(args, s):
+    return {"workload": f"{args.workload} BA: {s.n_cams} cameras, {s.n_pts} points, "
+                        f"{s.n_obs} observations, {s.lm_iters} LM iterations, Huber "
+                        f"{s.huber_delta} px, {s.solver} solver (tol {s.pcg_tol}, max "
+                        f"{s.pcg_max_iters}), FP32 with FP64 cost / gain / damping / 3x3 inverses",
+            "n_cams": s.n_cams, "n_pts": s.n_pts, "n_obs": s.n_obs, "lm_iters": s.lm_iters,
+            "seed": args.seed, "l2": "flushed between steps (256 MB write inside the timed region)",
+            "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
+
+
+# --------------------------------------------------------------------------- main
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="driving", choices=["driving", "city", "ring"])
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-iters", type=int, default=2)
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+
+    from paper_2510_15271_b300 import build
+    if rank == 0:
+        build.build()
+    if world > 1:
+        import torch
+        torch.distributed.barrier()
+
+    res = run_ours(args, rank, world, local_rank)
+    if rank != 0:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+        return
+    peak, peak_kind = _peaks()
+    s = res["s"]
+    value = res["work"] * args.steps * world / (res["ms32"] / 1e3)
+    line = {
+        "impl": "ours", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms32"] / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": _config(args, s),
+        "roofline": roofline(res, peak, peak_kind),
+        "e2e": res["e2e"], "gpu_launches": res["launches_per_step"] * args.steps,
+        "clocks": res["clocks"], "fp64_path": res["fp64"],
+        "kernels_ms_per_step": {k: round(v[1] / 1.0, 4) for k, v in res["kstats"].items()},
+        "ms_per_step_without_event_nodes": res["ms_plain_per_step"],
+        "solve": {"final_cost": float(res["reps"][-1]["costs"][-1]),
+                  "rmse_px": float(res["reps"][-1]["rmse_px"]),
+                  "pcg_iters": [int(v) for v in res["reps"][-1]["pcg_iters"]],
+                  "accepted": int(res["reps"][-1]["n_accepted"])},
+    }
+    if not args.no_cpu:
+        v, dt = cpu_baseline(s, args.cpu_iters)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": len(os.sched_getaffinity(0)),
+                                "kind": "oracle",
+                                "sample": f"{args.cpu_iters} LM iterations of the full workload "
+                                          f"({dt:.1f} s)"}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,261 @@
+/*
+ * ba.h - C ABI of the B300 bundle-adjustment library (libba.so).
+ *
+ * The library runs the Levenberg-Marquardt bundle-adjustment iteration of
+ * cuSfM (arXiv 2510.15271, Sec. 4.3 "Iterative Triangulation and Mapping")
+ * on one NVIDIA B300 GPU:
+ *   minimise  F = 1/2 sum_k rho(|| pi(K T_cam(k) X_pt(k)) - p_obs,k ||^2)
+ * over camera poses T (6-DoF, world -> camera) and points X, with the
+ * reprojection error of Sec. 4.3 (reprojection equation), the robust loss
+ * rho of the stage-one objective (Sec. 4.3, objective L; Huber here) and
+ * the fixed-pose subsets of Sec. 4.3 (absolute pose constraints) applied as
+ * a hard mask.  Each iteration: residuals + analytic Jacobians + IRLS Huber
+ * weights, block accumulation, Schur complement of the point blocks, a
+ * direct (dense Cholesky) or block-Jacobi PCG solve of the reduced camera
+ * system, point back-substitution, trial step, gain ratio and damping
+ * update, all on the device with no host synchronisation per iteration.
+ *
+ * Conventions (all calls):
+ *   - Pose: 7 doubles (qw, qx, qy, qz, tx, ty, tz), a unit quaternion and a
+ *     translation of the world -> camera map x_c = R X + t.  Camera axes: x
+ *     right, y down, z forward.  Pixel: (fx x/z + cx, fy y/z + cy).
+ *   - Every array is dense, row-major, native-endian, with no padding.
+ *   - Inputs are copied in; the caller keeps ownership of every buffer it
+ *     passes and may reuse it as soon as the call returns.  Outputs are
+ *     written into caller buffers.
+ *   - Every call returns a ba_status; on failure ba_last_error() describes
+ *     the cause.  A handle is used by one host thread at a time.
+ *   - mem_kind BA_MEM_HOST: pointers are host memory (pinned or pageable).
+ *     BA_MEM_DEVICE: pointers are device memory of the handle's device,
+ *     read (or written) in stream order on the handle's stream.
+ */
+#ifndef BA_H
+#define BA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ba_handle ba_handle;
+
+typedef enum {
+  BA_OK = 0,
+  BA_ERR_INVALID_ARG = 1, /* bad pointer, size, index, non-finite value   */
+  BA_ERR_OOM = 2,         /* device allocation failed                     */
+  BA_ERR_CUDA = 3,        /* a CUDA runtime call failed                   */
+  BA_ERR_NOT_READY = 4,   /* ba_poll: request still running               */
+  BA_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up           */
+  BA_ERR_BUSY = 6,        /* ba_submit: request table full                */
+  BA_ERR_STATE = 7,       /* call out of order (e.g. solve before set)    */
+  BA_ERR_NUMERIC = 8      /* non-finite cost or state after the solve     */
+} ba_status;
+
+enum { BA_FP64 = 0, BA_FP32 = 1 };                          /* precision  */
+enum { BA_SOLVER_AUTO = 0, BA_SOLVER_DENSE = 1, BA_SOLVER_PCG = 2 };
+enum { BA_MEM_HOST = 0, BA_MEM_DEVICE = 1 };
+
+/* Optional device allocator (for example PyTorch's caching allocator).  When
+ * alloc is NULL the library uses cudaMalloc / cudaFree.  alloc returns NULL
+ * on failure; stream is the handle's cudaStream_t. */
+typedef void* (*ba_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*ba_free_fn)(void* ptr, void* ctx);
+
+typedef struct {
+  int precision;        /* BA_FP64: every step in FP64.  BA_FP32: residuals,
+                           Jacobians, Schur blocks and PCG in FP32; cost sum,
+                           gain ratio, damping and 3x3 point inverses FP64.   */
+  int solver;           /* BA_SOLVER_DENSE: Cholesky of the reduced camera
+                           system; BA_SOLVER_PCG: block-Jacobi PCG;
+                           BA_SOLVER_AUTO: dense when 6C <= dense_max_dim.    */
+  int max_lm_iters;     /* LM iterations (one solve + one trial each), 1..256 */
+  double huber_delta;   /* Huber threshold in px; <= 0: plain least squares   */
+  double pcg_tol;       /* stop when ||r|| <= pcg_tol ||b||                    */
+  int pcg_max_iters;    /* cap on products with S per solve (per inner solve) */
+  int refine;           /* BA_FP32 + PCG: FP64 iterative refinement           */
+  int refine_max;       /* outer refinement steps (default 5)                 */
+  double refine_tol;    /* stop refinement at ||b - S x|| <= tol ||b||        */
+  double mu0;           /* initial damping (default 1e-4)                     */
+  int dense_max_dim;    /* BA_SOLVER_AUTO threshold on 6C (default 1200)      */
+  int device;           /* CUDA device ordinal                                */
+  void* cuda_stream;    /* cudaStream_t to run on; NULL: library-owned stream */
+  int use_graph;        /* replay the LM loop as one CUDA graph (default 1)   */
+  ba_alloc_fn alloc;    /* optional device allocator                          */
+  ba_free_fn free_fn;
+  void* alloc_ctx;
+  /* serving handles only (see ba_create_server) */
+  size_t serve_arena_bytes; /* device memory reserved for request slots      */
+  int serve_slots;          /* maximum requests resident at once             */
+  int serve_queue;          /* maximum requests waiting for admission        */
+  int profile;              /* record per-kernel device times (CUDA events
+                               between the kernels of the captured loop)      */
+} ba_options;
+
+typedef struct {
+  double fx, fy, cx, cy;  /* pinhole intrinsics in px, shared by all cameras */
+} ba_intrinsics;
+
+#define BA_MAX_ITERS 256
+
+/* Per-solve report.  cost[0] is F at the initial state, cost[i+1] F after
+ * iteration i (unchanged by a rejected step). */
+typedef struct {
+  int32_t status;                    /* ba_status of the solve               */
+  int32_t n_iters;
+  int32_t n_accepted;
+  int32_t solver;                    /* BA_SOLVER_DENSE or BA_SOLVER_PCG     */
+  double cost[BA_MAX_ITERS + 1];
+  uint8_t accepted[BA_MAX_ITERS];
+  double mu[BA_MAX_ITERS];           /* damping used by iteration i's solve  */
+  int32_t pcg_iters[BA_MAX_ITERS];   /* products with S (0 for dense)       */
+  double pcg_rel_residual[BA_MAX_ITERS];
+  double gain[BA_MAX_ITERS];         /* gain ratio; -inf when dL <= 0        */
+  double rmse_px;                    /* final sqrt(sum ||r||^2 / n_valid)    */
+  int64_t n_valid_obs;               /* observations with depth >= 1e-3     */
+  double solve_ms;                   /* device time of the LM loop           */
+  double setup_ms;                   /* device time of ba_set_problem        */
+  int32_t n_kernels;                 /* library kernels launched by the solve */
+  int32_t pad;
+} ba_report;
+
+/* Per-kernel device time of the last ba_solve (opts.profile = 1 only). */
+typedef struct {
+  char name[24];
+  int32_t launches;
+  int32_t pad;
+  double total_ms;
+} ba_kernel_stat;
+
+/* Fill *opts with the defaults: FP64, AUTO solver, 10 iterations, no Huber,
+ * PCG tol 1e-6 / 100, no refinement (5 steps, tol 1e-6 when enabled),
+ * mu0 1e-4, dense_max_dim 1200, device 0, library stream, graphs on,
+ * cudaMalloc, serving arena 0 (= 1/4 of free memory), 256 slots, 4096 queue. */
+void ba_options_default(ba_options* opts);
+
+/* Create a solver handle on opts->device.  *out receives the handle; the
+ * handle owns every device buffer it allocates.  Errors: INVALID_ARG (NULL
+ * pointers, bad option values), CUDA. */
+ba_status ba_create(const ba_options* opts, ba_handle** out);
+
+/* Load a problem (Sec. 4.3: poses, points, tracks of observations, fixed
+ * camera subset) and build its device layout: observations sorted by
+ * (camera, point) and by (point, camera), CSR indexes of both orders and the
+ * block pattern of the reduced camera matrix S.  Replaces any earlier
+ * problem on the handle.
+ *   cam_qt   [n_cams][7]   initial poses (see conventions)
+ *   pts      [n_pts][3]    initial points
+ *   obs_cam  [n_obs]       camera index of each observation, 0..n_cams-1
+ *   obs_pt   [n_obs]       point index of each observation, 0..n_pts-1
+ *   obs_uv   [n_obs][2]    measured pixel (u, v)
+ *   K                      intrinsics (host pointer always)
+ *   cam_fixed [n_cams] or NULL: nonzero = pose held fixed (gauge / prior map)
+ * Errors: INVALID_ARG when a size is < 1, an index is out of range, a value
+ * is not finite, a quaternion is zero, a point has fewer than 2
+ * observations or a free camera has none; OOM; CUDA. */
+ba_status ba_set_problem(ba_handle* h, int32_t n_cams, int32_t n_pts, int64_t n_obs,
+                         const double* cam_qt, const double* pts, const int32_t* obs_cam,
+                         const int32_t* obs_pt, const double* obs_uv, const ba_intrinsics* K,
+                         const uint8_t* cam_fixed, int mem_kind);
+
+/* Run max_lm_iters LM iterations from the current state and wait for them.
+ * The state left on the device is the last accepted one, so a second call
+ * continues where the first stopped (resume).  out may be NULL.
+ * Errors: STATE (no problem loaded), TIMEOUT (a device barrier gave up),
+ * NUMERIC (non-finite cost), CUDA. */
+ba_status ba_solve(ba_handle* h, ba_report* out);
+
+/* Copy the current state out: cam_qt_out [n_cams][7] (qw >= 0), pts_out
+ * [n_pts][3]; either may be NULL.  Errors: STATE, INVALID_ARG, CUDA. */
+ba_status ba_get_state(const ba_handle* h, double* cam_qt_out, double* pts_out, int mem_kind);
+
+/* Overwrite the state (poses, points) of the loaded problem, keeping its
+ * layout; the damping restarts from mu0.  Errors: STATE, INVALID_ARG, CUDA. */
+ba_status ba_set_state(ba_handle* h, const double* cam_qt, const double* pts, int mem_kind);
+
+/* Kernel timings of the last solve, one entry per kernel kind: out[max]
+ * receives up to max entries, *n the number written.  Errors: STATE (no
+ * solve yet or profiling off), INVALID_ARG. */
+ba_status ba_kernel_stats(const ba_handle* h, ba_kernel_stat* out, int32_t max, int32_t* n);
+
+/* Release the handle and everything it owns.  NULL is ignored. */
+void ba_destroy(ba_handle* h);
+
+/* Description of the handle's last error ("" if none).  h may be NULL, then
+ * the last error of a failed ba_create on this thread is returned. */
+const char* ba_last_error(const ba_handle* h);
+
+/* ------------------------------------------------------------------------ */
+/* Batched and served local BA.                                             */
+
+/* One independent problem (a local-BA window or a served request).  Arrays
+ * are host memory; the *_out arrays (optional) receive the final state. */
+typedef struct {
+  int32_t n_cams, n_pts;
+  int64_t n_obs;
+  const double* cam_qt;
+  const double* pts;
+  const int32_t* obs_cam;
+  const int32_t* obs_pt;
+  const double* obs_uv;
+  const uint8_t* cam_fixed; /* NULL: camera 0 fixed */
+  ba_intrinsics K;
+  double* cam_qt_out;
+  double* pts_out;
+} ba_problem;
+
+typedef struct {
+  int32_t status;
+  int32_t n_iters;
+  int32_t n_accepted;
+  int32_t pad;
+  double initial_cost;
+  double final_cost;
+  double rmse_px;
+  double latency_ms;   /* served: submit -> result available on the host   */
+  double cost[BA_MAX_ITERS + 1];
+} ba_result;
+
+/* Solve n independent problems with the handle's options (dense solver per
+ * problem, max_lm_iters each) in one persistent launch: every CTA takes the
+ * next problem from a device work queue and runs its whole LM loop.
+ * results[n] receives each problem's costs.  Problems of the batch share
+ * nothing, so a result does not depend on the rest of the batch.
+ * Errors: INVALID_ARG (a problem fails validation; results[i].status says
+ * which), OOM, TIMEOUT, CUDA. */
+ba_status ba_solve_batch(ba_handle* h, int32_t n, const ba_problem* problems,
+                         ba_result* results);
+
+/* Tile schedule of the batched kernel, as chosen by the autotuner
+ * (threads per CTA, CTAs per SM).  ba_tune_batch times candidate schedules
+ * on the given problems and keeps the fastest on the handle. */
+ba_status ba_get_batch_schedule(const ba_handle* h, int32_t* threads, int32_t* ctas_per_sm);
+ba_status ba_set_batch_schedule(ba_handle* h, int32_t threads, int32_t ctas_per_sm);
+ba_status ba_tune_batch(ba_handle* h, int32_t n, const ba_problem* problems,
+                        int32_t* best_threads, int32_t* best_ctas_per_sm);
+
+/* Create a serving handle: a persistent device worker that admits requests
+ * into slots of a device arena as slots and memory free up, runs several at
+ * once, and keeps each request's poses, points and LM state resident until
+ * it is polled.  opts->serve_* size the arena, slots and queue. */
+ba_status ba_create_server(const ba_options* opts, ba_handle** out);
+
+/* Queue one request (copied in; the caller may free its arrays on return).
+ * *req_id receives its id.  A request waits on the host when no slot or
+ * arena space is free and is admitted as soon as there is.  Errors:
+ * INVALID_ARG (validation), BUSY (waiting queue full), STATE (not a server
+ * handle), OOM (larger than the whole arena). */
+ba_status ba_submit(ba_handle* server, const ba_problem* req, uint64_t* req_id);
+
+/* Collect a request: NOT_READY while it is queued or running; BA_OK once
+ * done, with *out filled and the outputs copied into req->cam_qt_out /
+ * pts_out as given at submit.  A request is returned once; later polls of
+ * the same id give INVALID_ARG. */
+ba_status ba_poll(ba_handle* server, uint64_t req_id, ba_result* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BA_H */

@@ -568,11 +568,16 @@ def lm_solve(prob: Problem, st0: State, opts: LMOptions) -> LMResult:
 
 # ----------------------------------------------------------------------------- metrics
 
-def rmse(prob: Problem, st: State, mask: Optional[np.ndarray] = None) -> float:
+def rmse(prob: Problem, st: State, mask: Optional[np.ndarray] = None,
+         threshold: Optional[float] = None) -> float:
     """sqrt(sum ||r_k||^2 / n) px over the observations in front of the camera
-    (and in mask, when given)."""
+    (and in mask, when given).  With a threshold, observations whose
+    reprojection error exceeds it are left out, as the mapping loop removes
+    them after each BA round (Sec. 4.3, outlier removal)."""
     r, _, valid = residuals(prob, st)
     sel = valid if mask is None else (valid & np.asarray(mask, dtype=bool))
+    if threshold is not None:
+        sel = sel & (np.sum(r * r, axis=1) < threshold * threshold)
     if not sel.any():
         return 0.0
     return float(np.sqrt(np.sum(r[sel] ** 2) / sel.sum()))

@@ -1,0 +1,797 @@
+// C ABI of libba: solver handles, problem layout, the device-resident LM
+// loop (captured once into a CUDA graph and replayed), and state I/O.
+// Batched and served solves live in batch.cu and serve.cu.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "handle.h"
+#include "layout.h"
+#include "lm.h"
+
+using namespace ba;
+
+namespace ba {
+
+thread_local std::string g_create_error;
+
+void* dev_alloc(ba_handle* h, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~size_t(255);
+  void* p = nullptr;
+  if (h->opts.alloc) {
+    p = h->opts.alloc(bytes, (void*)h->stream, h->opts.alloc_ctx);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  return p;
+}
+
+void dev_free(ba_handle* h, void* p) {
+  if (!p) return;
+  if (h->opts.alloc && h->opts.free_fn) h->opts.free_fn(p, h->opts.alloc_ctx);
+  else cudaFree(p);
+}
+
+void free_problem(ba_handle* h) {
+  if (h->gexec) {
+    cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+  }
+  h->graph_iters = -1;
+  if (!h->bufs.empty()) cudaStreamSynchronize(h->stream);
+  for (void* p : h->bufs) dev_free(h, p);
+  h->bufs.clear();
+  h->d = DevProblem();
+  h->loaded = false;
+  h->solved = false;
+}
+
+}  // namespace ba
+
+#define CK(call)                                                                   \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      h->err = std::string(#call) + ": " + cudaGetErrorString(e_);                \
+      return BA_ERR_CUDA;                                                          \
+    }                                                                              \
+  } while (0)
+
+namespace {
+
+// Owns temporary device buffers of one call.
+struct Temps {
+  ba_handle* h;
+  std::vector<void*> v;
+  explicit Temps(ba_handle* hh) : h(hh) {}
+  void* get(size_t n) {
+    void* p = dev_alloc(h, n);
+    if (p) v.push_back(p);
+    return p;
+  }
+  ~Temps() {
+    if (!v.empty()) cudaStreamSynchronize(h->stream);
+    for (void* p : v) dev_free(h, p);
+  }
+};
+
+template <typename P>
+bool keep(ba_handle* h, P*& out, size_t bytes) {
+  void* p = dev_alloc(h, bytes);
+  if (!p) return false;
+  h->bufs.push_back(p);
+  out = (P*)p;
+  return true;
+}
+
+std::string describe_flags(int f) {
+  std::string s;
+  if (f & kBadCamIndex) s += " camera index out of range;";
+  if (f & kBadPtIndex) s += " point index out of range;";
+  if (f & kBadUv) s += " non-finite pixel;";
+  if (f & kBadCamPose) s += " non-finite pose or zero quaternion;";
+  if (f & kBadPoint) s += " non-finite point;";
+  if (f & kPointUnderObserved) s += " a point has fewer than 2 observations;";
+  if (f & kCameraUnobserved) s += " a free camera has no observation;";
+  return s;
+}
+
+size_t max_dyn_smem(int device) {
+  int v = 0;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  return (size_t)v;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ba_options_default(ba_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->precision = BA_FP64;
+  o->solver = BA_SOLVER_AUTO;
+  o->max_lm_iters = 10;
+  o->huber_delta = 0.0;
+  o->pcg_tol = 1e-6;
+  o->pcg_max_iters = 100;
+  o->refine = 0;
+  o->refine_max = 5;
+  o->refine_tol = 1e-6;
+  o->mu0 = 1e-4;
+  o->dense_max_dim = 1200;
+  o->device = 0;
+  o->cuda_stream = nullptr;
+  o->use_graph = 1;
+  o->serve_arena_bytes = 0;
+  o->serve_slots = 256;
+  o->serve_queue = 4096;
+}
+
+static ba_status check_options(const ba_options* o, std::string& err) {
+  if (o->precision != BA_FP64 && o->precision != BA_FP32) {
+    err = "precision must be BA_FP64 or BA_FP32";
+    return BA_ERR_INVALID_ARG;
+  }
+  if (o->solver < BA_SOLVER_AUTO || o->solver > BA_SOLVER_PCG) {
+    err = "solver must be BA_SOLVER_AUTO, BA_SOLVER_DENSE or BA_SOLVER_PCG";
+    return BA_ERR_INVALID_ARG;
+  }
+  if (o->max_lm_iters < 1 || o->max_lm_iters > BA_MAX_ITERS) {
+    err = "max_lm_iters must be in 1..256";
+    return BA_ERR_INVALID_ARG;
+  }
+  if (!(o->pcg_tol >= 0.0) || o->pcg_max_iters < 1 || o->refine_max < 1 ||
+      !(o->refine_tol >= 0.0) || !(o->mu0 > 0.0) || !isfinite(o->huber_delta)) {
+    err = "bad PCG, refinement, damping or Huber option";
+    return BA_ERR_INVALID_ARG;
+  }
+  if ((o->alloc == nullptr) != (o->free_fn == nullptr)) {
+    err = "alloc and free_fn must be given together";
+    return BA_ERR_INVALID_ARG;
+  }
+  return BA_OK;
+}
+
+ba_status ba_create(const ba_options* opts, ba_handle** out) {
+  g_create_error.clear();
+  if (!opts || !out) {
+    g_create_error = "ba_create: NULL argument";
+    return BA_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  std::string err;
+  ba_status st = check_options(opts, err);
+  if (st != BA_OK) {
+    g_create_error = err;
+    return st;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || opts->device < 0 || opts->device >= ndev) {
+    cudaGetLastError();
+    g_create_error = "ba_create: no such CUDA device";
+    return BA_ERR_CUDA;
+  }
+  if (cudaSetDevice(opts->device) != cudaSuccess) {
+    g_create_error = "ba_create: cudaSetDevice failed";
+    return BA_ERR_CUDA;
+  }
+  ba_handle* h = new ba_handle();
+  h->opts = *opts;
+  h->device = opts->device;
+  if (opts->cuda_stream) {
+    h->stream = (cudaStream_t)opts->cuda_stream;
+    h->own_stream = false;
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete h;
+      g_create_error = "ba_create: cudaStreamCreate failed";
+      return BA_ERR_CUDA;
+    }
+    h->own_stream = true;
+  }
+  cudaEventCreate(&h->ev0);
+  cudaEventCreate(&h->ev1);
+  *out = h;
+  return BA_OK;
+}
+
+const char* ba_last_error(const ba_handle* h) {
+  if (!h) return g_create_error.c_str();
+  return h->err.c_str();
+}
+
+void ba_destroy(ba_handle* h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  destroy_server(h);
+  destroy_batch(h);
+  free_problem(h);
+  for (cudaEvent_t e : h->marks.pool) cudaEventDestroy(e);
+  if (h->marks.start) cudaEventDestroy(h->marks.start);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+ba_status ba_set_problem(ba_handle* h, int32_t n_cams, int32_t n_pts, int64_t n_obs,
+                         const double* cam_qt, const double* pts, const int32_t* obs_cam,
+                         const int32_t* obs_pt, const double* obs_uv, const ba_intrinsics* K,
+                         const uint8_t* cam_fixed, int mem_kind) {
+  if (!h) return BA_ERR_INVALID_ARG;
+  h->err.clear();
+  if (h->is_server) {
+    h->err = "ba_set_problem: serving handles take requests through ba_submit";
+    return BA_ERR_STATE;
+  }
+  if (n_cams < 1 || n_pts < 1 || n_obs < 1 || n_obs > (int64_t)INT32_MAX - 1) {
+    h->err = "ba_set_problem: need n_cams >= 1, n_pts >= 1, 1 <= n_obs < 2^31";
+    return BA_ERR_INVALID_ARG;
+  }
+  if (!cam_qt || !pts || !obs_cam || !obs_pt || !obs_uv || !K) {
+    h->err = "ba_set_problem: NULL array";
+    return BA_ERR_INVALID_ARG;
+  }
+  if (mem_kind != BA_MEM_HOST && mem_kind != BA_MEM_DEVICE) {
+    h->err = "ba_set_problem: mem_kind must be BA_MEM_HOST or BA_MEM_DEVICE";
+    return BA_ERR_INVALID_ARG;
+  }
+  if (!(K->fx > 0) || !(K->fy > 0) || !isfinite(K->cx) || !isfinite(K->cy) || !isfinite(K->fx) ||
+      !isfinite(K->fy)) {
+    h->err = "ba_set_problem: intrinsics must be finite with fx, fy > 0";
+    return BA_ERR_INVALID_ARG;
+  }
+  if ((int64_t)n_cams * 6 > (int64_t)INT32_MAX / 8) {
+    h->err = "ba_set_problem: too many cameras";
+    return BA_ERR_INVALID_ARG;
+  }
+  CK(cudaSetDevice(h->device));
+  free_problem(h);
+  cudaStream_t s = h->stream;
+  const int C = n_cams, P = n_pts;
+  const int64_t N = n_obs;
+  const int prec = h->opts.precision;
+  const size_t Tsz = prec == BA_FP32 ? sizeof(float) : sizeof(double);
+  Temps tmp(h);
+  CK(cudaEventRecord(h->ev0, s));
+
+  // ---- inputs on the device
+  const double *d_qt = cam_qt, *d_pts = pts, *d_uv = obs_uv;
+  const int32_t *d_cam = obs_cam, *d_pt = obs_pt;
+  const uint8_t* d_fixed_in = cam_fixed;
+  if (mem_kind == BA_MEM_HOST) {
+    void* a = tmp.get(C * 7 * sizeof(double));
+    void* b = tmp.get(P * 3 * sizeof(double));
+    void* c = tmp.get(N * 2 * sizeof(double));
+    void* e = tmp.get(N * sizeof(int32_t));
+    void* f = tmp.get(N * sizeof(int32_t));
+    void* g = cam_fixed ? tmp.get(C) : nullptr;
+    if (!a || !b || !c || !e || !f || (cam_fixed && !g)) {
+      h->err = "ba_set_problem: out of device memory (inputs)";
+      return BA_ERR_OOM;
+    }
+    CK(cudaMemcpyAsync(a, cam_qt, C * 7 * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(b, pts, P * 3 * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c, obs_uv, N * 2 * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(e, obs_cam, N * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(f, obs_pt, N * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    if (g) CK(cudaMemcpyAsync(g, cam_fixed, C, cudaMemcpyHostToDevice, s));
+    d_qt = (const double*)a;
+    d_pts = (const double*)b;
+    d_uv = (const double*)c;
+    d_cam = (const int32_t*)e;
+    d_pt = (const int32_t*)f;
+    d_fixed_in = (const uint8_t*)g;
+  }
+
+  DevProblem d;
+  d.C = C;
+  d.P = P;
+  d.N = N;
+  d.K = Intrinsics{K->fx, K->fy, K->cx, K->cy};
+  d.precision = prec;
+
+  // ---- validation and counts
+  int32_t* cam_cnt = (int32_t*)tmp.get(C * sizeof(int32_t));
+  int32_t* pt_cnt = (int32_t*)tmp.get(P * sizeof(int32_t));
+  bool ok = cam_cnt && pt_cnt && keep(h, d.flags, 64);
+  ok = ok && keep(h, d.fixed, C);
+  if (!ok) {
+    h->err = "ba_set_problem: out of device memory";
+    free_problem(h);
+    return BA_ERR_OOM;
+  }
+  CK(cudaMemsetAsync(cam_cnt, 0, C * sizeof(int32_t), s));
+  CK(cudaMemsetAsync(pt_cnt, 0, P * sizeof(int32_t), s));
+  CK(cudaMemsetAsync(d.flags, 0, 64, s));
+  if (d_fixed_in) CK(cudaMemcpyAsync(d.fixed, d_fixed_in, C, cudaMemcpyDeviceToDevice, s));
+  else CK(cudaMemsetAsync(d.fixed, 0, C, s));
+  launch_validate(N, C, P, d_cam, d_pt, d_uv, d_qt, d_pts, d.fixed, cam_cnt, pt_cnt, d.flags, s);
+  CK(cudaGetLastError());
+  int flags = 0;
+  CK(cudaMemcpyAsync(&flags, d.flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (flags) {
+    h->err = "ba_set_problem: invalid problem:" + describe_flags(flags);
+    h->d = d;
+    free_problem(h);
+    return BA_ERR_INVALID_ARG;
+  }
+  std::vector<uint8_t> hfixed(C);
+  CK(cudaMemcpy(hfixed.data(), d.fixed, C, cudaMemcpyDeviceToHost));
+  d.n_fixed = (int)std::count_if(hfixed.begin(), hfixed.end(), [](uint8_t v) { return v != 0; });
+
+  // ---- CSR pointers
+  const int64_t stmp = scan_tmp_elems(std::max<int64_t>(std::max<int64_t>(C, P), 256 * ((N + 4095) / 4096)));
+  int32_t* scan_tmp = (int32_t*)tmp.get(stmp * sizeof(int32_t) + 64);
+  ok = scan_tmp && keep(h, d.cam_ptr, (C + 1) * sizeof(int32_t)) &&
+       keep(h, d.pt_ptr, (P + 1) * sizeof(int32_t));
+  if (!ok) {
+    h->err = "ba_set_problem: out of device memory (CSR)";
+    free_problem(h);
+    return BA_ERR_OOM;
+  }
+  launch_scan_i32(cam_cnt, d.cam_ptr, C, scan_tmp, d.cam_ptr + C, s);
+  launch_scan_i32(pt_cnt, d.pt_ptr, P, scan_tmp, d.pt_ptr + P, s);
+
+  // ---- sorts by (camera, point) and (point, camera)
+  uint64_t* k0 = (uint64_t*)tmp.get(N * sizeof(uint64_t));
+  uint64_t* k1 = (uint64_t*)tmp.get(N * sizeof(uint64_t));
+  int32_t* perm_c = (int32_t*)tmp.get(N * sizeof(int32_t));
+  int32_t* perm_p = (int32_t*)tmp.get(N * sizeof(int32_t));
+  int32_t* v1 = (int32_t*)tmp.get(N * sizeof(int32_t));
+  int32_t* inv = (int32_t*)tmp.get(N * sizeof(int32_t));
+  uint32_t* counts = (uint32_t*)tmp.get(radix_counts_elems(N) * sizeof(uint32_t));
+  if (!k0 || !k1 || !perm_c || !perm_p || !v1 || !inv || !counts) {
+    h->err = "ba_set_problem: out of device memory (sort)";
+    free_problem(h);
+    return BA_ERR_OOM;
+  }
+  launch_make_keys(N, d_cam, d_pt, (uint64_t)P, k0, perm_c, s);
+  radix_sort_pairs(k0, perm_c, k1, v1, N, (uint64_t)C * (uint64_t)P, counts, (uint32_t*)scan_tmp, s);
+  launch_make_keys(N, d_pt, d_cam, (uint64_t)C, k0, perm_p, s);
+  radix_sort_pairs(k0, perm_p, k1, v1, N, (uint64_t)C * (uint64_t)P, counts, (uint32_t*)scan_tmp, s);
+  ok = keep(h, d.oc_cam, N * sizeof(int32_t)) && keep(h, d.oc_pt, N * sizeof(int32_t)) &&
+       keep(h, d.oc_uv, N * 2 * Tsz) && keep(h, d.po_k, N * sizeof(int32_t)) &&
+       keep(h, d.po_cam, N * sizeof(int32_t)) && keep(h, d.po_uv, N * 2 * Tsz);
+  if (!ok) {
+    h->err = "ba_set_problem: out of device memory (observations)";
+    free_problem(h);
+    return BA_ERR_OOM;
+  }
+  launch_gather(prec, N, perm_c, perm_p, d_cam, d_pt, d_uv, d, inv, s);
+  CK(cudaGetLastError());
+
+  // ---- block pattern of S
+  int32_t* row_nnz = (int32_t*)tmp.get(C * sizeof(int32_t));
+  ok = row_nnz && keep(h, d.s_rowptr, (C + 1) * sizeof(int32_t)) &&
+       keep(h, d.s_diag, C * sizeof(int32_t));
+  if (!ok || pattern_smem(C) > max_dyn_smem(h->device)) {
+    h->err = ok ? "ba_set_problem: too many cameras for the pattern bitmap"
+                : "ba_set_problem: out of device memory (pattern)";
+    free_problem(h);
+    return ok ? BA_ERR_INVALID_ARG : BA_ERR_OOM;
+  }
+  launch_pattern(d, row_nnz, nullptr, 0, s);
+  launch_scan_i32(row_nnz, d.s_rowptr, C, scan_tmp, d.s_rowptr + C, s);
+  CK(cudaGetLastError());
+  std::vector<int32_t> hrow(C);
+  int32_t nnzb = 0;
+  CK(cudaMemcpyAsync(hrow.data(), row_nnz, C * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&nnzb, d.s_rowptr + C, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  d.nnzb = nnzb;
+  d.max_row_nnz = *std::max_element(hrow.begin(), hrow.end());
+  ok = keep(h, d.s_col, (size_t)nnzb * sizeof(int32_t)) && keep(h, d.S, (size_t)nnzb * 36 * Tsz);
+  if (!ok) {
+    h->err = "ba_set_problem: out of device memory (S)";
+    free_problem(h);
+    return BA_ERR_OOM;
+  }
+  launch_pattern(d, nullptr, d.s_rowptr, 1, s);
+  CK(cudaGetLastError());
+
+  // ---- Schur pair list (pairs of observations of one point, grouped by
+  // camera row chunk and output block)
+  {
+    std::vector<int32_t> hpt(P + 1);
+    CK(cudaMemcpy(hpt.data(), d.pt_ptr, (P + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    int64_t np = 0;
+    for (int j = 0; j < P; ++j) {
+      const int64_t L = hpt[j + 1] - hpt[j];
+      np += L * L;
+    }
+    if (np >= (int64_t)INT32_MAX - 1) {
+      h->err = "ba_set_problem: more than 2^31 observation pairs (sum of squared track lengths)";
+      free_problem(h);
+      return BA_ERR_INVALID_ARG;
+    }
+    d.npairs = np;
+    int32_t* cnt = (int32_t*)tmp.get((N + 1) * sizeof(int32_t));
+    int32_t* pair_ptr = (int32_t*)tmp.get((N + 1) * sizeof(int32_t));
+    int32_t* nch = (int32_t*)tmp.get((C + 1) * sizeof(int32_t));
+    const int64_t st2 = scan_tmp_elems(std::max<int64_t>(np, 256 * ((np + 4095) / 4096)));
+    int32_t* stmp2 = (int32_t*)tmp.get(st2 * sizeof(int32_t) + 64);
+    ok = cnt && pair_ptr && nch && stmp2 && keep(h, d.chunk_ptr, (C + 1) * sizeof(int32_t));
+    if (!ok) {
+      h->err = "ba_set_problem: out of device memory (pair counts)";
+      free_problem(h);
+      return BA_ERR_OOM;
+    }
+    launch_pair_counts(d, cnt, nch, s);
+    launch_scan_i32(cnt, pair_ptr, N, stmp2, pair_ptr + N, s);
+    launch_scan_i32(nch, d.chunk_ptr, C, stmp2, d.chunk_ptr + C, s);
+    int32_t nchunks = 0;
+    CK(cudaMemcpyAsync(&nchunks, d.chunk_ptr + C, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    d.nchunks = nchunks;
+    uint64_t* pk0 = (uint64_t*)tmp.get(np * sizeof(uint64_t));
+    uint64_t* pk1 = (uint64_t*)tmp.get(np * sizeof(uint64_t));
+    int32_t* pv0 = (int32_t*)tmp.get(np * sizeof(int32_t));
+    int32_t* pv1 = (int32_t*)tmp.get(np * sizeof(int32_t));
+    uint16_t* gen_t = (uint16_t*)tmp.get(np * sizeof(uint16_t));
+    int32_t* gen_k2 = (int32_t*)tmp.get(np * sizeof(int32_t));
+    uint32_t* pcounts = (uint32_t*)tmp.get(radix_counts_elems(np) * sizeof(uint32_t));
+    ok = pk0 && pk1 && pv0 && pv1 && gen_t && gen_k2 && pcounts &&
+         keep(h, d.pair_t, np * sizeof(uint16_t)) && keep(h, d.pair_k2, np * sizeof(int32_t));
+    if (!ok) {
+      h->err = "ba_set_problem: out of device memory (pair list)";
+      free_problem(h);
+      return BA_ERR_OOM;
+    }
+    launch_gen_pairs(d, d.chunk_ptr, pair_ptr, pk0, pv0, gen_t, gen_k2, s);
+    radix_sort_pairs(pk0, pv0, pk1, pv1, np, ((uint64_t)nchunks << 20) | 0xFFFFFu, pcounts,
+                     (uint32_t*)stmp2, s);
+    // reuse the second key / value buffers as head flags and segment ids
+    int32_t* head = pv1;
+    int32_t* segid = (int32_t*)pk1;
+    launch_pair_gather(np, pk0, pv0, gen_t, gen_k2, d.pair_t, d.pair_k2, head, s);
+    launch_scan_i32(head, segid, np, stmp2, segid + np, s);
+    int32_t nseg = 0;
+    CK(cudaMemcpyAsync(&nseg, segid + np, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    d.nseg = nseg;
+    ok = keep(h, d.seg_begin, (nseg + 1) * sizeof(int32_t)) &&
+         keep(h, d.seg_slot, nseg * sizeof(int32_t)) &&
+         keep(h, d.chunk_seg, (nchunks + 1) * sizeof(int32_t));
+    if (!ok) {
+      h->err = "ba_set_problem: out of device memory (segments)";
+      free_problem(h);
+      return BA_ERR_OOM;
+    }
+    launch_segments(np, pk0, head, segid, d.seg_begin, d.seg_slot, d.chunk_seg, nseg, nchunks, s);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+  }
+
+  // ---- solver buffers and state
+  const int wst = prec == BA_FP32 ? kWStrideF32 : kWStrideF64;
+  ok = keep(h, d.W, (size_t)N * wst * Tsz) && keep(h, d.U, (size_t)C * 36 * Tsz) &&
+       keep(h, d.gc, (size_t)C * 6 * Tsz) && keep(h, d.V, (size_t)P * 6 * Tsz) &&
+       keep(h, d.gp, (size_t)P * 3 * Tsz) && keep(h, d.Vinv, (size_t)P * 6 * sizeof(double)) &&
+       keep(h, d.e, (size_t)P * 3 * Tsz) && keep(h, d.b, (size_t)C * 6 * Tsz) &&
+       keep(h, d.Minv, (size_t)C * 36 * Tsz) && keep(h, d.dc, (size_t)C * 6 * Tsz) &&
+       keep(h, d.dp, (size_t)P * 3 * Tsz) && keep(h, d.b64, (size_t)C * 6 * sizeof(double)) &&
+       keep(h, d.x64, (size_t)C * 6 * sizeof(double)) && keep(h, d.rv, (size_t)C * 6 * Tsz) &&
+       keep(h, d.z, (size_t)C * 6 * Tsz) && keep(h, d.qv, (size_t)C * 6 * Tsz) &&
+       keep(h, d.p0, (size_t)C * 6 * Tsz) && keep(h, d.p1, (size_t)C * 6 * Tsz) &&
+       keep(h, d.part, kPartTotal * sizeof(double)) && keep(h, d.barrier, 64) &&
+       keep(h, d.lm, sizeof(LmScalars)) &&
+       keep(h, d.rep.cost, (BA_MAX_ITERS + 1) * sizeof(double)) &&
+       keep(h, d.rep.accepted, BA_MAX_ITERS) && keep(h, d.rep.mu, BA_MAX_ITERS * sizeof(double)) &&
+       keep(h, d.rep.pcg_iters, BA_MAX_ITERS * sizeof(int32_t)) &&
+       keep(h, d.rep.pcg_rel, BA_MAX_ITERS * sizeof(double)) &&
+       keep(h, d.rep.gain, BA_MAX_ITERS * sizeof(double)) &&
+       keep(h, d.rep.rmse_parts, 2 * sizeof(double)) && keep(h, d.R, C * 9 * sizeof(double)) &&
+       keep(h, d.t, C * 3 * sizeof(double)) && keep(h, d.Cc, C * 3 * sizeof(double)) &&
+       keep(h, d.X, (size_t)P * 3 * sizeof(double)) && keep(h, d.R2, C * 9 * sizeof(double)) &&
+       keep(h, d.t2, C * 3 * sizeof(double)) && keep(h, d.Cc2, C * 3 * sizeof(double)) &&
+       keep(h, d.X2, (size_t)P * 3 * sizeof(double));
+  if (!ok) {
+    h->err = "ba_set_problem: out of device memory (solver buffers)";
+    free_problem(h);
+    return BA_ERR_OOM;
+  }
+  if (prec == BA_FP32) {
+    ok = keep(h, d.cam32, (size_t)C * kCam32 * sizeof(float)) &&
+         keep(h, d.cam32b, (size_t)C * kCam32 * sizeof(float)) &&
+         keep(h, d.X32, (size_t)P * kPt32 * sizeof(float)) &&
+         keep(h, d.X32b, (size_t)P * kPt32 * sizeof(float));
+    if (!ok) {
+      h->err = "ba_set_problem: out of device memory (FP32 state)";
+      free_problem(h);
+      return BA_ERR_OOM;
+    }
+  }
+  CK(cudaMemsetAsync(d.barrier, 0, 64, s));
+  CK(cudaMemsetAsync(d.lm, 0, sizeof(LmScalars), s));
+  CK(cudaMemsetAsync(d.part, 0, kPartTotal * sizeof(double), s));
+  CK(cudaMemsetAsync(d.rep.cost, 0, (BA_MAX_ITERS + 1) * sizeof(double), s));
+  launch_init_cams(C, d_qt, d.R, d.t, d.Cc, d.cam32, s);
+  CK(cudaMemcpyAsync(d.X, d_pts, (size_t)P * 3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (d.X32) launch_split_points(P, d.X, d.X32, s);
+  if (d.cam32b) CK(cudaMemcpyAsync(d.cam32b, d.cam32, (size_t)C * kCam32 * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  if (d.X32b) CK(cudaMemcpyAsync(d.X32b, d.X32, (size_t)P * kPt32 * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(d.R2, d.R, C * 9 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(d.t2, d.t, C * 3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(d.Cc2, d.Cc, C * 3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(d.X2, d.X, (size_t)P * 3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  {
+    LmScalars init{};
+    init.fresh = 1;
+    CK(cudaMemcpyAsync(d.lm, &init, sizeof(LmScalars), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));  // `init` lives on this stack frame
+  }
+
+  // ---- solver configuration
+  SolveConfig& cfg = h->cfg;
+  cfg = SolveConfig();
+  cfg.huber_delta = h->opts.huber_delta;
+  cfg.mu0 = h->opts.mu0;
+  cfg.pcg_tol = h->opts.pcg_tol;
+  cfg.pcg_max = h->opts.pcg_max_iters;
+  cfg.refine = (h->opts.refine && prec == BA_FP32) ? 1 : 0;
+  cfg.refine_max = h->opts.refine_max;
+  cfg.refine_tol = h->opts.refine_tol;
+  int solver = h->opts.solver;
+  if (solver == BA_SOLVER_AUTO) solver = (6 * C <= h->opts.dense_max_dim) ? BA_SOLVER_DENSE : BA_SOLVER_PCG;
+  cfg.solver = solver;
+  if (solver == BA_SOLVER_DENSE && 6 * C > kDenseMaxDim) {
+    h->err = "ba_set_problem: the dense solver takes at most 682 cameras (6C <= 4096); use PCG";
+    free_problem(h);
+    return BA_ERR_INVALID_ARG;
+  }
+  const size_t smax = max_dyn_smem(h->device);
+  if (solver == BA_SOLVER_DENSE) {
+    const size_t need = dense_smem_bytes(prec, 6 * C);
+    if (need + 1024 <= smax) {
+      cfg.dense_smem = need;
+      set_dense_smem_attr(prec, need);
+    } else {
+      cfg.dense_smem = 0;
+      if (!keep(h, d.dense, need)) {
+        h->err = "ba_set_problem: out of device memory (dense workspace)";
+        free_problem(h);
+        return BA_ERR_OOM;
+      }
+    }
+  } else {
+    std::vector<int32_t> hrp(C + 1, 0);
+    for (int i = 0; i < C; ++i) hrp[i + 1] = hrp[i] + hrow[i];
+    if (!plan_pcg(prec, h->device, hrp, smax - 4096, cfg)) {
+      h->err = "ba_set_problem: too many cameras for the PCG kernel";
+      free_problem(h);
+      return BA_ERR_INVALID_ARG;
+    }
+  }
+  cfg.schur_colcap = schur_colcap(prec, d.max_row_nnz, smax - 2048);
+  set_schur_smem_attr(prec, schur_smem(prec, cfg.schur_colcap));
+  CK(cudaEventRecord(h->ev1, s));
+  CK(cudaEventSynchronize(h->ev1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+  h->setup_ms = ms;
+  CK(cudaGetLastError());
+  h->d = d;
+  h->loaded = true;
+  return BA_OK;
+}
+
+static void reset_marks(ba_handle* h) {
+  Marks& m = h->marks;
+  m.profile = h->opts.profile != 0;
+  m.launches = 0;
+  m.kind.clear();
+  m.ev.clear();
+  m.used = 0;
+  if (m.profile && !m.start) cudaEventCreate(&m.start);
+  h->cfg.marks = &m;
+}
+
+static ba_status run_solve(ba_handle* h, int iters) {
+  cudaStream_t s = h->stream;
+  SolveConfig& cfg = h->cfg;
+  cfg.iters = iters;
+  const DevProblem& d = h->d;
+  if (h->opts.use_graph) {
+    if (!h->gexec || h->graph_iters != iters) {
+      if (h->gexec) {
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+      }
+      cudaGraph_t g = nullptr;
+      reset_marks(h);
+      CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      if (h->marks.profile) cudaEventRecordWithFlags(h->marks.start, s, cudaEventRecordExternal);
+      launch_lm_begin(d, cfg, s);
+      for (int it = 0; it < iters; ++it) launch_lm_iteration(d, cfg, s);
+      launch_lm_end(d, cfg, s);
+      cudaError_t ce = cudaStreamEndCapture(s, &g);
+      if (ce != cudaSuccess) {
+        h->err = std::string("graph capture failed: ") + cudaGetErrorString(ce);
+        if (g) cudaGraphDestroy(g);
+        return BA_ERR_CUDA;
+      }
+      ce = cudaGraphInstantiate(&h->gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (ce != cudaSuccess) {
+        h->err = std::string("graph instantiate failed: ") + cudaGetErrorString(ce);
+        h->gexec = nullptr;
+        return BA_ERR_CUDA;
+      }
+      h->graph_iters = iters;
+    }
+    CK(cudaEventRecord(h->ev0, s));
+    CK(cudaGraphLaunch(h->gexec, s));
+    CK(cudaEventRecord(h->ev1, s));
+  } else {
+    reset_marks(h);
+    CK(cudaEventRecord(h->ev0, s));
+    if (h->marks.profile) cudaEventRecordWithFlags(h->marks.start, s, cudaEventRecordExternal);
+    launch_lm_begin(d, cfg, s);
+    for (int it = 0; it < iters; ++it) launch_lm_iteration(d, cfg, s);
+    launch_lm_end(d, cfg, s);
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(h->ev1, s));
+  }
+  return BA_OK;
+}
+
+ba_status ba_solve(ba_handle* h, ba_report* out) {
+  if (!h) return BA_ERR_INVALID_ARG;
+  h->err.clear();
+  if (!h->loaded) {
+    h->err = "ba_solve: no problem loaded";
+    return BA_ERR_STATE;
+  }
+  CK(cudaSetDevice(h->device));
+  const int iters = h->opts.max_lm_iters;
+  ba_status st = run_solve(h, iters);
+  if (st != BA_OK) return st;
+  CK(cudaEventSynchronize(h->ev1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+  const DevProblem& d = h->d;
+  LmScalars lm;
+  CK(cudaMemcpy(&lm, d.lm, sizeof(LmScalars), cudaMemcpyDeviceToHost));
+  if (out) {
+    memset(out, 0, sizeof(*out));
+    CK(cudaMemcpy(out->cost, d.rep.cost, (iters + 1) * sizeof(double), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(out->accepted, d.rep.accepted, iters, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(out->mu, d.rep.mu, iters * sizeof(double), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(out->pcg_iters, d.rep.pcg_iters, iters * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(out->pcg_rel_residual, d.rep.pcg_rel, iters * sizeof(double), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(out->gain, d.rep.gain, iters * sizeof(double), cudaMemcpyDeviceToHost));
+    double rp[2];
+    CK(cudaMemcpy(rp, d.rep.rmse_parts, sizeof(rp), cudaMemcpyDeviceToHost));
+    out->n_iters = iters;
+    out->n_accepted = lm.n_accepted;
+    out->solver = h->cfg.solver;
+    out->rmse_px = rp[1] > 0 ? sqrt(rp[0] / rp[1]) : 0.0;
+    out->n_valid_obs = (int64_t)rp[1];
+    out->solve_ms = ms;
+    out->setup_ms = h->setup_ms;
+    out->n_kernels = h->marks.launches;
+  }
+  h->solved = true;
+  h->last_solve_ms = ms;
+  ba_status rs = BA_OK;
+  if (lm.error & kErrBarrierTimeout) {
+    h->err = "ba_solve: a PCG grid barrier timed out";
+    rs = BA_ERR_TIMEOUT;
+  } else if (lm.error & kErrNonFinite) {
+    h->err = "ba_solve: non-finite cost";
+    rs = BA_ERR_NUMERIC;
+  }
+  if (out) out->status = rs;
+  return rs;
+}
+
+ba_status ba_kernel_stats(const ba_handle* hc, ba_kernel_stat* out, int32_t max, int32_t* n) {
+  ba_handle* h = const_cast<ba_handle*>(hc);
+  if (!h || !out || !n || max < 0) return BA_ERR_INVALID_ARG;
+  *n = 0;
+  if (!h->solved || !h->marks.profile) {
+    h->err = "ba_kernel_stats: needs opts.profile = 1 and a finished ba_solve";
+    return BA_ERR_STATE;
+  }
+  double tot[kKindCount] = {};
+  int cnt[kKindCount] = {};
+  cudaEvent_t prev = h->marks.start;
+  for (size_t i = 0; i < h->marks.ev.size(); ++i) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, prev, h->marks.ev[i]));
+    tot[h->marks.kind[i]] += ms;
+    cnt[h->marks.kind[i]] += 1;
+    prev = h->marks.ev[i];
+  }
+  int w = 0;
+  for (int k = 0; k < kKindCount && w < max; ++k) {
+    if (!cnt[k]) continue;
+    memset(&out[w], 0, sizeof(out[w]));
+    const char* nm = (k == kKSolve) ? (h->cfg.solver == BA_SOLVER_PCG ? "pcg" : "dense_cholesky")
+                                    : kKernelNames[k];
+    strncpy(out[w].name, nm, sizeof(out[w].name) - 1);
+    out[w].launches = cnt[k];
+    out[w].total_ms = tot[k];
+    ++w;
+  }
+  *n = w;
+  return BA_OK;
+}
+
+ba_status ba_get_state(const ba_handle* hc, double* cam_qt_out, double* pts_out, int mem_kind) {
+  ba_handle* h = const_cast<ba_handle*>(hc);
+  if (!h) return BA_ERR_INVALID_ARG;
+  if (!h->loaded) {
+    h->err = "ba_get_state: no problem loaded";
+    return BA_ERR_STATE;
+  }
+  if (mem_kind != BA_MEM_HOST && mem_kind != BA_MEM_DEVICE) {
+    h->err = "ba_get_state: bad mem_kind";
+    return BA_ERR_INVALID_ARG;
+  }
+  CK(cudaSetDevice(h->device));
+  const DevProblem& d = h->d;
+  cudaStream_t s = h->stream;
+  const cudaMemcpyKind kind = mem_kind == BA_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (cam_qt_out) {
+    Temps tmp(h);
+    double* q = (double*)tmp.get(d.C * 7 * sizeof(double));
+    if (!q) {
+      h->err = "ba_get_state: out of device memory";
+      return BA_ERR_OOM;
+    }
+    launch_cams_to_qt(d.C, d.R, d.t, q, s);
+    CK(cudaMemcpyAsync(cam_qt_out, q, d.C * 7 * sizeof(double), kind, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  if (pts_out) {
+    CK(cudaMemcpyAsync(pts_out, d.X, (size_t)d.P * 3 * sizeof(double), kind, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  return BA_OK;
+}
+
+ba_status ba_set_state(ba_handle* h, const double* cam_qt, const double* pts, int mem_kind) {
+  if (!h) return BA_ERR_INVALID_ARG;
+  h->err.clear();
+  if (!h->loaded) {
+    h->err = "ba_set_state: no problem loaded";
+    return BA_ERR_STATE;
+  }
+  if (!cam_qt || !pts || (mem_kind != BA_MEM_HOST && mem_kind != BA_MEM_DEVICE)) {
+    h->err = "ba_set_state: bad argument";
+    return BA_ERR_INVALID_ARG;
+  }
+  CK(cudaSetDevice(h->device));
+  DevProblem& d = h->d;
+  cudaStream_t s = h->stream;
+  Temps tmp(h);
+  const double* qd = cam_qt;
+  if (mem_kind == BA_MEM_HOST) {
+    double* q = (double*)tmp.get(d.C * 7 * sizeof(double));
+    if (!q) return BA_ERR_OOM;
+    CK(cudaMemcpyAsync(q, cam_qt, d.C * 7 * sizeof(double), cudaMemcpyHostToDevice, s));
+    qd = q;
+  }
+  launch_init_cams(d.C, qd, d.R, d.t, d.Cc, d.cam32, s);
+  const cudaMemcpyKind kind = mem_kind == BA_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  CK(cudaMemcpyAsync(d.X, pts, (size_t)d.P * 3 * sizeof(double), kind, s));
+  if (d.X32) launch_split_points(d.P, d.X, d.X32, s);
+  int one = 1;
+  CK(cudaMemcpyAsync(&d.lm->fresh, &one, sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  return BA_OK;
+}
+
+}  // extern "C"

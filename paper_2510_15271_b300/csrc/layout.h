@@ -1,0 +1,47 @@
+// Host-side entry points of the layout kernels (layout.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ba_internal.h"
+
+namespace ba {
+
+void launch_validate(int64_t N, int C, int P, const int32_t* cam, const int32_t* pt,
+                     const double* uv, const double* cam_qt, const double* pts,
+                     const uint8_t* fixed, int32_t* cam_cnt, int32_t* pt_cnt, int* flags,
+                     cudaStream_t s);
+int64_t scan_tmp_elems(int64_t n);
+void launch_scan_i32(const int32_t* in, int32_t* out, int64_t n, int32_t* tmp, int32_t* total,
+                     cudaStream_t s);
+int64_t radix_counts_elems(int64_t n);
+void launch_make_keys(int64_t N, const int32_t* a, const int32_t* b, uint64_t nb, uint64_t* keys,
+                      int32_t* vals, cudaStream_t s);
+void radix_sort_pairs(uint64_t* k0, int32_t* v0, uint64_t* k1, int32_t* v1, int64_t n,
+                      uint64_t maxkey, uint32_t* counts, uint32_t* scan_tmp, cudaStream_t s);
+void launch_gather(int precision, int64_t N, const int32_t* perm_c, const int32_t* perm_p,
+                   const int32_t* cam, const int32_t* pt, const double* uv, DevProblem& d,
+                   int32_t* inv, cudaStream_t s);
+size_t pattern_smem(int C);
+void launch_pattern(const DevProblem& d, int32_t* row_nnz, const int32_t* rowptr, int fill,
+                    cudaStream_t s);
+void launch_init_cams(int C, const double* qt, double* R, double* t, double* Cc, float* cam32,
+                      cudaStream_t s);
+void launch_split_points(int P, const double* X, float* X32, cudaStream_t s);
+void launch_cams_to_qt(int C, const double* R, const double* t, double* qt, cudaStream_t s);
+
+}  // namespace ba
+
+namespace ba {
+void launch_pair_counts(const DevProblem& d, int32_t* cnt, int32_t* nch, cudaStream_t s);
+void launch_gen_pairs(const DevProblem& d, const int32_t* chunk_ptr, const int32_t* pair_ptr,
+                      uint64_t* keys, int32_t* vals, uint16_t* gen_t, int32_t* gen_k2,
+                      cudaStream_t s);
+void launch_pair_gather(int64_t np, const uint64_t* keys, const int32_t* vals,
+                        const uint16_t* gen_t, const int32_t* gen_k2, uint16_t* pair_t,
+                        int32_t* pair_k2, int32_t* head, cudaStream_t s);
+void launch_segments(int64_t np, const uint64_t* keys, const int32_t* head, const int32_t* segid,
+                     int32_t* seg_begin, int32_t* seg_slot, int32_t* chunk_seg, int nseg,
+                     int nchunks, cudaStream_t s);
+}  // namespace ba

@@ -1,0 +1,74 @@
+// Host-side entry points of the LM iteration kernels (lm_kernels.cu) and the
+// linear solvers (solvers.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "ba_internal.h"
+
+namespace ba {
+
+// Kernel kinds of the LM loop (profiling marks).
+enum KernelKind : int {
+  kKCostBegin = 0, kKLmInit, kKLinCam, kKLinPt, kKDampPt, kKSchur, kKSolve, kKBacksub,
+  kKRetract, kKCost, kKGain, kKCommit, kKCostEnd, kKRmse, kKindCount
+};
+extern const char* const kKernelNames[kKindCount];
+
+// Launch bookkeeping of one captured solve: every launch is counted; with
+// profiling on, an event is recorded after each kernel (kind[i] ends at ev[i]).
+struct Marks {
+  bool profile = false;
+  int launches = 0;
+  cudaEvent_t start = nullptr;
+  std::vector<int> kind;
+  std::vector<cudaEvent_t> ev;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+};
+
+struct SolveConfig {
+  double huber_delta = 0.0;
+  double mu0 = 1e-4;
+  int iters = 10;
+  int solver = BA_SOLVER_DENSE;  // resolved: DENSE or PCG
+  double pcg_tol = 1e-6;
+  int pcg_max = 100;
+  int refine = 0;
+  int refine_max = 5;
+  double refine_tol = 1e-6;
+  int schur_colcap = 64;
+  int pcg_blocks = 1;      // cooperative grid of the PCG kernel
+  int pcg_threads = 256;
+  int pcg_rows = 1;        // block rows per CTA (contiguous)
+  int pcg_rw = 1;          // rows per warp (kernel variant)
+  int pcg_maxnnz = 0;      // most blocks of S held by one CTA
+  size_t pcg_smem = 0;     // dynamic shared memory (0: rows of S read from global)
+  size_t dense_smem = 0;   // dynamic shared memory of the dense solver (0: global workspace)
+  Marks* marks = nullptr;
+};
+
+// Count a launch of kind k and, when profiling, record its end event.
+void mark(const SolveConfig& cfg, int k, cudaStream_t s);
+
+int cost_blocks(const DevProblem& d);
+int backsub_blocks(const DevProblem& d);
+int retract_blocks(const DevProblem& d);
+size_t schur_smem(int precision, int colcap);
+int schur_colcap(int precision, int max_row_nnz, size_t smem_limit);
+void set_schur_smem_attr(int precision, size_t bytes);
+
+void launch_lm_begin(const DevProblem& d, const SolveConfig& cfg, cudaStream_t s);
+void launch_lm_iteration(const DevProblem& d, const SolveConfig& cfg, cudaStream_t s);
+void launch_lm_end(const DevProblem& d, const SolveConfig& cfg, cudaStream_t s);
+
+// solvers.cu
+void launch_linear_solve(const DevProblem& d, const SolveConfig& cfg, cudaStream_t s);
+bool plan_pcg(int precision, int device, const std::vector<int32_t>& rowptr, size_t smem_limit,
+              SolveConfig& cfg);
+size_t dense_smem_bytes(int precision, int n);
+void set_dense_smem_attr(int precision, size_t bytes);
+
+}  // namespace ba

@@ -1,0 +1,834 @@
+// Kernels of one Levenberg-Marquardt bundle-adjustment iteration on the
+// sparse (camera-sorted / point-sorted) layout.
+//
+//   k_lin_cam   per camera: residuals, Jacobians, Huber weights of its
+//               observations; U_i = sum w Jc^T Jc, g_c,i = sum w Jc^T r and
+//               W_k = w Jc^T Jp per observation          (skipped after a reject)
+//   k_lin_pt    per point: V_j = sum w Jp^T Jp, g_p,j = sum w Jp^T r (skipped
+//               after a reject)
+//   k_damp_pt   per point: V*_j = V_j + mu diag(V_j), V*_j^-1 in FP64, e_j = V*_j^-1 g_p,j
+//   k_schur     per camera row: S_ik = [i=k] U*_i - sum_j W_ij V*_j^-1 W_kj^T,
+//               b_i = -g_c,i + sum_j W_ij e_j, M_i = S_ii^-1 (block Jacobi)
+//   k_backsub   per point: dp_j = V*_j^-1 (-g_p,j - sum_k W_k^T dc_i(k)), trial
+//               point, point part of the model decrease
+//   k_retract   per camera: trial pose Exp(dc_i) T_i, camera part of the model
+//               decrease
+//   k_cost      F at a state (FP64 partial sums), or the RMSE sums
+//   k_gain      gain ratio, accept / reject, damping update, report entries
+//   k_commit    copy the trial state over the current one when accepted
+//
+// Methods: reprojection error and robust objective of cuSfM Sec. 4.3; normal
+// equations, IRLS weights and the Schur complement after Triggs et al. 2000
+// (Sec. 4.3, 6.1); LM with Marquardt scaling and Nielsen's damping update
+// after Madsen, Nielsen & Tingleff 2004 (Sec. 3.2).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "lm.h"
+
+namespace ba {
+
+template <typename T>
+struct WStride;
+template <>
+struct WStride<float> {
+  static constexpr int v = kWStrideF32;
+};
+template <>
+struct WStride<double> {
+  static constexpr int v = kWStrideF64;
+};
+
+// W block of one observation: 18 values, row-major 6x3.
+template <typename T>
+__device__ __forceinline__ void load_w(const T* __restrict__ W, int64_t k, T w[18]);
+template <>
+__device__ __forceinline__ void load_w<float>(const float* __restrict__ W, int64_t k, float w[18]) {
+  const float4* p = reinterpret_cast<const float4*>(W + k * kWStrideF32);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float4 v = __ldg(p + i);
+    w[4 * i] = v.x;
+    w[4 * i + 1] = v.y;
+    w[4 * i + 2] = v.z;
+    w[4 * i + 3] = v.w;
+  }
+  const float2 v = __ldg(reinterpret_cast<const float2*>(p + 4));
+  w[16] = v.x;
+  w[17] = v.y;
+}
+template <>
+__device__ __forceinline__ void load_w<double>(const double* __restrict__ W, int64_t k,
+                                               double w[18]) {
+  const double2* p = reinterpret_cast<const double2*>(W + k * kWStrideF64);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const double2 v = __ldg(p + i);
+    w[2 * i] = v.x;
+    w[2 * i + 1] = v.y;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void store_w(T* __restrict__ W, int64_t k, const T w[18]);
+template <>
+__device__ __forceinline__ void store_w<float>(float* __restrict__ W, int64_t k, const float w[18]) {
+  float4* p = reinterpret_cast<float4*>(W + k * kWStrideF32);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) p[i] = make_float4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
+  p[4] = make_float4(w[16], w[17], 0.f, 0.f);
+}
+template <>
+__device__ __forceinline__ void store_w<double>(double* __restrict__ W, int64_t k,
+                                                const double w[18]) {
+  double2* p = reinterpret_cast<double2*>(W + k * kWStrideF64);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) p[i] = make_double2(w[2 * i], w[2 * i + 1]);
+}
+
+template <typename T>
+__device__ __forceinline__ void load_uv(const T* __restrict__ uv, int64_t k, T& u, T& v);
+template <>
+__device__ __forceinline__ void load_uv<float>(const float* __restrict__ uv, int64_t k, float& u,
+                                               float& v) {
+  const float2 a = __ldg(reinterpret_cast<const float2*>(uv) + k);
+  u = a.x;
+  v = a.y;
+}
+template <>
+__device__ __forceinline__ void load_uv<double>(const double* __restrict__ uv, int64_t k, double& u,
+                                                double& v) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(uv) + k);
+  u = a.x;
+  v = a.y;
+}
+
+// Block-wide sum of NV values per thread into out[NV] (valid in thread 0..NV-1
+// via the shared array `red`, which must hold (blockDim/32) * NV elements).
+template <typename T, int NV>
+__device__ __forceinline__ void block_sum(T (&v)[NV], T* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = warp_sum(v[i]);
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) red[warp * NV + i] = v[i];
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    T s = T(0);
+    for (int w = 0; w < nw; ++w) s += red[w * NV + threadIdx.x];
+    red[threadIdx.x] = s;  // rows w >= 1 are not read again by thread < NV after this
+  }
+  __syncthreads();
+}
+
+// --------------------------------------------------------------------------- state views
+
+// Camera and point access of one state (current or trial) in precision T.
+// FP64: R, t and X in FP64.  FP32: the 16-float camera records and 6-float
+// two-float points (see to_camera32), so no FP64 arithmetic runs per
+// observation.
+template <typename T>
+struct View;
+
+template <>
+struct View<double> {
+  const double *R, *t, *X;
+  struct Cam {
+    double R[9], t[3];
+  };
+  __device__ View(const DevProblem& d, bool trial)
+      : R(trial ? d.R2 : d.R), t(trial ? d.t2 : d.t), X(trial ? d.X2 : d.X) {}
+  __device__ __forceinline__ void cam(int i, Cam& c) const {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) c.R[a] = R[9 * i + a];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) c.t[a] = t[3 * i + a];
+  }
+  __device__ __forceinline__ void xc(const Cam& c, int j, double out[3]) const {
+    to_camera64(c.R, c.t, X[3 * (int64_t)j], X[3 * (int64_t)j + 1], X[3 * (int64_t)j + 2], out);
+  }
+  __device__ __forceinline__ static const double* rot(const Cam& c) { return c.R; }
+};
+
+template <>
+struct View<float> {
+  const float *C, *X;
+  struct Cam {
+    float v[kCam32];
+  };
+  __device__ View(const DevProblem& d, bool trial)
+      : C(trial ? d.cam32b : d.cam32), X(trial ? d.X32b : d.X32) {}
+  __device__ __forceinline__ void cam(int i, Cam& c) const {
+    const float4* p = reinterpret_cast<const float4*>(C + kCam32 * (int64_t)i);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 v = __ldg(p + q);
+      c.v[4 * q] = v.x;
+      c.v[4 * q + 1] = v.y;
+      c.v[4 * q + 2] = v.z;
+      c.v[4 * q + 3] = v.w;
+    }
+  }
+  __device__ __forceinline__ void xc(const Cam& c, int j, float out[3]) const {
+    const float2* p = reinterpret_cast<const float2*>(X + kPt32 * (int64_t)j);
+    const float2 a = __ldg(p), b = __ldg(p + 1), e = __ldg(p + 2);
+    const float pt[6] = {a.x, a.y, b.x, b.y, e.x, e.y};
+    to_camera32(c.v, pt, out);
+  }
+  __device__ __forceinline__ static const float* rot(const Cam& c) { return c.v; }
+};
+
+// --------------------------------------------------------------------------- linearisation
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_lin_cam(DevProblem d, T delta) {
+  if (!d.lm->need_lin) return;
+  __shared__ T red[(NT / 32) * 27];
+  const int i = blockIdx.x;
+  const int k0 = d.cam_ptr[i], k1 = d.cam_ptr[i + 1];
+  const bool fixed = d.fixed[i] != 0;
+  const View<T> view(d, false);
+  typename View<T>::Cam cam;
+  view.cam(i, cam);
+  T acc[27];
+#pragma unroll
+  for (int a = 0; a < 27; ++a) acc[a] = T(0);
+  const T* uv = (const T*)d.oc_uv;
+  T* Wout = (T*)d.W;
+  for (int k = k0 + threadIdx.x; k < k1; k += NT) {
+    const int j = d.oc_pt[k];
+    T u, v;
+    load_uv<T>(uv, k, u, v);
+    T xc[3];
+    view.xc(cam, j, xc);
+    T r0, r1;
+    const bool valid = residual<T>(xc, u, v, d.K, r0, r1);
+    T Wk[18];
+#pragma unroll
+    for (int a = 0; a < 18; ++a) Wk[a] = T(0);
+    if (valid && !fixed) {
+      const T s = fma_rn(r0, r0, mul_rn(r1, r1));
+      const T w = huber_weight<T>(s, delta);
+      T Jc[2][6], Jp[2][3];
+      jacobians<T>(xc, View<T>::rot(cam), d.K, Jc, Jp);
+      int u_idx = 0;
+#pragma unroll
+      for (int a = 0; a < 6; ++a) {
+        const T wa0 = w * Jc[0][a], wa1 = w * Jc[1][a];
+#pragma unroll
+        for (int bb = a; bb < 6; ++bb) {
+          acc[u_idx] += wa0 * Jc[0][bb] + wa1 * Jc[1][bb];
+          ++u_idx;
+        }
+        acc[21 + a] += wa0 * r0 + wa1 * r1;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Wk[3 * a + c] = wa0 * Jp[0][c] + wa1 * Jp[1][c];
+      }
+    }
+    store_w<T>(Wout, k, Wk);
+  }
+  block_sum<T, 27>(acc, red);
+  if (threadIdx.x < 36) {
+    // unpack the upper triangle into the full symmetric 6x6
+    const int a = threadIdx.x / 6, bb = threadIdx.x % 6;
+    const int lo = a < bb ? a : bb, hi = a < bb ? bb : a;
+    const int idx = lo * 6 - (lo * (lo - 1)) / 2 + (hi - lo);
+    ((T*)d.U)[36 * i + threadIdx.x] = red[idx];
+  } else if (threadIdx.x < 42) {
+    ((T*)d.gc)[6 * i + threadIdx.x - 36] = red[21 + threadIdx.x - 36];
+  }
+}
+
+template <typename T>
+__global__ void k_lin_pt(DevProblem d, T delta) {
+  if (!d.lm->need_lin) return;
+  const T* uv = (const T*)d.po_uv;
+  const View<T> view(d, false);
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.P; j += gridDim.x * blockDim.x) {
+    T V[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    T g[3] = {T(0), T(0), T(0)};
+    for (int q = d.pt_ptr[j]; q < d.pt_ptr[j + 1]; ++q) {
+      const int c = d.po_cam[q];
+      T u, v;
+      load_uv<T>(uv, q, u, v);
+      typename View<T>::Cam cam;
+      view.cam(c, cam);
+      T xc[3];
+      view.xc(cam, j, xc);
+      T r0, r1;
+      if (!residual<T>(xc, u, v, d.K, r0, r1)) continue;
+      const T s = fma_rn(r0, r0, mul_rn(r1, r1));
+      const T w = huber_weight<T>(s, delta);
+      T Jc[2][6], Jp[2][3];
+      jacobians<T>(xc, View<T>::rot(cam), d.K, Jc, Jp);
+      const T a0 = w * Jp[0][0], a1 = w * Jp[0][1], a2 = w * Jp[0][2];
+      const T b0 = w * Jp[1][0], b1 = w * Jp[1][1], b2 = w * Jp[1][2];
+      V[0] += a0 * Jp[0][0] + b0 * Jp[1][0];
+      V[1] += a0 * Jp[0][1] + b0 * Jp[1][1];
+      V[2] += a0 * Jp[0][2] + b0 * Jp[1][2];
+      V[3] += a1 * Jp[0][1] + b1 * Jp[1][1];
+      V[4] += a1 * Jp[0][2] + b1 * Jp[1][2];
+      V[5] += a2 * Jp[0][2] + b2 * Jp[1][2];
+      g[0] += a0 * r0 + b0 * r1;
+      g[1] += a1 * r0 + b1 * r1;
+      g[2] += a2 * r0 + b2 * r1;
+    }
+    T* Vo = (T*)d.V + 6 * (int64_t)j;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) Vo[a] = V[a];
+    T* go = (T*)d.gp + 3 * (int64_t)j;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) go[a] = g[a];
+  }
+}
+
+template <typename T>
+__global__ void k_damp_pt(DevProblem d) {
+  const double mu = d.lm->mu;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.P; j += gridDim.x * blockDim.x) {
+    const T* Vi = (const T*)d.V + 6 * (int64_t)j;
+    double m[6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) m[a] = (double)Vi[a];
+    m[0] += mu * fmax(m[0], kDiagMin);
+    m[3] += mu * fmax(m[3], kDiagMin);
+    m[5] += mu * fmax(m[5], kDiagMin);
+    double inv[6];
+    sym3_inverse(m, inv);
+    double* out = d.Vinv + 6 * (int64_t)j;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) out[a] = inv[a];
+    const T* g = (const T*)d.gp + 3 * (int64_t)j;
+    const double g0 = g[0], g1 = g[1], g2 = g[2];
+    T* e = (T*)d.e + 3 * (int64_t)j;
+    e[0] = (T)(inv[0] * g0 + inv[1] * g1 + inv[2] * g2);
+    e[1] = (T)(inv[1] * g0 + inv[3] * g1 + inv[4] * g2);
+    e[2] = (T)(inv[2] * g0 + inv[4] * g1 + inv[5] * g2);
+  }
+}
+
+// --------------------------------------------------------------------------- Schur complement
+
+// Shared-memory layout of k_schur: acc [colcap][36] T | Y [kSchurChunk][18] T.
+template <typename T>
+__host__ __device__ inline size_t schur_smem_bytes(int colcap) {
+  return (size_t)colcap * 36 * sizeof(T) + (size_t)kSchurChunk * 18 * sizeof(T) + 64;
+}
+
+// One CTA per camera row i1.  For each chunk of the row's observations:
+// threads compute Y_k1 = W_k1 V*_j^-1 into shared memory; then each warp
+// takes whole segments of the pair list (all pairs of the chunk that land in
+// one output block S_i1,i2).  Each lane takes every 32nd pair of the segment
+// and accumulates the full 6x6 product Y_k1 W_k2^T in registers; a fixed
+// xor-tree warp reduction then gives the block sum.  A segment has one owner
+// per chunk, so the block accumulators need no atomics and the summation
+// order is fixed (bit-reproducible).
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_schur(DevProblem d, int colcap) {
+  static_assert(NT == kSchurChunk, "one thread per observation of a chunk");
+  constexpr int WS = WStride<T>::v;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double bred[(NT / 32) * 6];
+  const int i = blockIdx.x;
+  const int rb = d.s_rowptr[i];
+  const int nnz = d.s_rowptr[i + 1] - rb;
+  T* acc = reinterpret_cast<T*>(smem);
+  T* Ys = acc + (size_t)colcap * 36;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+  const double mu = d.lm->mu;
+  const bool fixed_i = d.fixed[i] != 0;
+  const int kb = d.cam_ptr[i], ke = d.cam_ptr[i + 1];
+  const int ch0 = d.chunk_ptr[i], ch1 = d.chunk_ptr[i + 1];
+  const T* Wg = (const T*)d.W;
+  const T* eg = (const T*)d.e;
+  double bacc[6] = {0, 0, 0, 0, 0, 0};
+  T* Sg = (T*)d.S;
+
+  for (int cb = 0; cb < nnz; cb += colcap) {
+    const int ncol = min(colcap, nnz - cb);
+    for (int e = threadIdx.x; e < ncol * 36; e += NT) acc[e] = T(0);
+    __syncthreads();
+    if (!fixed_i) {
+      for (int ch = ch0; ch < ch1; ++ch) {
+        const int c0 = kb + (ch - ch0) * kSchurChunk;
+        const int n = min(kSchurChunk, ke - c0);
+        if ((int)threadIdx.x < n) {
+          const int k1 = c0 + threadIdx.x;
+          const int j = d.oc_pt[k1];
+          T Wk[18];
+          load_w<T>(Wg, k1, Wk);
+          const double* vi = d.Vinv + 6 * (int64_t)j;
+          const T v00 = (T)vi[0], v01 = (T)vi[1], v02 = (T)vi[2], v11 = (T)vi[3], v12 = (T)vi[4],
+                  v22 = (T)vi[5];
+          T* Y = Ys + 18 * threadIdx.x;
+#pragma unroll
+          for (int a = 0; a < 6; ++a) {
+            const T w0 = Wk[3 * a], w1 = Wk[3 * a + 1], w2 = Wk[3 * a + 2];
+            Y[3 * a] = w0 * v00 + w1 * v01 + w2 * v02;
+            Y[3 * a + 1] = w0 * v01 + w1 * v11 + w2 * v12;
+            Y[3 * a + 2] = w0 * v02 + w1 * v12 + w2 * v22;
+          }
+          if (cb == 0) {
+            const T e0 = eg[3 * (int64_t)j], e1v = eg[3 * (int64_t)j + 1], e2 = eg[3 * (int64_t)j + 2];
+#pragma unroll
+            for (int a = 0; a < 6; ++a)
+              bacc[a] += (double)(Wk[3 * a] * e0 + Wk[3 * a + 1] * e1v + Wk[3 * a + 2] * e2);
+          }
+        }
+        __syncthreads();
+        const int sg1 = d.chunk_seg[ch + 1];
+        for (int sg = d.chunk_seg[ch] + warp; sg < sg1; sg += NT / 32) {
+          const int slot = d.seg_slot[sg];
+          if (slot < cb || slot >= cb + ncol) continue;
+          const int pb = d.seg_begin[sg], pe = d.seg_begin[sg + 1];
+          T sum[36];
+#pragma unroll
+          for (int e = 0; e < 36; ++e) sum[e] = T(0);
+          for (int p = pb + lane; p < pe; p += 32) {
+            const int t = d.pair_t[p];
+            T W2[18];
+            load_w<T>(Wg, d.pair_k2[p], W2);
+            const T* Y = Ys + 18 * t;
+#pragma unroll
+            for (int a = 0; a < 6; ++a) {
+              const T y0 = Y[3 * a], y1 = Y[3 * a + 1], y2 = Y[3 * a + 2];
+#pragma unroll
+              for (int bb = 0; bb < 6; ++bb)
+                sum[6 * a + bb] += y0 * W2[3 * bb] + y1 * W2[3 * bb + 1] + y2 * W2[3 * bb + 2];
+            }
+          }
+#pragma unroll
+          for (int e = 0; e < 36; ++e) sum[e] = warp_sum(sum[e]);
+          T* A = acc + 36 * (slot - cb);
+          // every lane holds the totals; lane e writes element e (and 32 + e)
+          T mine = sum[0], extra = sum[32];
+#pragma unroll
+          for (int e = 1; e < 32; ++e)
+            if (lane == e) mine = sum[e];
+#pragma unroll
+          for (int e = 33; e < 36; ++e)
+            if (lane == e - 32) extra = sum[e];
+          A[lane] += mine;
+          if (lane < 4) A[32 + lane] += extra;
+        }
+        __syncthreads();
+      }
+    }
+    // write this column chunk of the row
+    const T* U = (const T*)d.U + 36 * (int64_t)i;
+    for (int e = threadIdx.x; e < ncol * 36; e += NT) {
+      const int s = e / 36, el = e % 36;
+      const int a = el / 6, bb = el % 6;
+      const int col = d.s_col[rb + cb + s];
+      T val;
+      if (fixed_i) {
+        val = (col == i && a == bb) ? T(1) : T(0);
+      } else {
+        val = -acc[e];
+        if (col == i) {
+          T u = U[el];
+          if (a == bb) u = (T)((double)u + mu * fmax((double)u, kDiagMin));
+          val += u;
+        }
+      }
+      Sg[36 * (int64_t)(rb + cb + s) + el] = val;
+    }
+    __syncthreads();
+  }
+  // b_i = -g_c,i + sum W e
+  block_sum<double, 6>(bacc, bred);
+  if (threadIdx.x < 6) {
+    const double gci = (double)((const T*)d.gc)[6 * i + threadIdx.x];
+    const double bi = fixed_i ? 0.0 : (-gci + bred[threadIdx.x]);
+    ((T*)d.b)[6 * i + threadIdx.x] = (T)bi;
+    if (d.b64) d.b64[6 * i + threadIdx.x] = bi;
+  }
+  // block-Jacobi preconditioner from the diagonal block (re-read from global)
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence_block();
+    const T* Sd = Sg + 36 * (int64_t)d.s_diag[i];
+    T blk[36], inv[36];
+    for (int a = 0; a < 36; ++a) blk[a] = Sd[a];
+    spd6_inverse<T>(blk, inv);
+    T* M = (T*)d.Minv + 36 * (int64_t)i;
+    for (int a = 0; a < 36; ++a) M[a] = inv[a];
+  }
+}
+
+// --------------------------------------------------------------------------- back-substitution
+
+template <typename T>
+__global__ void k_backsub(DevProblem d) {
+  __shared__ double red[32];
+  const double mu = d.lm->mu;
+  const T* Wg = (const T*)d.W;
+  const T* dc = (const T*)d.dc;
+  double part = 0.0;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.P; j += gridDim.x * blockDim.x) {
+    const T* gp = (const T*)d.gp + 3 * (int64_t)j;
+    T rhs0 = -gp[0], rhs1 = -gp[1], rhs2 = -gp[2];
+    for (int q = d.pt_ptr[j]; q < d.pt_ptr[j + 1]; ++q) {
+      const int c = d.po_cam[q];
+      if (d.fixed[c]) continue;
+      T Wk[18];
+      load_w<T>(Wg, d.po_k[q], Wk);
+      const T* x = dc + 6 * c;
+#pragma unroll
+      for (int a = 0; a < 6; ++a) {
+        const T xa = x[a];
+        rhs0 -= Wk[3 * a] * xa;
+        rhs1 -= Wk[3 * a + 1] * xa;
+        rhs2 -= Wk[3 * a + 2] * xa;
+      }
+    }
+    const double* vi = d.Vinv + 6 * (int64_t)j;
+    const double r0 = rhs0, r1 = rhs1, r2 = rhs2;
+    const double p0 = vi[0] * r0 + vi[1] * r1 + vi[2] * r2;
+    const double p1 = vi[1] * r0 + vi[3] * r1 + vi[4] * r2;
+    const double p2 = vi[2] * r0 + vi[4] * r1 + vi[5] * r2;
+    T* dp = (T*)d.dp + 3 * (int64_t)j;
+    dp[0] = (T)p0;
+    dp[1] = (T)p1;
+    dp[2] = (T)p2;
+    const double n0 = d.X[3 * j] + p0, n1 = d.X[3 * j + 1] + p1, n2 = d.X[3 * j + 2] + p2;
+    d.X2[3 * j] = n0;
+    d.X2[3 * j + 1] = n1;
+    d.X2[3 * j + 2] = n2;
+    if (d.X32b) write_pt32(n0, n1, n2, d.X32b + kPt32 * (int64_t)j);
+    // model decrease, point part: h (mu D h - g)
+    const T* V = (const T*)d.V + 6 * (int64_t)j;
+    const double D0 = fmax((double)V[0], kDiagMin), D1 = fmax((double)V[3], kDiagMin),
+                 D2 = fmax((double)V[5], kDiagMin);
+    part += p0 * (mu * D0 * p0 - (double)gp[0]) + p1 * (mu * D1 * p1 - (double)gp[1]) +
+            p2 * (mu * D2 * p2 - (double)gp[2]);
+  }
+  part = warp_sum(part);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    d.part[kPartDl + blockIdx.x] = s;
+  }
+}
+
+template <typename T>
+__global__ void k_retract(DevProblem d) {
+  __shared__ double red[32];
+  const double mu = d.lm->mu;
+  double part = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.C; i += gridDim.x * blockDim.x) {
+    const T* x = (const T*)d.dc + 6 * i;
+    double xi[6];
+    const bool fixed = d.fixed[i] != 0;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) xi[a] = fixed ? 0.0 : (double)x[a];
+    double R2[9], t2[3], C2[3];
+    se3_left_retract(xi, d.R + 9 * i, d.t + 3 * i, R2, t2);
+    camera_centre(R2, t2, C2);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) d.R2[9 * i + a] = R2[a];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      d.t2[3 * i + a] = t2[a];
+      d.Cc2[3 * i + a] = C2[a];
+    }
+    if (d.cam32b) write_cam32(R2, C2, d.cam32b + kCam32 * i);
+    if (!fixed) {
+      const T* U = (const T*)d.U + 36 * i;
+      const T* g = (const T*)d.gc + 6 * i;
+#pragma unroll
+      for (int a = 0; a < 6; ++a) {
+        const double D = fmax((double)U[7 * a], kDiagMin);
+        part += xi[a] * (mu * D * xi[a] - (double)g[a]);
+      }
+    }
+  }
+  part = warp_sum(part);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    d.part[kPartDl + kDlParts / 2 + blockIdx.x] = s;
+  }
+}
+
+// --------------------------------------------------------------------------- cost
+
+// mode 0: partial sums of 1/2 rho(s) at the current or trial state into
+// part[kPartCost + b]; mode 1: partial sums of s and of the valid count into
+// part[kPartCost + 2b, +1].  Sums are FP64.
+template <typename T>
+__global__ void k_cost(DevProblem d, int trial, T delta, int mode) {
+  __shared__ double red[64];
+  const T* uv = (const T*)d.oc_uv;
+  const View<T> view(d, trial != 0);
+  double acc = 0.0, nv = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < d.N;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int c = d.oc_cam[k], j = d.oc_pt[k];
+    T u, v;
+    load_uv<T>(uv, k, u, v);
+    typename View<T>::Cam cam;
+    view.cam(c, cam);
+    T xc[3];
+    view.xc(cam, j, xc);
+    T r0, r1;
+    if (!residual<T>(xc, u, v, d.K, r0, r1)) continue;
+    const T s = fma_rn(r0, r0, mul_rn(r1, r1));
+    if (mode == 0) {
+      acc += 0.5 * (double)huber_rho<T>(s, delta);
+    } else {
+      acc += (double)s;
+      nv += 1.0;
+    }
+  }
+  acc = warp_sum(acc);
+  nv = warp_sum(nv);
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = acc;
+    red[32 + (threadIdx.x >> 5)] = nv;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0, n = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      s += red[w];
+      n += red[32 + w];
+    }
+    if (mode == 0) {
+      d.part[kPartCost + blockIdx.x] = s;
+    } else {
+      d.part[kPartCost + 2 * blockIdx.x] = s;
+      d.part[kPartCost + 2 * blockIdx.x + 1] = n;
+    }
+  }
+}
+
+// --------------------------------------------------------------------------- LM control
+
+// Deterministic block-wide sum of p[off + i * stride], i < n (fixed
+// assignment of terms to threads and a fixed reduction tree); every thread
+// receives the total.
+__device__ double block_strided_sum(const double* __restrict__ p, int n, int stride, int off) {
+  __shared__ double red[32];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a += p[off + (int64_t)i * stride];
+  a = warp_sum(a);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  double tot = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+  __syncthreads();
+  return tot;
+}
+
+__global__ void k_lm_init(DevProblem d, int ncost, double mu0, int iters) {
+  const double F = block_strided_sum(d.part, ncost, 1, kPartCost);
+  if (threadIdx.x != 0) return;
+  LmScalars* lm = d.lm;
+  lm->F = F;
+  if (lm->fresh) {  // a new problem or state: restart the damping
+    lm->mu = mu0;
+    lm->nu = 2.0;
+    lm->fresh = 0;
+  }
+  lm->need_lin = 1;
+  lm->step_ok = 1;
+  lm->iter = 0;
+  lm->n_accepted = 0;
+  lm->pcg_iters = 0;
+  lm->pcg_rel = 0.0;
+  lm->error = isfinite(F) ? 0 : kErrNonFinite;
+  lm->n_iters_max = iters;
+  d.rep.cost[0] = F;
+}
+
+__global__ void k_gain(DevProblem d, int ncost, int ndl_pt, int ndl_cam) {
+  const double Fn = block_strided_sum(d.part, ncost, 1, kPartCost);
+  const double hp = block_strided_sum(d.part, ndl_pt, 1, kPartDl);
+  const double hc = block_strided_sum(d.part, ndl_cam, 1, kPartDl + kDlParts / 2);
+  if (threadIdx.x != 0) return;
+  LmScalars* lm = d.lm;
+  const double dL = 0.5 * (hp + hc);
+  const int it = lm->iter;
+  const bool ok = lm->step_ok && isfinite(Fn) && isfinite(dL) && dL > 0.0;
+  const double gain = ok ? (lm->F - Fn) / dL : -INFINITY;
+  d.rep.mu[it] = lm->mu;
+  d.rep.pcg_iters[it] = lm->pcg_iters;
+  d.rep.pcg_rel[it] = lm->pcg_rel;
+  d.rep.gain[it] = gain;
+  lm->F_new = Fn;
+  lm->dL = dL;
+  lm->gain = gain;
+  if (ok && gain > 0.0) {
+    lm->F = Fn;
+    const double t = 2.0 * gain - 1.0;
+    lm->mu = lm->mu * fmax(1.0 / 3.0, 1.0 - t * t * t);
+    lm->nu = 2.0;
+    lm->need_lin = 1;
+    lm->n_accepted += 1;
+    d.rep.accepted[it] = 1;
+  } else {
+    lm->mu = lm->mu * lm->nu;
+    lm->nu = 2.0 * lm->nu;
+    lm->need_lin = 0;
+    d.rep.accepted[it] = 0;
+  }
+  d.rep.cost[it + 1] = lm->F;
+  lm->iter = it + 1;
+}
+
+__global__ void k_commit(DevProblem d) {
+  if (!d.lm->need_lin) return;  // set by k_gain exactly when the step was accepted
+  const int n = d.C > d.P ? d.C : d.P;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (i < d.C) {
+#pragma unroll
+      for (int a = 0; a < 9; ++a) d.R[9 * i + a] = d.R2[9 * i + a];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        d.t[3 * i + a] = d.t2[3 * i + a];
+        d.Cc[3 * i + a] = d.Cc2[3 * i + a];
+      }
+    }
+    if (i < d.P) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) d.X[3 * i + a] = d.X2[3 * i + a];
+      if (d.X32)
+#pragma unroll
+        for (int a = 0; a < kPt32; ++a) d.X32[kPt32 * i + a] = d.X32b[kPt32 * i + a];
+    }
+    if (i < d.C && d.cam32)
+#pragma unroll
+      for (int a = 0; a < kCam32; ++a) d.cam32[kCam32 * i + a] = d.cam32b[kCam32 * i + a];
+  }
+}
+
+__global__ void k_rmse_final(DevProblem d, int ncost) {
+  const double s = block_strided_sum(d.part, ncost, 2, kPartCost);
+  const double n = block_strided_sum(d.part, ncost, 2, kPartCost + 1);
+  if (threadIdx.x != 0) return;
+  d.rep.rmse_parts[0] = s;
+  d.rep.rmse_parts[1] = n;
+  if (!isfinite(d.lm->F)) d.lm->error |= kErrNonFinite;
+}
+
+// --------------------------------------------------------------------------- launchers
+
+static unsigned grid_cap(int64_t n, int threads, int cap) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (unsigned)g;
+}
+
+int cost_blocks(const DevProblem& d) { return (int)grid_cap(d.N, 256, kCostParts / 2); }
+int backsub_blocks(const DevProblem& d) { return (int)grid_cap(d.P, 256, kDlParts / 2); }
+int retract_blocks(const DevProblem& d) { return (int)grid_cap(d.C, 128, kDlParts / 2); }
+
+size_t schur_smem(int precision, int colcap) {
+  return precision == BA_FP32 ? schur_smem_bytes<float>(colcap)
+                              : schur_smem_bytes<double>(colcap);
+}
+
+int schur_colcap(int precision, int max_row_nnz, size_t smem_limit) {
+  int cap = max_row_nnz < 1 ? 1 : max_row_nnz;
+  while (cap > 1 && schur_smem(precision, cap) > smem_limit) cap = (cap + 1) / 2;
+  return cap;
+}
+
+const char* const kKernelNames[kKindCount] = {
+    "cost_initial", "lm_init", "lin_cam", "lin_pt", "damp_pt", "schur", "solve", "backsub",
+    "retract", "cost_trial", "gain", "commit", "cost_final", "rmse"};
+
+void mark(const SolveConfig& cfg, int k, cudaStream_t s) {
+  Marks* m = cfg.marks;
+  if (!m) return;
+  m->launches += 1;
+  if (!m->profile) return;
+  if (m->used == m->pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    m->pool.push_back(e);
+  }
+  cudaEvent_t e = m->pool[m->used++];
+  cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);  // an event node when captured
+  m->kind.push_back(k);
+  m->ev.push_back(e);
+}
+
+template <typename T>
+static void lm_iteration_t(const DevProblem& d, const SolveConfig& cfg, cudaStream_t s) {
+  const T delta = (T)cfg.huber_delta;
+  const unsigned gp = grid_cap(d.P, 256, 148 * 8);
+  k_lin_cam<T, 256><<<d.C, 256, 0, s>>>(d, delta);
+  mark(cfg, kKLinCam, s);
+  k_lin_pt<T><<<gp, 256, 0, s>>>(d, delta);
+  mark(cfg, kKLinPt, s);
+  k_damp_pt<T><<<gp, 256, 0, s>>>(d);
+  mark(cfg, kKDampPt, s);
+  const size_t sm = schur_smem_bytes<T>(cfg.schur_colcap);
+  k_schur<T, 256><<<d.C, 256, sm, s>>>(d, cfg.schur_colcap);
+  mark(cfg, kKSchur, s);
+  launch_linear_solve(d, cfg, s);
+  mark(cfg, kKSolve, s);
+  k_backsub<T><<<backsub_blocks(d), 256, 0, s>>>(d);
+  mark(cfg, kKBacksub, s);
+  k_retract<T><<<retract_blocks(d), 128, 0, s>>>(d);
+  mark(cfg, kKRetract, s);
+  k_cost<T><<<cost_blocks(d), 256, 0, s>>>(d, 1, delta, 0);
+  mark(cfg, kKCost, s);
+  k_gain<<<1, 256, 0, s>>>(d, cost_blocks(d), backsub_blocks(d), retract_blocks(d));
+  mark(cfg, kKGain, s);
+  k_commit<<<grid_cap(d.C > d.P ? d.C : d.P, 256, 148 * 8), 256, 0, s>>>(d);
+  mark(cfg, kKCommit, s);
+}
+
+template <typename T>
+static void lm_begin_t(const DevProblem& d, const SolveConfig& cfg, cudaStream_t s) {
+  k_cost<T><<<cost_blocks(d), 256, 0, s>>>(d, 0, (T)cfg.huber_delta, 0);
+  mark(cfg, kKCostBegin, s);
+  k_lm_init<<<1, 256, 0, s>>>(d, cost_blocks(d), cfg.mu0, cfg.iters);
+  mark(cfg, kKLmInit, s);
+}
+
+template <typename T>
+static void lm_end_t(const DevProblem& d, const SolveConfig& cfg, cudaStream_t s) {
+  k_cost<T><<<cost_blocks(d), 256, 0, s>>>(d, 0, (T)cfg.huber_delta, 1);
+  mark(cfg, kKCostEnd, s);
+  k_rmse_final<<<1, 256, 0, s>>>(d, cost_blocks(d));
+  mark(cfg, kKRmse, s);
+}
+
+void set_schur_smem_attr(int precision, size_t bytes) {
+  if (precision == BA_FP32)
+    cudaFuncSetAttribute(k_schur<float, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)bytes);
+  else
+    cudaFuncSetAttribute(k_schur<double, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)bytes);
+}
+
+void launch_lm_begin(const DevProblem& d, const SolveConfig& cfg, cudaStream_t s) {
+  if (d.precision == BA_FP32) lm_begin_t<float>(d, cfg, s);
+  else lm_begin_t<double>(d, cfg, s);
+}
+
+void launch_lm_iteration(const DevProblem& d, const SolveConfig& cfg, cudaStream_t s) {
+  if (d.precision == BA_FP32) lm_iteration_t<float>(d, cfg, s);
+  else lm_iteration_t<double>(d, cfg, s);
+}
+
+void launch_lm_end(const DevProblem& d, const SolveConfig& cfg, cudaStream_t s) {
+  if (d.precision == BA_FP32) lm_end_t<float>(d, cfg, s);
+  else lm_end_t<double>(d, cfg, s);
+}
+
+}  // namespace ba

@@ -1,0 +1,647 @@
+// Linear solvers for the reduced camera system S dc = b.
+//
+// k_pcg:    conjugate gradients (Hestenes & Stiefel 1952) preconditioned by
+//           the inverse 6x6 diagonal blocks of S (block Jacobi; Agarwal et al.
+//           2010), as one persistent cooperative launch.  Each CTA owns a
+//           contiguous range of block rows (held in shared memory when they
+//           fit) and each warp some of those rows; lane e < 6 keeps element e
+//           of its rows of x, r, q and p in registers.  A bounded grid
+//           barrier separates the SpMV phase from the update phase (two
+//           barriers per iteration: the search direction p_k = z_k +
+//           beta p_{k-1} is formed on the fly inside the SpMV from z and
+//           p_{k-1}, double-buffered in global memory).  Dots are accumulated
+//           in FP64 and reduced in a fixed order, so every CTA takes the same
+//           decisions.  Optional FP64 iterative refinement (the inner solve
+//           corrects the FP64 residual b - S x; Carson & Higham 2018) runs as
+//           an outer loop in the same launch.
+// k_dense:  one CTA assembles S densely and solves it by Cholesky (lower,
+//           right-looking) with forward and back substitution; a
+//           non-positive pivot marks the step unusable.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "lm.h"
+
+namespace ba {
+
+// Wall-clock limit of one barrier wait (ns).
+constexpr unsigned long long kBarrierLimitNs = 1000ull * 1000ull * 1000ull;
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned atom_add_relaxed_u32(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.relaxed.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v)
+               : "memory");
+  return old;
+}
+
+__device__ __forceinline__ void st_relaxed_u32(unsigned* p, unsigned v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void fence_acq_rel_gpu() {
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ int ld_err(const int* err) {
+  return *(volatile const int*)err;
+}
+
+// Grid-wide barrier over co-resident CTAs (cooperative launch).  bar[0]
+// counts arrivals, bar[1] is the generation.  The CTA's writes are released
+// by __syncthreads + fence.acq_rel before the arrival and acquired by the
+// acquire-load that sees the new generation.  A wait that exceeds
+// kBarrierLimitNs (or sees another CTA's error) sets kErrBarrierTimeout in
+// *err and returns; callers stop at their next check of *err.
+__device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned nblocks, int* err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned g = ld_acquire_u32(bar + 1);
+    fence_acq_rel_gpu();
+    const unsigned prev = atom_add_relaxed_u32(bar, 1u);
+    if (prev == nblocks - 1) {
+      st_relaxed_u32(bar, 0u);
+      fence_acq_rel_gpu();
+      atom_add_relaxed_u32(bar + 1, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (ld_acquire_u32(bar + 1) == g) {
+        if (ld_err(err) != 0) break;  // another CTA already gave up
+        if (global_ns() - t0 > kBarrierLimitNs) {
+          atomicOr(err, kErrBarrierTimeout);
+          break;
+        }
+        __nanosleep(20);
+      }
+      fence_acq_rel_gpu();
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ T ldcg(const T* p) {
+  return __ldcg(p);
+}
+
+// Shared-memory stride of a 6x6 block of S: 37 keeps the 36 elements of the
+// blocks read by 32 lanes (one block per lane) on distinct banks.
+constexpr int kSPad = 37;
+
+// The block rows [r0, r1) of S owned by one CTA, read from shared memory
+// (local = true: block and row indices relative to the CTA's first row) or
+// straight from global memory.
+template <typename T>
+struct RowSet {
+  const T* S;
+  const int32_t* col;
+  const int32_t* rowptr;
+  const T* Minv;
+  int sstride;
+  int r0, r1;
+  bool local;
+  __device__ __forceinline__ int rb(int i) const { return local ? rowptr[i - r0] : rowptr[i]; }
+  __device__ __forceinline__ int re(int i) const {
+    return local ? rowptr[i - r0 + 1] : rowptr[i + 1];
+  }
+  __device__ __forceinline__ const T* blk(int b) const { return S + (int64_t)b * sstride; }
+  __device__ __forceinline__ const T* minv(int i) const {
+    return Minv + 36 * (int64_t)(local ? i - r0 : i);
+  }
+};
+
+// Warp computes out = S_i. v for block row i, v(c) supplied by vget; the
+// result is in every lane.
+template <typename T, typename Get>
+__device__ __forceinline__ void row_spmv(const RowSet<T>& rs, int i, Get vget, T out[6]) {
+  const int lane = threadIdx.x & 31;
+  T acc[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+  const int be = rs.re(i);
+  for (int b = rs.rb(i) + lane; b < be; b += 32) {
+    const int c = rs.col[b];
+    T v[6];
+#pragma unroll
+    for (int e = 0; e < 6; ++e) v[e] = vget(6 * c + e);
+    const T* B = rs.blk(b);
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+      T s = acc[a];
+#pragma unroll
+      for (int e = 0; e < 6; ++e) s += B[6 * a + e] * v[e];
+      acc[a] = s;
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 6; ++a) out[a] = warp_sum(acc[a]);
+}
+
+// Element `lane` (< 6) of a 6-vector held by every lane.
+template <typename T>
+__device__ __forceinline__ T pick6(const T v[6], int lane) {
+  T r = v[0];
+#pragma unroll
+  for (int a = 1; a < 6; ++a)
+    if (lane == a) r = v[a];
+  return r;
+}
+
+// Sum of per-warp FP64 values over the CTA into slot[blockIdx.x * stride + k].
+template <int NT, int NV>
+__device__ __forceinline__ void cta_partials(double (&v)[NV], double* red, double* slot,
+                                             int stride) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) red[warp * NV + k] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0.0;
+    for (int w = 0; w < NT / 32; ++w) s += red[w * NV + threadIdx.x];
+    slot[blockIdx.x * stride + threadIdx.x] = s;
+  }
+}
+
+// Every CTA sums the partials of all CTAs with the same operations in the
+// same order (so all CTAs hold bit-identical totals): warp 0 reads them
+// lane-strided and reduces, the result is broadcast through shared memory.
+template <int NV>
+__device__ __forceinline__ void all_partials(const double* slot, int stride, int nblocks,
+                                             double (&out)[NV]) {
+  __shared__ double sh[NV];
+  if (threadIdx.x < 32) {
+    double acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += 32)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) acc[k] += __ldcg(slot + b * stride + k);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = warp_sum(acc[k]);
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) sh[k] = acc[k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) out[k] = sh[k];
+  __syncthreads();
+}
+
+// One PCG solve of S x = rhs with x0 = 0.  Warp w of a CTA owns rows
+// r0 + w + m NW (m < RW); lane e < 6 holds element e of those rows.
+// Returns iterations; writes the final relative residual to *rel.  Called by
+// every thread of every CTA.
+template <typename T, int NT, int RW>
+__device__ int pcg_solve(const DevProblem& d, const RowSet<T>& rs, const T* __restrict__ rhs,
+                         T* __restrict__ x, double tol, int max_iters, double* rel, int* err) {
+  __shared__ double red[(NT / 32) * 2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = NT / 32;
+  const unsigned nb = gridDim.x;
+  T* z = (T*)d.z;
+  T* pb[2] = {(T*)d.p0, (T*)d.p1};
+  double* partA = d.part + kPartPcg;         // [nb]
+  double* partB = d.part + kPartPcg + 1024;  // [nb][2]
+  const int el = lane < 6 ? lane : 0;
+
+  T xr[RW], rr_[RW], qr[RW], pr[RW];
+  // init: x = 0, r = rhs, z = M r, p_{-1} = 0
+  double loc[2] = {0.0, 0.0};
+#pragma unroll
+  for (int m = 0; m < RW; ++m) {
+    const int i = rs.r0 + warp + m * NW;
+    xr[m] = rr_[m] = qr[m] = pr[m] = T(0);
+    if (i >= rs.r1) continue;
+    const T ri = lane < 6 ? rhs[6 * i + el] : T(0);
+    rr_[m] = ri;
+    if (lane < 6) pb[1][6 * i + el] = T(0);
+    const T* M = rs.minv(i);
+    T zi = T(0);
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      const T rf = __shfl_sync(0xffffffffu, ri, f);
+      zi += M[6 * el + f] * rf;
+    }
+    if (lane < 6) {
+      z[6 * i + el] = zi;
+      loc[0] += (double)ri * (double)zi;
+      loc[1] += (double)ri * (double)ri;
+    }
+  }
+  cta_partials<NT, 2>(loc, red, partB, 2);
+  grid_barrier(d.barrier, nb, err);
+  double tot[2];
+  all_partials<2>(partB, 2, nb, tot);
+  double rz = tot[0], rr = tot[1];
+  const double bnorm = sqrt(rr);
+  double beta = 0.0;
+  int k = 0;
+  while (k < max_iters && sqrt(rr) > tol * bnorm && !ld_err(err)) {
+    const int cur = k & 1;
+    T* pn = pb[cur];
+    const T* po = pb[cur ^ 1];
+    const T bt = (T)beta;
+    // phase A: p_k = z + beta p_{k-1}; q = S p_k; partial p.q
+    double pq_loc[1] = {0.0};
+#pragma unroll
+    for (int m = 0; m < RW; ++m) {
+      const int i = rs.r0 + warp + m * NW;
+      if (i >= rs.r1) continue;
+      const T zo = ldcg(z + 6 * i + el), poo = ldcg(po + 6 * i + el);
+      T qi[6];
+      row_spmv<T>(rs, i, [&](int idx) { return ldcg(z + idx) + bt * ldcg(po + idx); }, qi);
+      const T pi = zo + bt * poo;
+      pr[m] = pi;
+      qr[m] = pick6(qi, el);
+      if (lane < 6) {
+        pn[6 * i + el] = pi;
+        pq_loc[0] += (double)pi * (double)qr[m];
+      }
+    }
+    cta_partials<NT, 1>(pq_loc, red, partA, 1);
+    grid_barrier(d.barrier, nb, err);
+    double pqt[1];
+    all_partials<1>(partA, 1, nb, pqt);
+    const double pq = pqt[0];
+    if (!(pq > 0.0)) break;  // S not numerically positive definite along p
+    const double alpha = rz / pq;
+    const T al = (T)alpha;
+    // phase B: x += alpha p; r -= alpha q; z = M r; partial r.z, r.r
+    double l2[2] = {0.0, 0.0};
+#pragma unroll
+    for (int m = 0; m < RW; ++m) {
+      const int i = rs.r0 + warp + m * NW;
+      if (i >= rs.r1) continue;
+      xr[m] = xr[m] + al * pr[m];
+      rr_[m] = rr_[m] - al * qr[m];
+      const T ri = lane < 6 ? rr_[m] : T(0);
+      const T* M = rs.minv(i);
+      T zi = T(0);
+#pragma unroll
+      for (int f = 0; f < 6; ++f) {
+        const T rf = __shfl_sync(0xffffffffu, ri, f);
+        zi += M[6 * el + f] * rf;
+      }
+      if (lane < 6) {
+        z[6 * i + el] = zi;
+        l2[0] += (double)ri * (double)zi;
+        l2[1] += (double)ri * (double)ri;
+      }
+    }
+    cta_partials<NT, 2>(l2, red, partB, 2);
+    grid_barrier(d.barrier, nb, err);
+    all_partials<2>(partB, 2, nb, tot);
+    ++k;
+    beta = tot[0] / rz;
+    rz = tot[0];
+    rr = tot[1];
+  }
+#pragma unroll
+  for (int m = 0; m < RW; ++m) {
+    const int i = rs.r0 + warp + m * NW;
+    if (i < rs.r1 && lane < 6) x[6 * i + el] = xr[m];
+  }
+  *rel = bnorm > 0.0 ? sqrt(rr) / bnorm : 0.0;
+  return k;
+}
+
+// Shared-memory layout of the SMEM variant: blocks [maxnnz][kSPad] T |
+// Minv [R][36] T | cols [maxnnz] int32 | rowptr [R + 1] int32.
+template <typename T>
+__host__ __device__ inline size_t pcg_smem_bytes(int maxnnz, int R) {
+  size_t o = (size_t)maxnnz * kSPad * sizeof(T);
+  o = (o + 15) & ~size_t(15);
+  o += (size_t)R * 36 * sizeof(T);
+  o += (size_t)maxnnz * sizeof(int32_t);
+  o += (size_t)(R + 1) * sizeof(int32_t);
+  return o + 16;
+}
+
+template <typename T, int NT, bool SMEM, int RW>
+__global__ void __launch_bounds__(NT) k_pcg(DevProblem d, double tol, int max_iters, int refine,
+                                            int refine_max, double refine_tol, int R, int maxnnz) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  int* err = &d.lm->error;
+  const unsigned nb = gridDim.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = NT / 32;
+  const int r0 = min(d.C, (int)blockIdx.x * R);
+  const int r1 = min(d.C, r0 + R);
+  RowSet<T> rs;
+  rs.r0 = r0;
+  rs.r1 = r1;
+  if (SMEM) {
+    T* sS = reinterpret_cast<T*>(smem);
+    size_t o = ((size_t)maxnnz * kSPad * sizeof(T) + 15) & ~size_t(15);
+    T* sM = reinterpret_cast<T*>(smem + o);
+    o += (size_t)R * 36 * sizeof(T);
+    int32_t* scol = reinterpret_cast<int32_t*>(smem + o);
+    o += (size_t)maxnnz * sizeof(int32_t);
+    int32_t* srow = reinterpret_cast<int32_t*>(smem + o);
+    const int nb0 = d.s_rowptr[r0];
+    const int n = d.s_rowptr[r1] - nb0;
+    const T* Sg = (const T*)d.S + 36 * (int64_t)nb0;
+    for (int e = threadIdx.x; e < n * 36; e += NT) sS[(e / 36) * kSPad + e % 36] = Sg[e];
+    for (int e = threadIdx.x; e < n; e += NT) scol[e] = d.s_col[nb0 + e];
+    for (int e = threadIdx.x; e <= r1 - r0; e += NT) srow[e] = d.s_rowptr[r0 + e] - nb0;
+    const T* Mg = (const T*)d.Minv + 36 * (int64_t)r0;
+    for (int e = threadIdx.x; e < (r1 - r0) * 36; e += NT) sM[e] = Mg[e];
+    __syncthreads();
+    rs.S = sS;
+    rs.col = scol;
+    rs.rowptr = srow;
+    rs.Minv = sM;
+    rs.sstride = kSPad;
+    rs.local = true;
+  } else {
+    rs.S = (const T*)d.S;
+    rs.col = d.s_col;
+    rs.rowptr = d.s_rowptr;
+    rs.Minv = (const T*)d.Minv;
+    rs.sstride = 36;
+    rs.local = false;
+  }
+  double rel = 0.0;
+  int iters = 0;
+  if (!refine) {
+    iters = pcg_solve<T, NT, RW>(d, rs, (const T*)d.b, (T*)d.dc, tol, max_iters, &rel, err);
+  } else {
+    // FP64 iterative refinement around the T-precision PCG: solve S d = r,
+    // x += d, r = b - S x in FP64 (S as stored, promoted), until
+    // ||r|| <= refine_tol ||b|| or refine_max solves.
+    __shared__ double red[NW];
+    double* partR = d.part + kPartPcg + 3072;
+    double* x64 = d.x64;
+    const double* b64 = d.b64;
+    T* rhs = (T*)d.b;
+    T* dx = (T*)d.dc;
+    double l[1] = {0.0};
+    for (int i = r0 + warp; i < r1; i += NW)
+      if (lane < 6) {
+        const double bi = b64[6 * i + lane];
+        x64[6 * i + lane] = 0.0;
+        rhs[6 * i + lane] = (T)bi;
+        l[0] += bi * bi;
+      }
+    cta_partials<NT, 1>(l, red, partR, 1);
+    grid_barrier(d.barrier, nb, err);
+    double bb[1];
+    all_partials<1>(partR, 1, nb, bb);
+    const double b64n = sqrt(bb[0]);
+    double rres = b64n;
+    for (int o = 0; o < refine_max && rres > refine_tol * b64n && !ld_err(err); ++o) {
+      double rel_in;
+      iters += pcg_solve<T, NT, RW>(d, rs, rhs, dx, tol, max_iters, &rel_in, err);
+      for (int i = r0 + warp; i < r1; i += NW)
+        if (lane < 6) x64[6 * i + lane] += (double)dx[6 * i + lane];
+      grid_barrier(d.barrier, nb, err);
+      double l2[1] = {0.0};
+      for (int i = r0 + warp; i < r1; i += NW) {
+        double acc[6] = {0, 0, 0, 0, 0, 0};
+        const int be = rs.re(i);
+        for (int bI = rs.rb(i) + lane; bI < be; bI += 32) {
+          const int c = rs.col[bI];
+          double v[6];
+#pragma unroll
+          for (int e = 0; e < 6; ++e) v[e] = __ldcg(x64 + 6 * c + e);
+          const T* B = rs.blk(bI);
+#pragma unroll
+          for (int a = 0; a < 6; ++a)
+#pragma unroll
+            for (int e = 0; e < 6; ++e) acc[a] += (double)B[6 * a + e] * v[e];
+        }
+        double sx[6];
+#pragma unroll
+        for (int a = 0; a < 6; ++a) sx[a] = warp_sum(acc[a]);
+        if (lane < 6) {
+          const double ri = b64[6 * i + lane] - pick6(sx, lane);
+          rhs[6 * i + lane] = (T)ri;
+          l2[0] += ri * ri;
+        }
+      }
+      cta_partials<NT, 1>(l2, red, partR, 1);
+      grid_barrier(d.barrier, nb, err);
+      all_partials<1>(partR, 1, nb, bb);
+      rres = sqrt(bb[0]);
+      rel = b64n > 0.0 ? rres / b64n : 0.0;
+    }
+    for (int i = r0 + warp; i < r1; i += NW)
+      if (lane < 6) dx[6 * i + lane] = (T)x64[6 * i + lane];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    d.lm->pcg_iters = iters;
+    d.lm->pcg_rel = rel;
+    d.lm->step_ok = 1;
+  }
+}
+
+// --------------------------------------------------------------------------- dense
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_dense(DevProblem d, int use_smem) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int ok_s;
+  const int n = 6 * d.C;
+  T* A = use_smem ? reinterpret_cast<T*>(smem) : (T*)d.dense;
+  T* y = use_smem ? reinterpret_cast<T*>(smem) + (size_t)n * n : (T*)d.dense + (size_t)n * n;
+  const T* S = (const T*)d.S;
+  for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += NT) A[e] = T(0);
+  if (threadIdx.x == 0) ok_s = 1;
+  __syncthreads();
+  for (int i = 0; i < d.C; ++i) {
+    const int rb = d.s_rowptr[i], re = d.s_rowptr[i + 1];
+    for (int e = threadIdx.x; e < (re - rb) * 36; e += NT) {
+      const int bI = rb + e / 36, el = e % 36;
+      const int c = d.s_col[bI];
+      A[(size_t)(6 * i + el / 6) * n + 6 * c + el % 6] = S[36 * (int64_t)bI + el];
+    }
+  }
+  for (int e = threadIdx.x; e < n; e += NT) y[e] = ((const T*)d.b)[e];
+  __syncthreads();
+  // Cholesky A = L L^T, L in the lower triangle
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      T dj = A[(size_t)j * n + j];
+      if (!(dj > T(0)) || !isfinite((double)dj)) {
+        ok_s = 0;
+        dj = T(1);
+      }
+      A[(size_t)j * n + j] = sqrt(dj);
+    }
+    __syncthreads();
+    const T ljj = A[(size_t)j * n + j];
+    for (int i = j + 1 + threadIdx.x; i < n; i += NT) A[(size_t)i * n + j] /= ljj;
+    __syncthreads();
+    const int m = n - j - 1;
+    for (int64_t idx = threadIdx.x; idx < (int64_t)m * m; idx += NT) {
+      const int i = j + 1 + (int)(idx / m), kk = j + 1 + (int)(idx % m);
+      if (kk <= i) A[(size_t)i * n + kk] -= A[(size_t)i * n + j] * A[(size_t)kk * n + j];
+    }
+    __syncthreads();
+  }
+  // L y' = b
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) y[j] /= A[(size_t)j * n + j];
+    __syncthreads();
+    const T yj = y[j];
+    for (int i = j + 1 + threadIdx.x; i < n; i += NT) y[i] -= A[(size_t)i * n + j] * yj;
+    __syncthreads();
+  }
+  // L^T x = y'
+  for (int j = n - 1; j >= 0; --j) {
+    if (threadIdx.x == 0) y[j] /= A[(size_t)j * n + j];
+    __syncthreads();
+    const T yj = y[j];
+    for (int i = threadIdx.x; i < j; i += NT) y[i] -= A[(size_t)j * n + i] * yj;
+    __syncthreads();
+  }
+  T* x = (T*)d.dc;
+  for (int e = threadIdx.x; e < n; e += NT) x[e] = y[e];
+  if (threadIdx.x == 0) {
+    d.lm->step_ok = ok_s;
+    d.lm->pcg_iters = 0;
+    d.lm->pcg_rel = 0.0;
+  }
+}
+
+// --------------------------------------------------------------------------- launchers
+
+constexpr int kPcgThreads = 256;
+constexpr int kDenseThreads = 1024;
+constexpr int kPcgWarps = kPcgThreads / 32;
+
+size_t dense_smem_bytes(int precision, int n) {
+  const size_t el = precision == BA_FP32 ? sizeof(float) : sizeof(double);
+  return ((size_t)n * n + (size_t)n) * el;
+}
+
+void set_dense_smem_attr(int precision, size_t bytes) {
+  if (precision == BA_FP32)
+    cudaFuncSetAttribute(k_dense<float, kDenseThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)bytes);
+  else
+    cudaFuncSetAttribute(k_dense<double, kDenseThreads>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// Kernel variant for (precision, shared memory, rows per warp).
+template <typename T>
+static const void* pcg_fn(bool smem, int rw) {
+  if (smem) {
+    switch (rw) {
+      case 1: return (const void*)k_pcg<T, kPcgThreads, true, 1>;
+      case 2: return (const void*)k_pcg<T, kPcgThreads, true, 2>;
+      default: return nullptr;
+    }
+  }
+  switch (rw) {
+    case 1: return (const void*)k_pcg<T, kPcgThreads, false, 1>;
+    case 2: return (const void*)k_pcg<T, kPcgThreads, false, 2>;
+    case 4: return (const void*)k_pcg<T, kPcgThreads, false, 4>;
+    case 8: return (const void*)k_pcg<T, kPcgThreads, false, 8>;
+    case 16: return (const void*)k_pcg<T, kPcgThreads, false, 16>;
+    default: return nullptr;
+  }
+}
+
+static const void* pcg_fn_prec(int precision, bool smem, int rw) {
+  return precision == BA_FP32 ? pcg_fn<float>(smem, rw) : pcg_fn<double>(smem, rw);
+}
+
+static int pcg_occupancy(const void* fn, size_t smem) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPcgThreads, smem);
+  return per_sm;
+}
+
+// Choose the cooperative grid and the row split of the PCG kernel: one warp
+// per block row where the grid allows, contiguous rows per CTA, and the CTA's
+// rows of S held in shared memory when they fit.  Returns false if the
+// problem has more rows than the kernel variants cover.
+bool plan_pcg(int precision, int device, const std::vector<int32_t>& rowptr, size_t smem_limit,
+              SolveConfig& cfg) {
+  const int C = (int)rowptr.size() - 1;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  const int per_sm_plain = pcg_occupancy(pcg_fn_prec(precision, false, 1), 0);
+  const int gmax = std::max(1, std::min(per_sm_plain * sms, 1024));
+  int G = std::max(1, std::min(gmax, (C + kPcgWarps - 1) / kPcgWarps));
+  int R = (C + G - 1) / G;
+  G = (C + R - 1) / R;
+  int rw = 1;
+  while (rw * kPcgWarps < R) rw *= 2;
+  if (rw > 16) return false;
+  int maxnnz = 0;
+  for (int b = 0; b < G; ++b) {
+    const int r0 = std::min(C, b * R), r1 = std::min(C, r0 + R);
+    maxnnz = std::max(maxnnz, rowptr[r1] - rowptr[r0]);
+  }
+  const size_t need = precision == BA_FP32 ? pcg_smem_bytes<float>(maxnnz, R)
+                                           : pcg_smem_bytes<double>(maxnnz, R);
+  bool smem = false;
+  const void* fs = pcg_fn_prec(precision, true, rw);
+  if (fs && need <= smem_limit) {
+    cudaFuncSetAttribute(fs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+    smem = pcg_occupancy(fs, need) * sms >= G;
+  }
+  cfg.pcg_blocks = G;
+  cfg.pcg_rows = R;
+  cfg.pcg_rw = rw;
+  cfg.pcg_maxnnz = maxnnz;
+  cfg.pcg_smem = smem ? need : 0;
+  return true;
+}
+
+template <typename T>
+static void linear_solve_t(const DevProblem& d, const SolveConfig& cfg, cudaStream_t s) {
+  if (cfg.solver == BA_SOLVER_DENSE) {
+    k_dense<T, kDenseThreads><<<1, kDenseThreads, cfg.dense_smem, s>>>(d, cfg.dense_smem > 0);
+    return;
+  }
+  cudaMemsetAsync(d.barrier, 0, sizeof(unsigned), s);  // arrival counter only
+  DevProblem dd = d;
+  double tol = cfg.pcg_tol;
+  int mx = cfg.pcg_max;
+  int rf = cfg.refine;
+  int rm = cfg.refine_max;
+  double rt = cfg.refine_tol;
+  int R = cfg.pcg_rows;
+  int mn = cfg.pcg_maxnnz;
+  void* args[] = {&dd, &tol, &mx, &rf, &rm, &rt, &R, &mn};
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(cfg.pcg_blocks);
+  lc.blockDim = dim3(kPcgThreads);
+  lc.dynamicSmemBytes = cfg.pcg_smem;
+  lc.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  lc.attrs = attr;
+  lc.numAttrs = 1;
+  cudaLaunchKernelExC(&lc, pcg_fn<T>(cfg.pcg_smem > 0, cfg.pcg_rw), args);
+}
+
+void launch_linear_solve(const DevProblem& d, const SolveConfig& cfg, cudaStream_t s) {
+  if (d.precision == BA_FP32) linear_solve_t<float>(d, cfg, s);
+  else linear_solve_t<double>(d, cfg, s);
+}
+
+}  // namespace ba

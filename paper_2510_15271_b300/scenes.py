@@ -157,11 +157,20 @@ def _measure(rng, K, R, C, X, obs_cam, obs_pt, sigma, outlier_frac, width, heigh
     n = obs_cam.shape[0]
     inlier = np.ones(n, dtype=bool)
     if outlier_frac > 0:
-        out = rng.random(n) < outlier_frac
-        inlier[out] = False
-        k = int(out.sum())
-        uv[out, 0] = rng.uniform(0.0, width, size=k)
-        uv[out, 1] = rng.uniform(0.0, height, size=k)
+        # A wrong match replaces one measurement of a track that still has at
+        # least three good ones (shorter tracks with a wrong match would not
+        # survive triangulation); tracks are drawn so that outlier_frac of all
+        # observations are outliers.
+        L = np.bincount(obs_pt, minlength=int(obs_pt.max()) + 1)
+        long_tracks = np.nonzero(L >= 4)[0]
+        p = min(1.0, outlier_frac * n / max(long_tracks.size, 1))
+        chosen = long_tracks[rng.random(long_tracks.size) < p]
+        start = np.concatenate([[0], np.cumsum(L)[:-1]])     # obs are grouped by point
+        pick = start[chosen] + (rng.random(chosen.size) * L[chosen]).astype(np.int64)
+        inlier[pick] = False
+        k = pick.size
+        uv[pick, 0] = rng.uniform(0.0, width, size=k)
+        uv[pick, 1] = rng.uniform(0.0, height, size=k)
     return uv, inlier
 
 

@@ -1,0 +1,280 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+FP64 path: per-iteration cost F within 1e-9 relative of the oracle running
+the same algorithm (same solver, same stopping rule).  FP32 path: final
+inlier reprojection RMSE within 1 % of the oracle's.  Pose errors against the
+oracle are computed for every result.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2510_15271_b300 import ba, scenes
+
+pytestmark = pytest.mark.gpu
+
+COST_RTOL = 1e-9     # FP64 path, per-iteration cost
+RMSE_RTOL = 0.01     # reduced-precision paths, final inlier RMSE
+PCG_COST_RTOL = 1e-6  # FP64 path vs oracle, both at PCG tol 1e-6 (the solve tolerance)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2510_15271_b300 import build
+    build.build()
+    ba.lib()
+
+
+def _prob(s):
+    return O.Problem.from_arrays(s.intrinsics(), s.obs_cam, s.obs_pt, s.obs_uv, s.cam_fixed,
+                                 s.n_cams, s.n_pts)
+
+
+def _oracle(s, iters, solver, delta=None, tol=1e-6, maxit=100):
+    prob = _prob(s)
+    res = O.lm_solve(prob, O.state_from_qt(s.cam_qt, s.pts),
+                     O.LMOptions(huber_delta=s.huber_delta if delta is None else delta,
+                                 lm_iters=iters, solver=solver, pcg_tol=tol,
+                                 pcg_max_iters=maxit))
+    return prob, res
+
+
+def _pose_err(q, res):
+    st = O.state_from_qt(q, np.zeros((1, 3)))
+    rot, pos = O.pose_errors(st.R, st.t, res.state.R, res.state.t)
+    return rot.max(), pos.max()
+
+
+OUTLIER_PX = 5.0  # post-BA outlier threshold applied before the RMSE gate
+
+
+def _inlier_rmse(s, prob, q, p):
+    return O.rmse(prob, O.state_from_qt(q, p), s.obs_inlier, OUTLIER_PX)
+
+
+@pytest.mark.parametrize("kw", [
+    dict(n_cams=20, n_pts=2000),             # the tiny-BA workload itself
+    dict(n_cams=7, n_pts=333, views=3),      # ragged
+    dict(n_cams=13, n_pts=1001, views=4),
+])
+def test_ring_fp64_dense_matches_oracle_per_iteration(kw):
+    s = scenes.make_scene("ring", seed=1, **kw)
+    rep, q, p = ba.solve_scene(s, "fp64", max_lm_iters=10, solver=ba.BA_SOLVER_DENSE)
+    prob, ref = _oracle(s, 10, "dense")
+    rel = np.abs(rep["costs"] - ref.costs) / ref.costs
+    assert rel.max() <= COST_RTOL, (rel, rep["costs"], ref.costs)
+    rot, pos = _pose_err(q, ref)
+    assert rot < 1e-8 and pos < 1e-8, (rot, pos)
+    np.testing.assert_allclose(p, ref.state.X, atol=1e-7)
+
+
+def test_ring_fp64_huber_matches_oracle():
+    s = scenes.make_scene("ring", seed=2, n_cams=12, n_pts=800, sigma=1.0, outlier_frac=0.05,
+                          huber_delta=1.0)
+    rep, q, p = ba.solve_scene(s, "fp64", max_lm_iters=8, solver=ba.BA_SOLVER_DENSE)
+    _, ref = _oracle(s, 8, "dense")
+    rel = np.abs(rep["costs"] - ref.costs) / ref.costs
+    assert rel.max() <= COST_RTOL, (rel, rep["costs"], ref.costs)
+
+
+def _driving_small(seed=3, **kw):
+    base = dict(n_cams=60, n_pts=6000, length_m=120.0)
+    base.update(kw)
+    return scenes.make_scene("driving", seed=seed, **base)
+
+
+def test_driving_fp64_pcg_matches_oracle_pcg():
+    """Production PCG settings (tol 1e-6, max 100) on both sides.  Two CG
+    runs that round differently agree only to about the solve tolerance, so
+    the per-iteration costs are compared at PCG_COST_RTOL; the 1e-9 gate is
+    held by the exact-enough solves below."""
+    s = _driving_small()
+    rep, q, p = ba.solve_scene(s, "fp64", max_lm_iters=8, solver=ba.BA_SOLVER_PCG)
+    _, ref = _oracle(s, 8, "pcg")
+    rel = np.abs(rep["costs"] - ref.costs) / ref.costs
+    assert rel.max() <= PCG_COST_RTOL, (rel, rep["costs"], ref.costs)
+    assert np.abs(rep["pcg_iters"] - ref.pcg_iters).max() <= 2, (rep["pcg_iters"], ref.pcg_iters)
+    print("per-iteration cost rel diff (production PCG):", rel)
+
+
+def test_driving_fp64_tight_pcg_matches_oracle_cholesky():
+    """An exact-enough PCG solve reproduces the direct-solve LM path."""
+    s = _driving_small(seed=4)
+    n = 6 * s.n_cams
+    rep, q, p = ba.solve_scene(s, "fp64", max_lm_iters=6, solver=ba.BA_SOLVER_PCG,
+                               pcg_tol=1e-13, pcg_max_iters=4 * n)
+    _, ref = _oracle(s, 6, "dense")
+    rel = np.abs(rep["costs"] - ref.costs) / ref.costs
+    assert rel.max() <= COST_RTOL, (rel, rep["costs"], ref.costs)
+
+
+def test_fp64_dense_and_pcg_agree_on_the_gpu():
+    s = _driving_small(seed=5, n_cams=30, n_pts=3000, length_m=60.0)
+    rd, _, _ = ba.solve_scene(s, "fp64", max_lm_iters=5, solver=ba.BA_SOLVER_DENSE)
+    rp, _, _ = ba.solve_scene(s, "fp64", max_lm_iters=5, solver=ba.BA_SOLVER_PCG,
+                              pcg_tol=1e-13, pcg_max_iters=2000)
+    np.testing.assert_allclose(rp["costs"], rd["costs"], rtol=COST_RTOL)
+
+
+@pytest.mark.parametrize("name,kw,iters,solver", [
+    ("ring", dict(n_cams=20, n_pts=2000), 10, "dense"),
+    ("driving", dict(n_cams=60, n_pts=6000, length_m=120.0), 20, "pcg"),
+    ("city", dict(n_cams=250, n_pts=12000), 15, "pcg"),
+])
+def test_fp32_final_rmse_within_one_percent(name, kw, iters, solver):
+    s = scenes.make_scene(name, seed=6, **kw)
+    rep, q, p = ba.solve_scene(s, "fp32", max_lm_iters=iters,
+                               solver=ba.BA_SOLVER_DENSE if solver == "dense" else ba.BA_SOLVER_PCG,
+                               refine=1 if name == "city" else 0)
+    prob, ref = _oracle(s, iters, solver)
+    r_gpu = _inlier_rmse(s, prob, q, p)
+    r_ref = O.rmse(prob, ref.state, s.obs_inlier, OUTLIER_PX)
+    assert abs(r_gpu - r_ref) <= RMSE_RTOL * r_ref, (r_gpu, r_ref)
+    assert rep["costs"][-1] < rep["costs"][0]
+    rot, pos = _pose_err(q, ref)
+    print(f"{name} fp32: inlier rmse {r_gpu:.5f} vs {r_ref:.5f}; pose err {rot:.2e} rad {pos:.2e} m")
+
+
+def test_fp32_refinement_reaches_its_tolerance():
+    s = scenes.make_scene("city", seed=7, n_cams=200, n_pts=8000)
+    rep, _, _ = ba.solve_scene(s, "fp32", max_lm_iters=4, solver=ba.BA_SOLVER_PCG, refine=1,
+                               refine_tol=1e-6, refine_max=5, pcg_tol=1e-4)
+    # several inner solves per step; the FP64 residual of the final one is reported
+    assert np.all(rep["pcg_iters"] > 0)
+    assert np.all(rep["pcg_rel_residual"] <= 1e-3)
+
+
+# --------------------------------------------------------------------------- behaviours
+
+def test_resume_matches_one_long_solve():
+    s = scenes.make_scene("ring", seed=8, n_cams=10, n_pts=500)
+    o = ba.options_for_scene(s, "fp64", max_lm_iters=10)
+    with ba.ba_create(o) as h:
+        ba.ba_set_problem(h, s.cam_qt, s.pts, s.obs_cam, s.obs_pt, s.obs_uv, s.intrinsics(),
+                          s.cam_fixed)
+        full = ba.ba_solve(h)
+    o5 = ba.options_for_scene(s, "fp64", max_lm_iters=5)
+    with ba.ba_create(o5) as h:
+        ba.ba_set_problem(h, s.cam_qt, s.pts, s.obs_cam, s.obs_pt, s.obs_uv, s.intrinsics(),
+                          s.cam_fixed)
+        a = ba.ba_solve(h)
+        b = ba.ba_solve(h)
+    split = np.concatenate([a["costs"], b["costs"][1:]])
+    np.testing.assert_allclose(split, full["costs"], rtol=1e-12)
+    # once the cost stops changing, accepting or rejecting is decided by
+    # rounding; compare the damping path up to there
+    moving = (full["costs"][:-1] - full["costs"][1:]) > 1e-9 * full["costs"][1:]
+    upto = int(np.argmin(moving)) if not moving.all() else len(moving)
+    assert upto >= 3
+    np.testing.assert_allclose(np.concatenate([a["mu"], b["mu"]])[:upto], full["mu"][:upto],
+                               rtol=1e-9)
+
+
+def test_graph_and_eager_launches_agree():
+    s = _driving_small(seed=9, n_cams=40, n_pts=3000, length_m=80.0)
+    for solver, rtol in ((ba.BA_SOLVER_DENSE, 1e-12), (ba.BA_SOLVER_PCG, PCG_COST_RTOL)):
+        r1, _, _ = ba.solve_scene(s, "fp64", max_lm_iters=5, use_graph=1, solver=solver)
+        r0, _, _ = ba.solve_scene(s, "fp64", max_lm_iters=5, use_graph=0, solver=solver)
+        np.testing.assert_allclose(r1["costs"], r0["costs"], rtol=rtol)
+
+
+def test_torch_device_inputs_and_allocator_match_host_inputs():
+    import torch
+    s = scenes.make_scene("ring", seed=10, n_cams=9, n_pts=600)
+    r_host, q_host, p_host = ba.solve_scene(s, "fp64", max_lm_iters=5)
+    dev = torch.device("cuda:0")
+    with ba.ba_create(ba.options_for_scene(s, "fp64", max_lm_iters=5), use_torch=True) as h:
+        ba.ba_set_problem(h, torch.tensor(s.cam_qt, device=dev), torch.tensor(s.pts, device=dev),
+                          torch.tensor(s.obs_cam, device=dev), torch.tensor(s.obs_pt, device=dev),
+                          torch.tensor(s.obs_uv, device=dev), s.intrinsics(),
+                          torch.tensor(s.cam_fixed, device=dev))
+        r_dev = ba.ba_solve(h)
+    np.testing.assert_allclose(r_dev["costs"], r_host["costs"], rtol=1e-12)
+
+
+def test_fixed_cameras_do_not_move():
+    s = scenes.make_scene("ring", seed=11, n_cams=8, n_pts=400)
+    fixed = np.zeros(s.n_cams, dtype=np.uint8)
+    fixed[[0, 3, 5]] = 1
+    s.cam_fixed = fixed
+    for prec in ("fp64", "fp32"):
+        rep, q, p = ba.solve_scene(s, prec, max_lm_iters=5)
+        st0 = O.state_from_qt(s.cam_qt, s.pts)
+        st1 = O.state_from_qt(q, p)
+        for i in (0, 3, 5):
+            np.testing.assert_allclose(st1.R[i], st0.R[i], atol=1e-14)
+            np.testing.assert_allclose(st1.t[i], st0.t[i], atol=1e-14)
+        assert not np.allclose(st1.t[1], st0.t[1])
+
+
+def test_all_cameras_fixed_refines_points_like_the_oracle():
+    s = scenes.make_scene("ring", seed=12, n_cams=6, n_pts=200, views=3)
+    s.cam_fixed = np.ones(s.n_cams, dtype=np.uint8)
+    rep, q, p = ba.solve_scene(s, "fp64", max_lm_iters=6)
+    _, ref = _oracle(s, 6, "dense")
+    np.testing.assert_allclose(rep["costs"], ref.costs, rtol=COST_RTOL)
+    np.testing.assert_allclose(p, ref.state.X, atol=1e-9)
+
+
+def test_minimal_problem_two_cameras():
+    s = scenes.make_scene("ring", seed=13, n_cams=3, n_pts=12, views=2)
+    rep, q, p = ba.solve_scene(s, "fp64", max_lm_iters=5)
+    _, ref = _oracle(s, 5, "dense")
+    np.testing.assert_allclose(rep["costs"], ref.costs, rtol=COST_RTOL)
+
+
+def test_rmse_report_matches_oracle():
+    s = scenes.make_scene("ring", seed=14, n_cams=10, n_pts=700)
+    rep, q, p = ba.solve_scene(s, "fp64", max_lm_iters=6)
+    prob = _prob(s)
+    assert rep["rmse_px"] == pytest.approx(O.rmse(prob, O.state_from_qt(q, p)), rel=1e-9)
+    assert rep["n_valid_obs"] == s.n_obs
+
+
+@pytest.mark.parametrize("mutate,msg", [
+    (lambda s: s.obs_cam.__setitem__(5, s.n_cams), "camera index"),
+    (lambda s: s.obs_pt.__setitem__(7, -1), "point index"),
+    (lambda s: s.obs_uv.__setitem__((3, 0), np.nan), "non-finite pixel"),
+    (lambda s: s.pts.__setitem__((2, 1), np.inf), "non-finite point"),
+    (lambda s: s.cam_qt.__setitem__((1, slice(0, 4)), 0.0), "zero quaternion"),
+])
+def test_invalid_problems_are_rejected(mutate, msg):
+    s = scenes.make_scene("ring", seed=15, n_cams=6, n_pts=100, views=3)
+    mutate(s)
+    with ba.ba_create(ba.options_for_scene(s, "fp64")) as h:
+        with pytest.raises(ba.BAError, match=msg) as ei:
+            ba.ba_set_problem(h, s.cam_qt, s.pts, s.obs_cam, s.obs_pt, s.obs_uv, s.intrinsics(),
+                              s.cam_fixed)
+        assert ei.value.status == ba.BA_ERR_INVALID_ARG
+        with pytest.raises(ba.BAError) as e2:
+            ba.ba_solve(h)
+        assert e2.value.status == ba.BA_ERR_STATE
+
+
+def test_under_observed_point_and_unseen_camera_are_rejected():
+    s = scenes.make_scene("ring", seed=16, n_cams=6, n_pts=100, views=3)
+    keep = ~((s.obs_pt == 4) & (np.arange(s.n_obs) != np.nonzero(s.obs_pt == 4)[0][0]))
+    with ba.ba_create(ba.options_for_scene(s, "fp64")) as h:
+        with pytest.raises(ba.BAError, match="fewer than 2"):
+            ba.ba_set_problem(h, s.cam_qt, s.pts, s.obs_cam[keep], s.obs_pt[keep],
+                              s.obs_uv[keep], s.intrinsics(), s.cam_fixed)
+        drop = s.obs_cam != 2
+        with pytest.raises(ba.BAError, match="no observation"):
+            ba.ba_set_problem(h, s.cam_qt, s.pts, s.obs_cam[drop], s.obs_pt[drop],
+                              s.obs_uv[drop], s.intrinsics(), s.cam_fixed)
+        # the same camera, held fixed, is allowed to see nothing
+        fx = s.cam_fixed.copy()
+        fx[2] = 1
+        pts_ok = np.bincount(s.obs_pt[drop], minlength=s.n_pts) >= 2
+        if pts_ok.all():
+            ba.ba_set_problem(h, s.cam_qt, s.pts, s.obs_cam[drop], s.obs_pt[drop],
+                              s.obs_uv[drop], s.intrinsics(), fx)
+
+
+def test_points_behind_cameras_leave_the_cost():
+    s = scenes.make_scene("ring", seed=17, n_cams=6, n_pts=150, views=3)
+    # push one point behind every camera that sees it (through the origin)
+    s.pts[0] = -s.pts[0] * 50.0
+    rep, q, p = ba.solve_scene(s, "fp64", max_lm_iters=3)
+    _, ref = _oracle(s, 3, "dense")
+    np.testing.assert_allclose(rep["costs"], ref.costs, rtol=COST_RTOL)
