@@ -179,6 +179,34 @@ ba_status ba_set_state(ba_handle* h, const double* cam_qt, const double* pts, in
  * solve yet or profiling off), INVALID_ARG. */
 ba_status ba_kernel_stats(const ba_handle* h, ba_kernel_stat* out, int32_t max, int32_t* n);
 
+/* Reprojection cost F = 1/2 sum_k rho(||r_k||^2) of a given state, with no
+ * device allocation.  The paper has no counterpart: this entry point exists
+ * for callers that may not allocate device memory at the point of use (for
+ * example a vehicle or robot process whose device memory plan is fixed at
+ * start-up, or a host library that owns every allocation of its context
+ * through its own pool).  It calls no cudaMalloc, cudaFree or allocating
+ * library routine; its scratch is one file-scope device array of about
+ * 1.5 MB, held by every GPU that loads the library until the process exits.
+ *   device       CUDA device ordinal; the caller's current device is restored
+ *   cuda_stream  cudaStream_t to run on (NULL: the legacy default stream)
+ *   cam_qt, pts, obs_cam, obs_pt, obs_uv   device pointers, layouts as in
+ *                ba_set_problem; observations in any order
+ *   K            host pointer; huber_delta as in ba_options (<= 0: none)
+ *   cost_out     device pointer to one double that receives F
+ * Observations with depth below 1e-3 leave the sum, as in ba_solve.  The call
+ * blocks until cost_out is written.  Limits: n_cams <= 16384.  Every call on
+ * a device shares the scratch array and keeps the last call's contents (the
+ * call clears what must start at zero); calls whose work overlaps on the GPU
+ * race.  The first call on a device looks up the array's device address,
+ * with that device current; make that first call before any stream capture
+ * on the device begins.  Errors (message in ba_last_error(NULL)):
+ * INVALID_ARG (NULL pointer, size < 1, n_cams above the limit, an index out
+ * of range), CUDA. */
+ba_status ba_cost_noalloc(int device, void* cuda_stream, int32_t n_cams, int32_t n_pts,
+                          int64_t n_obs, const double* cam_qt, const double* pts,
+                          const int32_t* obs_cam, const int32_t* obs_pt, const double* obs_uv,
+                          const ba_intrinsics* K, double huber_delta, double* cost_out);
+
 /* Release the handle and everything it owns.  NULL is ignored. */
 void ba_destroy(ba_handle* h);
 

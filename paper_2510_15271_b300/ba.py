@@ -122,6 +122,9 @@ _SIGNATURES = {
     "ba_create_server": (c_int, [POINTER(Options), POINTER(c_void_p)]),
     "ba_submit": (c_int, [c_void_p, POINTER(Problem), POINTER(c_uint64)]),
     "ba_poll": (c_int, [c_void_p, c_uint64, POINTER(Result)]),
+    "ba_cost_noalloc": (c_int, [c_int, c_void_p, c_int32, c_int32, c_int64, c_void_p, c_void_p,
+                                c_void_p, c_void_p, c_void_p, POINTER(Intrinsics), c_double,
+                                c_void_p]),
 }
 
 EXPORTS = tuple(_SIGNATURES)
