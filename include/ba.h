@@ -91,6 +91,13 @@ typedef struct {
   int serve_queue;          /* maximum requests waiting for admission        */
   int profile;              /* record per-kernel device times (CUDA events
                                between the kernels of the captured loop)      */
+  int pcg_variant;          /* 0 or 1: standard PCG (two grid barriers per
+                               iteration); 2: pipelined PCG (one barrier per
+                               iteration; in FP32 it converges less well)    */
+  double mu_min;            /* floor of the damping used in the linear system;
+                               < 0: auto (1e-4 for BA_FP32, where rounding in
+                               the FP32 Schur complement otherwise exceeds its
+                               smallest eigenvalues; 0 for BA_FP64)          */
 } ba_options;
 
 typedef struct {

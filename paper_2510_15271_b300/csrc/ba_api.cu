@@ -134,11 +134,16 @@ void ba_options_default(ba_options* o) {
   o->serve_arena_bytes = 0;
   o->serve_slots = 256;
   o->serve_queue = 4096;
+  o->mu_min = -1.0;
 }
 
 static ba_status check_options(const ba_options* o, std::string& err) {
   if (o->precision != BA_FP64 && o->precision != BA_FP32) {
     err = "precision must be BA_FP64 or BA_FP32";
+    return BA_ERR_INVALID_ARG;
+  }
+  if (o->pcg_variant < 0 || o->pcg_variant > 2) {
+    err = "pcg_variant must be 0 (auto), 1 (standard) or 2 (pipelined)";
     return BA_ERR_INVALID_ARG;
   }
   if (o->solver < BA_SOLVER_AUTO || o->solver > BA_SOLVER_PCG) {
@@ -299,6 +304,7 @@ ba_status ba_set_problem(ba_handle* h, int32_t n_cams, int32_t n_pts, int64_t n_
   d.N = N;
   d.K = Intrinsics{K->fx, K->fy, K->cx, K->cy};
   d.precision = prec;
+  d.mu_min = h->opts.mu_min >= 0.0 ? h->opts.mu_min : (prec == BA_FP32 ? kMuMinFp32 : 0.0);
 
   // ---- validation and counts
   int32_t* cam_cnt = (int32_t*)tmp.get(C * sizeof(int32_t));
@@ -471,6 +477,51 @@ ba_status ba_set_problem(ba_handle* h, int32_t n_cams, int32_t n_pts, int64_t n_
     launch_segments(np, pk0, head, segid, d.seg_begin, d.seg_slot, d.chunk_seg, nseg, nchunks, s);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s));
+
+    // sub-segments of at most sub_len pairs (host side, from the segment table)
+    std::vector<int32_t> hsb(nseg + 1), hslot(nseg), hcs(nchunks + 1);
+    CK(cudaMemcpy(hsb.data(), d.seg_begin, (nseg + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(hslot.data(), d.seg_slot, nseg * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(hcs.data(), d.chunk_seg, (nchunks + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    const size_t smax_sub = max_dyn_smem(h->device) - 4096;
+    const int colcap_guess = std::min<int>(*std::max_element(hrow.begin(), hrow.end()), 64);
+    int sub_len = 8, max_subs = 0;
+    for (;; sub_len *= 2) {
+      max_subs = 0;
+      for (int ch = 0; ch < nchunks; ++ch) {
+        int n = 0;
+        for (int sg = hcs[ch]; sg < hcs[ch + 1]; ++sg)
+          n += (hsb[sg + 1] - hsb[sg] + sub_len - 1) / sub_len;
+        max_subs = std::max(max_subs, n);
+      }
+      if (schur_smem(prec, colcap_guess, max_subs) <= smax_sub || sub_len >= 4096) break;
+    }
+    std::vector<int32_t> hss(nseg + 1), hsub, hsubslot;
+    hsub.reserve((size_t)nseg * 2);
+    for (int sg = 0; sg < nseg; ++sg) {
+      hss[sg] = (int32_t)hsub.size();
+      for (int p = hsb[sg]; p < hsb[sg + 1]; p += sub_len) {
+        hsub.push_back(p);
+        hsubslot.push_back(hslot[sg]);
+      }
+    }
+    hss[nseg] = (int32_t)hsub.size();
+    const int nsub = (int)hsub.size();
+    hsub.push_back((int32_t)np);
+    ok = keep(h, d.sub_begin, (nsub + 1) * sizeof(int32_t)) &&
+         keep(h, d.sub_slot, std::max(nsub, 1) * sizeof(int32_t)) &&
+         keep(h, d.seg_sub, (nseg + 1) * sizeof(int32_t));
+    if (!ok) {
+      h->err = "ba_set_problem: out of device memory (sub-segments)";
+      free_problem(h);
+      return BA_ERR_OOM;
+    }
+    CK(cudaMemcpy(d.sub_begin, hsub.data(), (nsub + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+    if (nsub) CK(cudaMemcpy(d.sub_slot, hsubslot.data(), nsub * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.seg_sub, hss.data(), (nseg + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+    d.nsub = nsub;
+    d.sub_len = sub_len;
+    d.max_chunk_subs = max_subs;
   }
 
   // ---- solver buffers and state
@@ -542,6 +593,7 @@ ba_status ba_set_problem(ba_handle* h, int32_t n_cams, int32_t n_pts, int64_t n_
   cfg.refine = (h->opts.refine && prec == BA_FP32) ? 1 : 0;
   cfg.refine_max = h->opts.refine_max;
   cfg.refine_tol = h->opts.refine_tol;
+  cfg.pcg_pipelined = h->opts.pcg_variant == 2;
   int solver = h->opts.solver;
   if (solver == BA_SOLVER_AUTO) solver = (6 * C <= h->opts.dense_max_dim) ? BA_SOLVER_DENSE : BA_SOLVER_PCG;
   cfg.solver = solver;
@@ -567,14 +619,30 @@ ba_status ba_set_problem(ba_handle* h, int32_t n_cams, int32_t n_pts, int64_t n_
   } else {
     std::vector<int32_t> hrp(C + 1, 0);
     for (int i = 0; i < C; ++i) hrp[i + 1] = hrp[i] + hrow[i];
-    if (!plan_pcg(prec, h->device, hrp, smax - 4096, cfg)) {
+    std::vector<int32_t> hcol(d.nnzb);
+    CK(cudaMemcpy(hcol.data(), d.s_col, d.nnzb * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    PcgPlan plan;
+    if (!plan_pcg(prec, h->device, hrp, hcol, smax - 4096, cfg, plan)) {
       h->err = "ba_set_problem: too many cameras for the PCG kernel";
       free_problem(h);
       return BA_ERR_INVALID_ARG;
     }
+    ok = keep(h, d.pcg_ucol, std::max<size_t>(plan.ucol.size(), 1) * sizeof(int32_t)) &&
+         keep(h, d.pcg_uptr, plan.uptr.size() * sizeof(int32_t)) &&
+         keep(h, d.pcg_lcol, std::max<size_t>(plan.lcol.size(), 1) * sizeof(int32_t)) &&
+         keep(h, d.pcg_lown, plan.lown.size() * sizeof(int32_t));
+    if (!ok) {
+      h->err = "ba_set_problem: out of device memory (PCG plan)";
+      free_problem(h);
+      return BA_ERR_OOM;
+    }
+    CK(cudaMemcpy(d.pcg_ucol, plan.ucol.data(), plan.ucol.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.pcg_uptr, plan.uptr.data(), plan.uptr.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.pcg_lcol, plan.lcol.data(), plan.lcol.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.pcg_lown, plan.lown.data(), plan.lown.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   }
-  cfg.schur_colcap = schur_colcap(prec, d.max_row_nnz, smax - 2048);
-  set_schur_smem_attr(prec, schur_smem(prec, cfg.schur_colcap));
+  cfg.schur_colcap = schur_colcap(prec, d.max_row_nnz, d.max_chunk_subs, smax - 2048);
+  set_schur_smem_attr(prec, schur_smem(prec, cfg.schur_colcap, d.max_chunk_subs));
   CK(cudaEventRecord(h->ev1, s));
   CK(cudaEventSynchronize(h->ev1));
   float ms = 0.f;

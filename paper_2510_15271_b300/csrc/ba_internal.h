@@ -69,6 +69,7 @@ struct DevProblem {
   Intrinsics K{};
   int precision = BA_FP64;
   int n_fixed = 0;
+  double mu_min = 0.0;  // floor of the damping used in the linear system
   // state (FP64) and trial state
   double *R = nullptr, *t = nullptr, *Cc = nullptr, *X = nullptr;
   double *R2 = nullptr, *t2 = nullptr, *Cc2 = nullptr, *X2 = nullptr;
@@ -105,6 +106,18 @@ struct DevProblem {
   int32_t* chunk_seg = nullptr; // [nchunks + 1] first segment of each chunk
   int64_t npairs = 0;
   int nseg = 0, nchunks = 0;
+  // Each segment split into sub-segments of at most sub_len consecutive
+  // pairs (one thread accumulates one sub-segment); sub-segments of a
+  // segment are consecutive.
+  int32_t* sub_begin = nullptr;  // [nsub + 1] first pair of each sub-segment
+  int32_t* sub_slot = nullptr;   // [nsub] output block slot
+  int32_t* seg_sub = nullptr;    // [nseg + 1] first sub-segment of each segment
+  int nsub = 0, sub_len = 16, max_chunk_subs = 0;
+  // PCG shared-memory variant: per-CTA lists of referenced columns
+  int32_t* pcg_ucol = nullptr;  // concatenated lists
+  int32_t* pcg_uptr = nullptr;  // [G + 1]
+  int32_t* pcg_lcol = nullptr;  // [nnzb] list index of each block's column
+  int32_t* pcg_lown = nullptr;  // [C] list index of each row's own column
   // linearisation (T)
   void* W = nullptr;    // [N][W_STRIDE]
   void* U = nullptr;    // [C][36]
@@ -141,6 +154,7 @@ struct DevProblem {
 };
 
 constexpr int kSchurChunk = 256;      // observations of a camera row per Schur chunk
+constexpr double kMuMinFp32 = 1e-4;   // default damping floor of the FP32 path
 constexpr int kDenseMaxDim = 4096;     // largest 6C the one-CTA dense solver accepts
 constexpr int kWStrideF32 = 20;  // 18 used, padded to 80 B (float4 aligned)
 constexpr int kWStrideF64 = 18;  // 144 B (double2 aligned)

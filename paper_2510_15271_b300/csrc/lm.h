@@ -44,7 +44,9 @@ struct SolveConfig {
   int pcg_threads = 256;
   int pcg_rows = 1;        // block rows per CTA (contiguous)
   int pcg_rw = 1;          // rows per warp (kernel variant)
+  int pcg_pipelined = 0;   // one-barrier pipelined PCG instead of the standard recurrence
   int pcg_maxnnz = 0;      // most blocks of S held by one CTA
+  int pcg_maxu = 0;        // most distinct columns referenced by one CTA
   size_t pcg_smem = 0;     // dynamic shared memory (0: rows of S read from global)
   size_t dense_smem = 0;   // dynamic shared memory of the dense solver (0: global workspace)
   Marks* marks = nullptr;
@@ -56,8 +58,8 @@ void mark(const SolveConfig& cfg, int k, cudaStream_t s);
 int cost_blocks(const DevProblem& d);
 int backsub_blocks(const DevProblem& d);
 int retract_blocks(const DevProblem& d);
-size_t schur_smem(int precision, int colcap);
-int schur_colcap(int precision, int max_row_nnz, size_t smem_limit);
+size_t schur_smem(int precision, int colcap, int max_subs);
+int schur_colcap(int precision, int max_row_nnz, int max_subs, size_t smem_limit);
 void set_schur_smem_attr(int precision, size_t bytes);
 
 void launch_lm_begin(const DevProblem& d, const SolveConfig& cfg, cudaStream_t s);
@@ -66,8 +68,16 @@ void launch_lm_end(const DevProblem& d, const SolveConfig& cfg, cudaStream_t s);
 
 // solvers.cu
 void launch_linear_solve(const DevProblem& d, const SolveConfig& cfg, cudaStream_t s);
-bool plan_pcg(int precision, int device, const std::vector<int32_t>& rowptr, size_t smem_limit,
-              SolveConfig& cfg);
+// Per-CTA column lists of the PCG kernel's shared-memory variant (host copy).
+struct PcgPlan {
+  std::vector<int32_t> ucol;  // concatenated sorted column lists of the CTAs
+  std::vector<int32_t> uptr;  // [G + 1]
+  std::vector<int32_t> lcol;  // [nnzb] list index of each block's column
+  std::vector<int32_t> lown;  // [C] list index of each row's own column
+};
+bool plan_pcg(int precision, int device, const std::vector<int32_t>& rowptr,
+              const std::vector<int32_t>& col, size_t smem_limit, SolveConfig& cfg,
+              PcgPlan& plan);
 size_t dense_smem_bytes(int precision, int n);
 void set_dense_smem_attr(int precision, size_t bytes);
 

@@ -287,7 +287,7 @@ __global__ void k_lin_pt(DevProblem d, T delta) {
 
 template <typename T>
 __global__ void k_damp_pt(DevProblem d) {
-  const double mu = d.lm->mu;
+  const double mu = fmax(d.lm->mu, d.mu_min);  // damping of the linear system
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.P; j += gridDim.x * blockDim.x) {
     const T* Vi = (const T*)d.V + 6 * (int64_t)j;
     double m[6];
@@ -312,24 +312,28 @@ __global__ void k_damp_pt(DevProblem d) {
 
 // --------------------------------------------------------------------------- Schur complement
 
-// Shared-memory layout of k_schur: acc [colcap][36] T | Y [kSchurChunk][18] T.
+// Row stride of a sub-segment result in shared memory (37: the 36 elements
+// written by consecutive threads spread over the banks).
+constexpr int kResStride = 37;
+
+// Shared-memory layout of k_schur: acc [colcap][36] T | Y [kSchurChunk][18] T |
+// sub-segment results [max_subs][kResStride] T.
 template <typename T>
-__host__ __device__ inline size_t schur_smem_bytes(int colcap) {
-  return (size_t)colcap * 36 * sizeof(T) + (size_t)kSchurChunk * 18 * sizeof(T) + 64;
+__host__ __device__ inline size_t schur_smem_bytes(int colcap, int max_subs) {
+  return (size_t)colcap * 36 * sizeof(T) + (size_t)kSchurChunk * 18 * sizeof(T) +
+         (size_t)max_subs * kResStride * sizeof(T) + 64;
 }
 
 // One CTA per camera row i1.  For each chunk of the row's observations:
-// threads compute Y_k1 = W_k1 V*_j^-1 into shared memory; then each warp
-// takes whole segments of the pair list (all pairs of the chunk that land in
-// one output block S_i1,i2).  Each lane takes every 32nd pair of the segment
-// and accumulates the full 6x6 product Y_k1 W_k2^T in registers; a fixed
-// xor-tree warp reduction then gives the block sum.  A segment has one owner
-// per chunk, so the block accumulators need no atomics and the summation
-// order is fixed (bit-reproducible).
+// threads compute Y_k1 = W_k1 V*_j^-1 into shared memory; each thread then
+// takes whole sub-segments of the pair list (at most sub_len consecutive
+// pairs of the chunk that land in one output block S_i1,i2) and accumulates
+// sum Y_k1 W_k2^T over them in registers; finally the sub-segment results of
+// each block are added in order.  No atomics; the summation order is fixed
+// (bit-reproducible).
 template <typename T, int NT>
-__global__ void __launch_bounds__(NT) k_schur(DevProblem d, int colcap) {
-  static_assert(NT == kSchurChunk, "one thread per observation of a chunk");
-  constexpr int WS = WStride<T>::v;
+__global__ void __launch_bounds__(NT, 2) k_schur(DevProblem d, int colcap) {
+  static_assert(NT >= kSchurChunk, "one thread per observation of a chunk");
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double bred[(NT / 32) * 6];
   const int i = blockIdx.x;
@@ -337,9 +341,9 @@ __global__ void __launch_bounds__(NT) k_schur(DevProblem d, int colcap) {
   const int nnz = d.s_rowptr[i + 1] - rb;
   T* acc = reinterpret_cast<T*>(smem);
   T* Ys = acc + (size_t)colcap * 36;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T* Rs = Ys + (size_t)kSchurChunk * 18;
 
-  const double mu = d.lm->mu;
+  const double mu = fmax(d.lm->mu, d.mu_min);  // damping of the linear system
   const bool fixed_i = d.fixed[i] != 0;
   const int kb = d.cam_ptr[i], ke = d.cam_ptr[i + 1];
   const int ch0 = d.chunk_ptr[i], ch1 = d.chunk_ptr[i + 1];
@@ -380,40 +384,62 @@ __global__ void __launch_bounds__(NT) k_schur(DevProblem d, int colcap) {
           }
         }
         __syncthreads();
-        const int sg1 = d.chunk_seg[ch + 1];
-        for (int sg = d.chunk_seg[ch] + warp; sg < sg1; sg += NT / 32) {
-          const int slot = d.seg_slot[sg];
+        // each thread accumulates whole sub-segments (<= sub_len pairs)
+        const int sg0 = d.chunk_seg[ch], sg1 = d.chunk_seg[ch + 1];
+        const int u0 = d.seg_sub[sg0], u1 = d.seg_sub[sg1];
+        // a thread pair per sub-segment: thread h = tid & 1 owns output rows
+        // 3h .. 3h+2; both read the same W gathers (one request)
+        const int h = threadIdx.x & 1;
+        for (int u = u0 + (int)(threadIdx.x >> 1); u < u1; u += NT / 2) {
+          const int slot = d.sub_slot[u];
           if (slot < cb || slot >= cb + ncol) continue;
-          const int pb = d.seg_begin[sg], pe = d.seg_begin[sg + 1];
-          T sum[36];
+          const int pb = d.sub_begin[u], pe = d.sub_begin[u + 1];
+          T sum[18];
 #pragma unroll
-          for (int e = 0; e < 36; ++e) sum[e] = T(0);
-          for (int p = pb + lane; p < pe; p += 32) {
-            const int t = d.pair_t[p];
-            T W2[18];
-            load_w<T>(Wg, d.pair_k2[p], W2);
-            const T* Y = Ys + 18 * t;
+          for (int e = 0; e < 18; ++e) sum[e] = T(0);
+          // groups of up to 4 pairs: the indices are loaded first, so the W
+          // gathers of the (unrolled) group can be issued together
+          for (int p0 = pb; p0 < pe; p0 += 4) {
+            // all four gathers are issued before any arithmetic: past the end
+            // of the sub-segment the last pair is re-read and weighted by 0
+            int tq[4], kq[4];
+            T wq[4];
 #pragma unroll
-            for (int a = 0; a < 6; ++a) {
-              const T y0 = Y[3 * a], y1 = Y[3 * a + 1], y2 = Y[3 * a + 2];
+            for (int q = 0; q < 4; ++q) {
+              const int p = min(p0 + q, pe - 1);
+              tq[q] = (int)d.pair_t[p];
+              kq[q] = d.pair_k2[p];
+              wq[q] = (p0 + q < pe) ? T(1) : T(0);
+            }
+            T W2[4][18];
 #pragma unroll
-              for (int bb = 0; bb < 6; ++bb)
-                sum[6 * a + bb] += y0 * W2[3 * bb] + y1 * W2[3 * bb + 1] + y2 * W2[3 * bb + 2];
+            for (int q = 0; q < 4; ++q) load_w<T>(Wg, kq[q], W2[q]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const T* Y = Ys + 18 * tq[q] + 9 * h;
+#pragma unroll
+              for (int a = 0; a < 3; ++a) {
+                const T y0 = wq[q] * Y[3 * a], y1 = wq[q] * Y[3 * a + 1], y2 = wq[q] * Y[3 * a + 2];
+#pragma unroll
+                for (int bb = 0; bb < 6; ++bb)
+                  sum[6 * a + bb] +=
+                      y0 * W2[q][3 * bb] + y1 * W2[q][3 * bb + 1] + y2 * W2[q][3 * bb + 2];
+              }
             }
           }
+          T* res = Rs + (size_t)(u - u0) * kResStride + 18 * h;
 #pragma unroll
-          for (int e = 0; e < 36; ++e) sum[e] = warp_sum(sum[e]);
-          T* A = acc + 36 * (slot - cb);
-          // every lane holds the totals; lane e writes element e (and 32 + e)
-          T mine = sum[0], extra = sum[32];
-#pragma unroll
-          for (int e = 1; e < 32; ++e)
-            if (lane == e) mine = sum[e];
-#pragma unroll
-          for (int e = 33; e < 36; ++e)
-            if (lane == e - 32) extra = sum[e];
-          A[lane] += mine;
-          if (lane < 4) A[32 + lane] += extra;
+          for (int e = 0; e < 18; ++e) res[e] = sum[e];
+        }
+        __syncthreads();
+        // combine the sub-segments of each segment in order
+        for (int it = threadIdx.x; it < (sg1 - sg0) * 36; it += NT) {
+          const int sg = sg0 + it / 36, e = it % 36;
+          const int slot = d.seg_slot[sg];
+          if (slot < cb || slot >= cb + ncol) continue;
+          T s = T(0);
+          for (int u = d.seg_sub[sg]; u < d.seg_sub[sg + 1]; ++u) s += Rs[(size_t)(u - u0) * kResStride + e];
+          acc[36 * (slot - cb) + e] += s;
         }
         __syncthreads();
       }
@@ -465,7 +491,7 @@ __global__ void __launch_bounds__(NT) k_schur(DevProblem d, int colcap) {
 template <typename T>
 __global__ void k_backsub(DevProblem d) {
   __shared__ double red[32];
-  const double mu = d.lm->mu;
+  const double mu = fmax(d.lm->mu, d.mu_min);  // damping of the linear system
   const T* Wg = (const T*)d.W;
   const T* dc = (const T*)d.dc;
   double part = 0.0;
@@ -520,7 +546,7 @@ __global__ void k_backsub(DevProblem d) {
 template <typename T>
 __global__ void k_retract(DevProblem d) {
   __shared__ double red[32];
-  const double mu = d.lm->mu;
+  const double mu = fmax(d.lm->mu, d.mu_min);  // damping of the linear system
   double part = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.C; i += gridDim.x * blockDim.x) {
     const T* x = (const T*)d.dc + 6 * i;
@@ -635,7 +661,7 @@ __global__ void k_lm_init(DevProblem d, int ncost, double mu0, int iters) {
   LmScalars* lm = d.lm;
   lm->F = F;
   if (lm->fresh) {  // a new problem or state: restart the damping
-    lm->mu = mu0;
+    lm->mu = fmax(mu0, d.mu_min);
     lm->nu = 2.0;
     lm->fresh = 0;
   }
@@ -670,7 +696,7 @@ __global__ void k_gain(DevProblem d, int ncost, int ndl_pt, int ndl_cam) {
   if (ok && gain > 0.0) {
     lm->F = Fn;
     const double t = 2.0 * gain - 1.0;
-    lm->mu = lm->mu * fmax(1.0 / 3.0, 1.0 - t * t * t);
+    lm->mu = fmax(lm->mu * fmax(1.0 / 3.0, 1.0 - t * t * t), d.mu_min);
     lm->nu = 2.0;
     lm->need_lin = 1;
     lm->n_accepted += 1;
@@ -733,14 +759,14 @@ int cost_blocks(const DevProblem& d) { return (int)grid_cap(d.N, 256, kCostParts
 int backsub_blocks(const DevProblem& d) { return (int)grid_cap(d.P, 256, kDlParts / 2); }
 int retract_blocks(const DevProblem& d) { return (int)grid_cap(d.C, 128, kDlParts / 2); }
 
-size_t schur_smem(int precision, int colcap) {
-  return precision == BA_FP32 ? schur_smem_bytes<float>(colcap)
-                              : schur_smem_bytes<double>(colcap);
+size_t schur_smem(int precision, int colcap, int max_subs) {
+  return precision == BA_FP32 ? schur_smem_bytes<float>(colcap, max_subs)
+                              : schur_smem_bytes<double>(colcap, max_subs);
 }
 
-int schur_colcap(int precision, int max_row_nnz, size_t smem_limit) {
+int schur_colcap(int precision, int max_row_nnz, int max_subs, size_t smem_limit) {
   int cap = max_row_nnz < 1 ? 1 : max_row_nnz;
-  while (cap > 1 && schur_smem(precision, cap) > smem_limit) cap = (cap + 1) / 2;
+  while (cap > 1 && schur_smem(precision, cap, max_subs) > smem_limit) cap = (cap + 1) / 2;
   return cap;
 }
 
@@ -774,7 +800,7 @@ static void lm_iteration_t(const DevProblem& d, const SolveConfig& cfg, cudaStre
   mark(cfg, kKLinPt, s);
   k_damp_pt<T><<<gp, 256, 0, s>>>(d);
   mark(cfg, kKDampPt, s);
-  const size_t sm = schur_smem_bytes<T>(cfg.schur_colcap);
+  const size_t sm = schur_smem_bytes<T>(cfg.schur_colcap, d.max_chunk_subs);
   k_schur<T, 256><<<d.C, 256, sm, s>>>(d, cfg.schur_colcap);
   mark(cfg, kKSchur, s);
   launch_linear_solve(d, cfg, s);

@@ -3,17 +3,22 @@
 // k_pcg:    conjugate gradients (Hestenes & Stiefel 1952) preconditioned by
 //           the inverse 6x6 diagonal blocks of S (block Jacobi; Agarwal et al.
 //           2010), as one persistent cooperative launch.  Each CTA owns a
-//           contiguous range of block rows (held in shared memory when they
-//           fit) and each warp some of those rows; lane e < 6 keeps element e
-//           of its rows of x, r, q and p in registers.  A bounded grid
-//           barrier separates the SpMV phase from the update phase (two
-//           barriers per iteration: the search direction p_k = z_k +
-//           beta p_{k-1} is formed on the fly inside the SpMV from z and
-//           p_{k-1}, double-buffered in global memory).  Dots are accumulated
-//           in FP64 and reduced in a fixed order, so every CTA takes the same
+//           contiguous range of block rows and each warp some of those rows;
+//           lane e < 6 keeps element e of its rows of x, r, q and p in
+//           registers.  When the CTA's rows fit in shared memory (SMEM
+//           variant) they stay there for the whole solve, together with the
+//           list of columns they reference: every iteration first stages the
+//           search direction of those columns into shared memory with
+//           coalesced loads, and the block-row products read only shared
+//           memory.  A bounded grid barrier separates the product phase from
+//           the update phase (two barriers per iteration; p_k = z_k +
+//           beta p_{k-1} is formed while staging, from z and p_{k-1}, which
+//           are double-buffered in global memory).  Dots are accumulated in
+//           FP64 and reduced in a fixed order, so every CTA takes the same
 //           decisions.  Optional FP64 iterative refinement (the inner solve
 //           corrects the FP64 residual b - S x; Carson & Higham 2018) runs as
-//           an outer loop in the same launch.
+//           an outer loop in the same launch.  A pipelined variant
+//           (Ghysels & Vanroose 2014) needs one barrier per iteration.
 // k_dense:  one CTA assembles S densely and solves it by Cholesky (lower,
 //           right-looking) with forward and back substitution; a
 //           non-positive pivot marks the step unusable.
@@ -44,6 +49,13 @@ __device__ __forceinline__ unsigned atom_add_relaxed_u32(unsigned* p, unsigned v
   return old;
 }
 
+__device__ __forceinline__ unsigned atom_add_release_u32(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.release.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v)
+               : "memory");
+  return old;
+}
+
 __device__ __forceinline__ void st_relaxed_u32(unsigned* p, unsigned v) {
   asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -64,16 +76,15 @@ __device__ __forceinline__ int ld_err(const int* err) {
 
 // Grid-wide barrier over co-resident CTAs (cooperative launch).  bar[0]
 // counts arrivals, bar[1] is the generation.  The CTA's writes are released
-// by __syncthreads + fence.acq_rel before the arrival and acquired by the
-// acquire-load that sees the new generation.  A wait that exceeds
-// kBarrierLimitNs (or sees another CTA's error) sets kErrBarrierTimeout in
-// *err and returns; callers stop at their next check of *err.
+// by __syncthreads + the release arrival and acquired by the acquire-load
+// that sees the new generation (the last arriver acquires through its fence).
+// A wait that exceeds kBarrierLimitNs (or sees another CTA's error) sets
+// kErrBarrierTimeout in *err and returns; callers stop at their next check.
 __device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned nblocks, int* err) {
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned g = ld_acquire_u32(bar + 1);
-    fence_acq_rel_gpu();
-    const unsigned prev = atom_add_relaxed_u32(bar, 1u);
+    const unsigned prev = atom_add_release_u32(bar, 1u);
     if (prev == nblocks - 1) {
       st_relaxed_u32(bar, 0u);
       fence_acq_rel_gpu();
@@ -103,15 +114,21 @@ __device__ __forceinline__ T ldcg(const T* p) {
 // blocks read by 32 lanes (one block per lane) on distinct banks.
 constexpr int kSPad = 37;
 
-// The block rows [r0, r1) of S owned by one CTA, read from shared memory
-// (local = true: block and row indices relative to the CTA's first row) or
-// straight from global memory.
+// The block rows [r0, r1) of S owned by one CTA.  SMEM variant: blocks,
+// inverse diagonal blocks and row pointers in shared memory, block columns
+// as indices into the CTA's column list ucol, and the staged vector sv
+// (6 values per listed column).  Otherwise everything is read from global
+// memory with global column indices.
 template <typename T>
 struct RowSet {
   const T* S;
   const int32_t* col;
   const int32_t* rowptr;
   const T* Minv;
+  const int32_t* ucol;  // SMEM: global camera of each listed column
+  const int32_t* own;   // SMEM: list index of each owned row's own column
+  T* sv;                // SMEM: staged vector
+  int nu;               // SMEM: listed columns
   int sstride;
   int r0, r1;
   bool local;
@@ -123,20 +140,39 @@ struct RowSet {
   __device__ __forceinline__ const T* minv(int i) const {
     return Minv + 36 * (int64_t)(local ? i - r0 : i);
   }
+  __device__ __forceinline__ int gcol(int b) const { return local ? ucol[col[b]] : col[b]; }
 };
 
-// Warp computes out = S_i. v for block row i, v(c) supplied by vget; the
-// result is in every lane.
+// sv = a + beta b over the listed columns (b may be null); coalesced: the 6
+// values of a column are consecutive in both.
+template <typename T, int NT>
+__device__ __forceinline__ void stage(const RowSet<T>& rs, const T* a, const T* b, T beta) {
+  for (int idx = threadIdx.x; idx < rs.nu * 6; idx += NT) {
+    const int g = 6 * rs.ucol[idx / 6] + idx % 6;
+    rs.sv[idx] = b ? ldcg(a + g) + beta * ldcg(b + g) : ldcg(a + g);
+  }
+  __syncthreads();
+}
+
+// Warp computes out = S_i. v for block row i, v(c) supplied by vget (c is
+// the block's column index of rs.col); the result is in every lane.
 template <typename T, typename Get>
 __device__ __forceinline__ void row_spmv(const RowSet<T>& rs, int i, Get vget, T out[6]) {
   const int lane = threadIdx.x & 31;
   T acc[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
   const int be = rs.re(i);
-  for (int b = rs.rb(i) + lane; b < be; b += 32) {
+  // two blocks per lane per round so that both rounds of gathers are in flight
+  for (int b = rs.rb(i) + lane; b < be; b += 64) {
+    const int b2 = b + 32;
+    const bool two = b2 < be;
     const int c = rs.col[b];
-    T v[6];
+    const int c2 = two ? rs.col[b2] : c;
+    T v[6], v2[6];
 #pragma unroll
-    for (int e = 0; e < 6; ++e) v[e] = vget(6 * c + e);
+    for (int e = 0; e < 6; ++e) {
+      v[e] = vget(6 * c + e);
+      v2[e] = vget(6 * c2 + e);
+    }
     const T* B = rs.blk(b);
 #pragma unroll
     for (int a = 0; a < 6; ++a) {
@@ -144,6 +180,16 @@ __device__ __forceinline__ void row_spmv(const RowSet<T>& rs, int i, Get vget, T
 #pragma unroll
       for (int e = 0; e < 6; ++e) s += B[6 * a + e] * v[e];
       acc[a] = s;
+    }
+    if (two) {
+      const T* B2 = rs.blk(b2);
+#pragma unroll
+      for (int a = 0; a < 6; ++a) {
+        T s = acc[a];
+#pragma unroll
+        for (int e = 0; e < 6; ++e) s += B2[6 * a + e] * v2[e];
+        acc[a] = s;
+      }
     }
   }
 #pragma unroll
@@ -209,7 +255,7 @@ __device__ __forceinline__ void all_partials(const double* slot, int stride, int
 // r0 + w + m NW (m < RW); lane e < 6 holds element e of those rows.
 // Returns iterations; writes the final relative residual to *rel.  Called by
 // every thread of every CTA.
-template <typename T, int NT, int RW>
+template <typename T, int NT, int RW, bool STAGED>
 __device__ int pcg_solve(const DevProblem& d, const RowSet<T>& rs, const T* __restrict__ rhs,
                          T* __restrict__ x, double tol, int max_iters, double* rel, int* err) {
   __shared__ double red[(NT / 32) * 2];
@@ -236,10 +282,7 @@ __device__ int pcg_solve(const DevProblem& d, const RowSet<T>& rs, const T* __re
     const T* M = rs.minv(i);
     T zi = T(0);
 #pragma unroll
-    for (int f = 0; f < 6; ++f) {
-      const T rf = __shfl_sync(0xffffffffu, ri, f);
-      zi += M[6 * el + f] * rf;
-    }
+    for (int f = 0; f < 6; ++f) zi += M[6 * el + f] * __shfl_sync(0xffffffffu, ri, f);
     if (lane < 6) {
       z[6 * i + el] = zi;
       loc[0] += (double)ri * (double)zi;
@@ -260,15 +303,21 @@ __device__ int pcg_solve(const DevProblem& d, const RowSet<T>& rs, const T* __re
     const T* po = pb[cur ^ 1];
     const T bt = (T)beta;
     // phase A: p_k = z + beta p_{k-1}; q = S p_k; partial p.q
+    if (STAGED) stage<T, NT>(rs, z, po, bt);
     double pq_loc[1] = {0.0};
 #pragma unroll
     for (int m = 0; m < RW; ++m) {
       const int i = rs.r0 + warp + m * NW;
       if (i >= rs.r1) continue;
-      const T zo = ldcg(z + 6 * i + el), poo = ldcg(po + 6 * i + el);
-      T qi[6];
-      row_spmv<T>(rs, i, [&](int idx) { return ldcg(z + idx) + bt * ldcg(po + idx); }, qi);
-      const T pi = zo + bt * poo;
+      T qi[6], pi;
+      if (STAGED) {
+        row_spmv<T>(rs, i, [&](int idx) { return rs.sv[idx]; }, qi);
+        pi = rs.sv[6 * rs.own[i - rs.r0] + el];
+      } else {
+        const T zo = ldcg(z + 6 * i + el), poo = ldcg(po + 6 * i + el);
+        row_spmv<T>(rs, i, [&](int idx) { return ldcg(z + idx) + bt * ldcg(po + idx); }, qi);
+        pi = zo + bt * poo;
+      }
       pr[m] = pi;
       qr[m] = pick6(qi, el);
       if (lane < 6) {
@@ -296,10 +345,7 @@ __device__ int pcg_solve(const DevProblem& d, const RowSet<T>& rs, const T* __re
       const T* M = rs.minv(i);
       T zi = T(0);
 #pragma unroll
-      for (int f = 0; f < 6; ++f) {
-        const T rf = __shfl_sync(0xffffffffu, ri, f);
-        zi += M[6 * el + f] * rf;
-      }
+      for (int f = 0; f < 6; ++f) zi += M[6 * el + f] * __shfl_sync(0xffffffffu, ri, f);
       if (lane < 6) {
         z[6 * i + el] = zi;
         l2[0] += (double)ri * (double)zi;
@@ -323,21 +369,160 @@ __device__ int pcg_solve(const DevProblem& d, const RowSet<T>& rs, const T* __re
   return k;
 }
 
-// Shared-memory layout of the SMEM variant: blocks [maxnnz][kSPad] T |
-// Minv [R][36] T | cols [maxnnz] int32 | rowptr [R + 1] int32.
+// Pipelined PCG (Ghysels & Vanroose 2014, "Hiding global synchronization
+// latency in the preconditioned conjugate gradient algorithm", Alg. 3): the
+// same Krylov iterates as PCG in exact arithmetic, with the two dot products
+// of an iteration reduced together and overlapped with the product n = S m,
+// m = M w, so each iteration needs one grid barrier instead of two.  Lane
+// e < 6 of the owning warp keeps element e of x, r, u, w, z, q, s, p of its
+// rows in registers; m is exchanged through global memory (double-buffered).
+// Same stopping rule as pcg_solve (||r|| <= tol ||b||, at most max_iters
+// products with S after the initial one, stop if the curvature term is not
+// positive).
+template <typename T, int NT, int RW, bool STAGED>
+__device__ int pcg_solve_pipelined(const DevProblem& d, const RowSet<T>& rs,
+                                   const T* __restrict__ rhs, T* __restrict__ x, double tol,
+                                   int max_iters, double* rel, int* err) {
+  __shared__ double red[(NT / 32) * 3];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = NT / 32;
+  const unsigned nb = gridDim.x;
+  T* mb[2] = {(T*)d.p0, (T*)d.p1};  // M w, exchanged
+  T* ub = (T*)d.z;                  // u at the start, exchanged once
+  double* partA = d.part + kPartPcg;  // [nb][3]
+  const int el = lane < 6 ? lane : 0;
+
+  T xr[RW], rr_[RW], ur[RW], wr[RW], zr[RW], qr[RW], sr[RW], pr[RW], mr[RW];
+  // r = rhs, u = M r (published for w = S u)
+#pragma unroll
+  for (int m = 0; m < RW; ++m) {
+    const int i = rs.r0 + warp + m * NW;
+    xr[m] = rr_[m] = ur[m] = wr[m] = zr[m] = qr[m] = sr[m] = pr[m] = mr[m] = T(0);
+    if (i >= rs.r1) continue;
+    const T ri = lane < 6 ? rhs[6 * i + el] : T(0);
+    rr_[m] = ri;
+    const T* M = rs.minv(i);
+    T ui = T(0);
+#pragma unroll
+    for (int f = 0; f < 6; ++f) ui += M[6 * el + f] * __shfl_sync(0xffffffffu, ri, f);
+    ur[m] = ui;
+    if (lane < 6) ub[6 * i + el] = ui;
+  }
+  grid_barrier(d.barrier, nb, err);
+  // w = S u
+  if (STAGED) stage<T, NT>(rs, ub, (const T*)nullptr, T(0));
+#pragma unroll
+  for (int m = 0; m < RW; ++m) {
+    const int i = rs.r0 + warp + m * NW;
+    if (i >= rs.r1) continue;
+    T wi[6];
+    if (STAGED) row_spmv<T>(rs, i, [&](int idx) { return rs.sv[idx]; }, wi);
+    else row_spmv<T>(rs, i, [&](int idx) { return ldcg(ub + idx); }, wi);
+    wr[m] = pick6(wi, el);
+  }
+  double bnorm = -1.0, gamma_prev = 0.0, alpha_prev = 0.0, rr = 0.0;
+  int k = 0;
+  for (;;) {
+    // local: gamma = (r,u), delta = (w,u), (r,r); m = M w (published)
+    T* mo = mb[k & 1];
+    double loc[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int m = 0; m < RW; ++m) {
+      const int i = rs.r0 + warp + m * NW;
+      if (i >= rs.r1) continue;
+      const T* M = rs.minv(i);
+      const T wi = lane < 6 ? wr[m] : T(0);
+      T mi = T(0);
+#pragma unroll
+      for (int f = 0; f < 6; ++f) mi += M[6 * el + f] * __shfl_sync(0xffffffffu, wi, f);
+      mr[m] = mi;
+      if (lane < 6) {
+        mo[6 * i + el] = mi;
+        loc[0] += (double)rr_[m] * (double)ur[m];
+        loc[1] += (double)wr[m] * (double)ur[m];
+        loc[2] += (double)rr_[m] * (double)rr_[m];
+      }
+    }
+    cta_partials<NT, 3>(loc, red, partA, 3);
+    grid_barrier(d.barrier, nb, err);
+    double tot[3];
+    all_partials<3>(partA, 3, nb, tot);
+    const double gamma = tot[0], delta = tot[1];
+    rr = tot[2];
+    if (bnorm < 0.0) bnorm = sqrt(rr);
+    if (!(k < max_iters && sqrt(rr) > tol * bnorm) || ld_err(err)) break;
+    double beta, alpha;
+    if (k == 0) {
+      beta = 0.0;
+      alpha = gamma / delta;
+    } else {
+      beta = gamma / gamma_prev;
+      const double den = delta - beta * gamma / alpha_prev;
+      alpha = gamma / den;
+    }
+    if (!(alpha > 0.0) || !isfinite(alpha)) break;  // curvature not positive
+    const T bt = (T)beta, al = (T)alpha;
+    // n = S m; recurrences
+    if (STAGED) stage<T, NT>(rs, mo, (const T*)nullptr, T(0));
+#pragma unroll
+    for (int m = 0; m < RW; ++m) {
+      const int i = rs.r0 + warp + m * NW;
+      if (i >= rs.r1) continue;
+      T ni6[6];
+      if (STAGED) row_spmv<T>(rs, i, [&](int idx) { return rs.sv[idx]; }, ni6);
+      else row_spmv<T>(rs, i, [&](int idx) { return ldcg(mo + idx); }, ni6);
+      const T ni = pick6(ni6, el);
+      zr[m] = ni + bt * zr[m];
+      qr[m] = mr[m] + bt * qr[m];
+      sr[m] = wr[m] + bt * sr[m];
+      pr[m] = ur[m] + bt * pr[m];
+      xr[m] = xr[m] + al * pr[m];
+      rr_[m] = rr_[m] - al * sr[m];
+      ur[m] = ur[m] - al * qr[m];
+      wr[m] = wr[m] - al * zr[m];
+    }
+    gamma_prev = gamma;
+    alpha_prev = alpha;
+    ++k;
+  }
+#pragma unroll
+  for (int m = 0; m < RW; ++m) {
+    const int i = rs.r0 + warp + m * NW;
+    if (i < rs.r1 && lane < 6) x[6 * i + el] = xr[m];
+  }
+  *rel = bnorm > 0.0 ? sqrt(rr) / bnorm : 0.0;
+  return k;
+}
+
+template <typename T, int NT, int RW, bool PIPE, bool STAGED>
+__device__ __forceinline__ int pcg_dispatch(const DevProblem& d, const RowSet<T>& rs,
+                                            const T* rhs, T* x, double tol, int max_iters,
+                                            double* rel, int* err) {
+  if (PIPE) return pcg_solve_pipelined<T, NT, RW, STAGED>(d, rs, rhs, x, tol, max_iters, rel, err);
+  return pcg_solve<T, NT, RW, STAGED>(d, rs, rhs, x, tol, max_iters, rel, err);
+}
+
+// Shared-memory layout of the SMEM variant:
+//   blocks [maxnnz][kSPad] T | Minv [R][36] T | staged vector [maxu][6] T |
+//   block columns [maxnnz] | row pointers [R + 1] | column list [maxu] |
+//   own-column index [R]   (int32)
 template <typename T>
-__host__ __device__ inline size_t pcg_smem_bytes(int maxnnz, int R) {
+__host__ __device__ inline size_t pcg_smem_bytes(int maxnnz, int R, int maxu) {
   size_t o = (size_t)maxnnz * kSPad * sizeof(T);
   o = (o + 15) & ~size_t(15);
   o += (size_t)R * 36 * sizeof(T);
+  o += (size_t)maxu * 6 * sizeof(T);
   o += (size_t)maxnnz * sizeof(int32_t);
   o += (size_t)(R + 1) * sizeof(int32_t);
+  o += (size_t)maxu * sizeof(int32_t);
+  o += (size_t)R * sizeof(int32_t);
   return o + 16;
 }
 
-template <typename T, int NT, bool SMEM, int RW>
+template <typename T, int NT, bool SMEM, int RW, bool PIPE>
 __global__ void __launch_bounds__(NT) k_pcg(DevProblem d, double tol, int max_iters, int refine,
-                                            int refine_max, double refine_tol, int R, int maxnnz) {
+                                            int refine_max, double refine_tol, int R, int maxnnz,
+                                            int maxu) {
   extern __shared__ __align__(16) unsigned char smem[];
   int* err = &d.lm->error;
   const unsigned nb = gridDim.x;
@@ -353,15 +538,25 @@ __global__ void __launch_bounds__(NT) k_pcg(DevProblem d, double tol, int max_it
     size_t o = ((size_t)maxnnz * kSPad * sizeof(T) + 15) & ~size_t(15);
     T* sM = reinterpret_cast<T*>(smem + o);
     o += (size_t)R * 36 * sizeof(T);
+    T* sv = reinterpret_cast<T*>(smem + o);
+    o += (size_t)maxu * 6 * sizeof(T);
     int32_t* scol = reinterpret_cast<int32_t*>(smem + o);
     o += (size_t)maxnnz * sizeof(int32_t);
     int32_t* srow = reinterpret_cast<int32_t*>(smem + o);
+    o += (size_t)(R + 1) * sizeof(int32_t);
+    int32_t* sucol = reinterpret_cast<int32_t*>(smem + o);
+    o += (size_t)maxu * sizeof(int32_t);
+    int32_t* sown = reinterpret_cast<int32_t*>(smem + o);
     const int nb0 = d.s_rowptr[r0];
     const int n = d.s_rowptr[r1] - nb0;
+    const int u0 = d.pcg_uptr[blockIdx.x];
+    const int nu = d.pcg_uptr[blockIdx.x + 1] - u0;
     const T* Sg = (const T*)d.S + 36 * (int64_t)nb0;
     for (int e = threadIdx.x; e < n * 36; e += NT) sS[(e / 36) * kSPad + e % 36] = Sg[e];
-    for (int e = threadIdx.x; e < n; e += NT) scol[e] = d.s_col[nb0 + e];
+    for (int e = threadIdx.x; e < n; e += NT) scol[e] = d.pcg_lcol[nb0 + e];
     for (int e = threadIdx.x; e <= r1 - r0; e += NT) srow[e] = d.s_rowptr[r0 + e] - nb0;
+    for (int e = threadIdx.x; e < nu; e += NT) sucol[e] = d.pcg_ucol[u0 + e];
+    for (int e = threadIdx.x; e < r1 - r0; e += NT) sown[e] = d.pcg_lown[r0 + e];
     const T* Mg = (const T*)d.Minv + 36 * (int64_t)r0;
     for (int e = threadIdx.x; e < (r1 - r0) * 36; e += NT) sM[e] = Mg[e];
     __syncthreads();
@@ -369,6 +564,10 @@ __global__ void __launch_bounds__(NT) k_pcg(DevProblem d, double tol, int max_it
     rs.col = scol;
     rs.rowptr = srow;
     rs.Minv = sM;
+    rs.ucol = sucol;
+    rs.own = sown;
+    rs.sv = sv;
+    rs.nu = nu;
     rs.sstride = kSPad;
     rs.local = true;
   } else {
@@ -376,13 +575,18 @@ __global__ void __launch_bounds__(NT) k_pcg(DevProblem d, double tol, int max_it
     rs.col = d.s_col;
     rs.rowptr = d.s_rowptr;
     rs.Minv = (const T*)d.Minv;
+    rs.ucol = nullptr;
+    rs.own = nullptr;
+    rs.sv = nullptr;
+    rs.nu = 0;
     rs.sstride = 36;
     rs.local = false;
   }
   double rel = 0.0;
   int iters = 0;
   if (!refine) {
-    iters = pcg_solve<T, NT, RW>(d, rs, (const T*)d.b, (T*)d.dc, tol, max_iters, &rel, err);
+    iters = pcg_dispatch<T, NT, RW, PIPE, SMEM>(d, rs, (const T*)d.b, (T*)d.dc, tol, max_iters,
+                                                &rel, err);
   } else {
     // FP64 iterative refinement around the T-precision PCG: solve S d = r,
     // x += d, r = b - S x in FP64 (S as stored, promoted), until
@@ -409,7 +613,7 @@ __global__ void __launch_bounds__(NT) k_pcg(DevProblem d, double tol, int max_it
     double rres = b64n;
     for (int o = 0; o < refine_max && rres > refine_tol * b64n && !ld_err(err); ++o) {
       double rel_in;
-      iters += pcg_solve<T, NT, RW>(d, rs, rhs, dx, tol, max_iters, &rel_in, err);
+      iters += pcg_dispatch<T, NT, RW, PIPE, SMEM>(d, rs, rhs, dx, tol, max_iters, &rel_in, err);
       for (int i = r0 + warp; i < r1; i += NW)
         if (lane < 6) x64[6 * i + lane] += (double)dx[6 * i + lane];
       grid_barrier(d.barrier, nb, err);
@@ -418,7 +622,7 @@ __global__ void __launch_bounds__(NT) k_pcg(DevProblem d, double tol, int max_it
         double acc[6] = {0, 0, 0, 0, 0, 0};
         const int be = rs.re(i);
         for (int bI = rs.rb(i) + lane; bI < be; bI += 32) {
-          const int c = rs.col[bI];
+          const int c = rs.gcol(bI);
           double v[6];
 #pragma unroll
           for (int e = 0; e < 6; ++e) v[e] = __ldcg(x64 + 6 * c + e);
@@ -542,28 +746,33 @@ void set_dense_smem_attr(int precision, size_t bytes) {
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-// Kernel variant for (precision, shared memory, rows per warp).
-template <typename T>
-static const void* pcg_fn(bool smem, int rw) {
+// Kernel variant for (precision, shared memory, rows per warp, pipelined).
+template <typename T, bool PIPE>
+static const void* pcg_fn_p(bool smem, int rw) {
   if (smem) {
     switch (rw) {
-      case 1: return (const void*)k_pcg<T, kPcgThreads, true, 1>;
-      case 2: return (const void*)k_pcg<T, kPcgThreads, true, 2>;
+      case 1: return (const void*)k_pcg<T, kPcgThreads, true, 1, PIPE>;
+      case 2: return (const void*)k_pcg<T, kPcgThreads, true, 2, PIPE>;
       default: return nullptr;
     }
   }
   switch (rw) {
-    case 1: return (const void*)k_pcg<T, kPcgThreads, false, 1>;
-    case 2: return (const void*)k_pcg<T, kPcgThreads, false, 2>;
-    case 4: return (const void*)k_pcg<T, kPcgThreads, false, 4>;
-    case 8: return (const void*)k_pcg<T, kPcgThreads, false, 8>;
-    case 16: return (const void*)k_pcg<T, kPcgThreads, false, 16>;
+    case 1: return (const void*)k_pcg<T, kPcgThreads, false, 1, PIPE>;
+    case 2: return (const void*)k_pcg<T, kPcgThreads, false, 2, PIPE>;
+    case 4: return (const void*)k_pcg<T, kPcgThreads, false, 4, PIPE>;
+    case 8: return (const void*)k_pcg<T, kPcgThreads, false, 8, PIPE>;
+    case 16: return (const void*)k_pcg<T, kPcgThreads, false, 16, PIPE>;
     default: return nullptr;
   }
 }
 
-static const void* pcg_fn_prec(int precision, bool smem, int rw) {
-  return precision == BA_FP32 ? pcg_fn<float>(smem, rw) : pcg_fn<double>(smem, rw);
+template <typename T>
+static const void* pcg_fn(bool smem, int rw, bool pipe) {
+  return pipe ? pcg_fn_p<T, true>(smem, rw) : pcg_fn_p<T, false>(smem, rw);
+}
+
+static const void* pcg_fn_prec(int precision, bool smem, int rw, bool pipe) {
+  return precision == BA_FP32 ? pcg_fn<float>(smem, rw, pipe) : pcg_fn<double>(smem, rw, pipe);
 }
 
 static int pcg_occupancy(const void* fn, size_t smem) {
@@ -574,14 +783,17 @@ static int pcg_occupancy(const void* fn, size_t smem) {
 
 // Choose the cooperative grid and the row split of the PCG kernel: one warp
 // per block row where the grid allows, contiguous rows per CTA, and the CTA's
-// rows of S held in shared memory when they fit.  Returns false if the
-// problem has more rows than the kernel variants cover.
-bool plan_pcg(int precision, int device, const std::vector<int32_t>& rowptr, size_t smem_limit,
-              SolveConfig& cfg) {
+// rows of S held in shared memory (with the list of columns they reference)
+// when they fit.  Returns false if the problem has more rows than the kernel
+// variants cover.
+bool plan_pcg(int precision, int device, const std::vector<int32_t>& rowptr,
+              const std::vector<int32_t>& col, size_t smem_limit, SolveConfig& cfg,
+              PcgPlan& plan) {
   const int C = (int)rowptr.size() - 1;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-  const int per_sm_plain = pcg_occupancy(pcg_fn_prec(precision, false, 1), 0);
+  const bool pipe = cfg.pcg_pipelined != 0;
+  const int per_sm_plain = pcg_occupancy(pcg_fn_prec(precision, false, 1, pipe), 0);
   const int gmax = std::max(1, std::min(per_sm_plain * sms, 1024));
   int G = std::max(1, std::min(gmax, (C + kPcgWarps - 1) / kPcgWarps));
   int R = (C + G - 1) / G;
@@ -589,15 +801,32 @@ bool plan_pcg(int precision, int device, const std::vector<int32_t>& rowptr, siz
   int rw = 1;
   while (rw * kPcgWarps < R) rw *= 2;
   if (rw > 16) return false;
-  int maxnnz = 0;
+  // per-CTA column lists
+  plan.ucol.clear();
+  plan.uptr.assign(G + 1, 0);
+  plan.lcol.assign(col.size(), 0);
+  plan.lown.assign(C, 0);
+  int maxnnz = 0, maxu = 0;
+  std::vector<int32_t> cols;
   for (int b = 0; b < G; ++b) {
     const int r0 = std::min(C, b * R), r1 = std::min(C, r0 + R);
     maxnnz = std::max(maxnnz, rowptr[r1] - rowptr[r0]);
+    cols.assign(col.begin() + rowptr[r0], col.begin() + rowptr[r1]);
+    std::sort(cols.begin(), cols.end());
+    cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+    plan.uptr[b] = (int32_t)plan.ucol.size();
+    plan.ucol.insert(plan.ucol.end(), cols.begin(), cols.end());
+    maxu = std::max(maxu, (int)cols.size());
+    for (int k = rowptr[r0]; k < rowptr[r1]; ++k)
+      plan.lcol[k] = (int32_t)(std::lower_bound(cols.begin(), cols.end(), col[k]) - cols.begin());
+    for (int i = r0; i < r1; ++i)
+      plan.lown[i] = (int32_t)(std::lower_bound(cols.begin(), cols.end(), i) - cols.begin());
   }
-  const size_t need = precision == BA_FP32 ? pcg_smem_bytes<float>(maxnnz, R)
-                                           : pcg_smem_bytes<double>(maxnnz, R);
+  plan.uptr[G] = (int32_t)plan.ucol.size();
+  const size_t need = precision == BA_FP32 ? pcg_smem_bytes<float>(maxnnz, R, maxu)
+                                           : pcg_smem_bytes<double>(maxnnz, R, maxu);
   bool smem = false;
-  const void* fs = pcg_fn_prec(precision, true, rw);
+  const void* fs = pcg_fn_prec(precision, true, rw, pipe);
   if (fs && need <= smem_limit) {
     cudaFuncSetAttribute(fs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
     smem = pcg_occupancy(fs, need) * sms >= G;
@@ -606,6 +835,7 @@ bool plan_pcg(int precision, int device, const std::vector<int32_t>& rowptr, siz
   cfg.pcg_rows = R;
   cfg.pcg_rw = rw;
   cfg.pcg_maxnnz = maxnnz;
+  cfg.pcg_maxu = maxu;
   cfg.pcg_smem = smem ? need : 0;
   return true;
 }
@@ -625,7 +855,8 @@ static void linear_solve_t(const DevProblem& d, const SolveConfig& cfg, cudaStre
   double rt = cfg.refine_tol;
   int R = cfg.pcg_rows;
   int mn = cfg.pcg_maxnnz;
-  void* args[] = {&dd, &tol, &mx, &rf, &rm, &rt, &R, &mn};
+  int mu = cfg.pcg_maxu;
+  void* args[] = {&dd, &tol, &mx, &rf, &rm, &rt, &R, &mn, &mu};
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3(cfg.pcg_blocks);
   lc.blockDim = dim3(kPcgThreads);
@@ -636,7 +867,7 @@ static void linear_solve_t(const DevProblem& d, const SolveConfig& cfg, cudaStre
   attr[0].val.cooperative = 1;
   lc.attrs = attr;
   lc.numAttrs = 1;
-  cudaLaunchKernelExC(&lc, pcg_fn<T>(cfg.pcg_smem > 0, cfg.pcg_rw), args);
+  cudaLaunchKernelExC(&lc, pcg_fn<T>(cfg.pcg_smem > 0, cfg.pcg_rw, cfg.pcg_pipelined != 0), args);
 }
 
 void launch_linear_solve(const DevProblem& d, const SolveConfig& cfg, cudaStream_t s) {

@@ -108,6 +108,26 @@ def test_driving_fp64_tight_pcg_matches_oracle_cholesky():
     assert rel.max() <= COST_RTOL, (rel, rep["costs"], ref.costs)
 
 
+def test_pipelined_pcg_matches_oracle_pcg():
+    """The one-barrier pipelined recurrence produces the same iterates as
+    standard PCG in exact arithmetic: FP64 costs agree with the oracle's
+    standard PCG to the solve tolerance, and to 1e-9 when both solves are
+    exact enough."""
+    s = _driving_small(seed=3)
+    rep, _, _ = ba.solve_scene(s, "fp64", max_lm_iters=8, solver=ba.BA_SOLVER_PCG, pcg_variant=2)
+    _, ref = _oracle(s, 8, "pcg")
+    rel = np.abs(rep["costs"] - ref.costs) / ref.costs
+    assert rel.max() <= PCG_COST_RTOL, (rel, rep["costs"], ref.costs)
+    assert np.abs(rep["pcg_iters"] - ref.pcg_iters).max() <= 2, (rep["pcg_iters"], ref.pcg_iters)
+    s = _driving_small(seed=4)
+    n = 6 * s.n_cams
+    rep, _, _ = ba.solve_scene(s, "fp64", max_lm_iters=6, solver=ba.BA_SOLVER_PCG,
+                               pcg_tol=1e-12, pcg_max_iters=4 * n, pcg_variant=2)
+    _, ref = _oracle(s, 6, "dense")
+    rel = np.abs(rep["costs"] - ref.costs) / ref.costs
+    assert rel.max() <= COST_RTOL, (rel, rep["costs"], ref.costs)
+
+
 def test_fp64_dense_and_pcg_agree_on_the_gpu():
     s = _driving_small(seed=5, n_cams=30, n_pts=3000, length_m=60.0)
     rd, _, _ = ba.solve_scene(s, "fp64", max_lm_iters=5, solver=ba.BA_SOLVER_DENSE)
