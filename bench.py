@@ -18,8 +18,10 @@ roofline of the dominant kernel, SM clocks during the timed region, and the
 FP64 CPU oracle on the host cores as a reported baseline.
 """
 import argparse
+import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -290,10 +292,52 @@ def roofline(res, peak_gbs, peak_kind):
     mean_pcg = float(np.mean(res["reps"][-1]["pcg_iters"])) if name == "pcg" else 0
     nbytes = algorithmic_bytes(s, nnzb, name, True, pcg_iters=mean_pcg)
     achieved = nbytes / (per_launch_ms / 1e3) / 1e9
-    return {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak_gbs,
-            "unit": "GB/s", "frac": round(achieved / peak_gbs, 4), "traffic": None,
-            "peak_source": peak_kind, "bytes_per_launch": int(nbytes),
-            "launch_ms": round(per_launch_ms, 4), "nnzb": nnzb, "sum_track_len_sq": sumL2}
+    out = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak_gbs,
+           "unit": "GB/s", "frac": round(achieved / peak_gbs, 4),
+           "traffic": measured_traffic(s, name),
+           "peak_source": peak_kind, "bytes_per_launch": int(nbytes),
+           "launch_ms": round(per_launch_ms, 4), "nnzb": nnzb, "sum_track_len_sq": sumL2}
+    if name == "pcg" and mean_pcg > 0:
+        # S is staged in shared memory once per launch, so the per-iteration
+        # bytes above never reach DRAM: the fraction measures the iteration
+        # latency (two grid barriers per iteration), not bandwidth.
+        out["per_iter_us"] = round(per_launch_ms * 1e3 / mean_pcg, 2)
+        out["limiter"] = "grid-barrier latency (S resident in shared memory)"
+    return out
+
+
+PROFILE_KERNELS = os.path.join(ROOT, "profiles", "driving_fp32_kernels.md")
+_PROFILE_NAMES = {"pcg": "k_pcg", "schur": "k_schur", "backsub": "k_backsub",
+                  "lin_cam": "k_lin_cam", "lin_pt": "k_lin_pt", "cost_trial": "k_cost"}
+
+
+def source_digest():
+    """sha256 (first 16 hex digits) of the kernel sources' names and bytes."""
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2510_15271_b300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(s, name):
+    """DRAM bytes per launch of `name` from the committed ncu summary of the
+    driving FP32 workload, or None when the workload differs or the kernel
+    sources changed since the capture."""
+    if s.name != "driving" or name not in _PROFILE_NAMES or not os.path.exists(PROFILE_KERNELS):
+        return None
+    text = open(PROFILE_KERNELS).read()
+    m = re.search(r"Source digest.*?`([0-9a-f]{16})`", text, re.S)
+    if not m or m.group(1) != source_digest():
+        return None
+    for line in text.splitlines():
+        cells = [c.strip() for c in line.strip().strip("|").split("|")]
+        if len(cells) > 4 and cells[0] == _PROFILE_NAMES[name]:
+            return int(cells[4])
+    return None
 
 
 # --------------------------------------------------------------------------- reference arm
