@@ -768,30 +768,35 @@ ba_status ba_kernel_stats(const ba_handle* hc, ba_kernel_stat* out, int32_t max,
   ba_handle* h = const_cast<ba_handle*>(hc);
   if (!h || !out || !n || max < 0) return BA_ERR_INVALID_ARG;
   *n = 0;
-  if (!h->solved || !h->marks.profile) {
-    h->err = "ba_kernel_stats: needs opts.profile = 1 and a finished ba_solve";
-    return BA_ERR_STATE;
-  }
-  double tot[kKindCount] = {};
-  int cnt[kKindCount] = {};
-  cudaEvent_t prev = h->marks.start;
-  for (size_t i = 0; i < h->marks.ev.size(); ++i) {
-    float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, prev, h->marks.ev[i]));
-    tot[h->marks.kind[i]] += ms;
-    cnt[h->marks.kind[i]] += 1;
-    prev = h->marks.ev[i];
-  }
   int w = 0;
-  for (int k = 0; k < kKindCount && w < max; ++k) {
-    if (!cnt[k]) continue;
-    memset(&out[w], 0, sizeof(out[w]));
-    const char* nm = (k == kKSolve) ? (h->cfg.solver == BA_SOLVER_PCG ? "pcg" : "dense_cholesky")
-                                    : kKernelNames[k];
-    strncpy(out[w].name, nm, sizeof(out[w].name) - 1);
-    out[w].launches = cnt[k];
-    out[w].total_ms = tot[k];
-    ++w;
+  if (h->solved && h->marks.profile) {
+    double tot[kKindCount] = {};
+    int cnt[kKindCount] = {};
+    cudaEvent_t prev = h->marks.start;
+    for (size_t i = 0; i < h->marks.ev.size(); ++i) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, prev, h->marks.ev[i]));
+      tot[h->marks.kind[i]] += ms;
+      cnt[h->marks.kind[i]] += 1;
+      prev = h->marks.ev[i];
+    }
+    for (int k = 0; k < kKindCount && w < max; ++k) {
+      if (!cnt[k]) continue;
+      memset(&out[w], 0, sizeof(out[w]));
+      const char* nm = (k == kKSolve) ? (h->cfg.solver == BA_SOLVER_PCG ? "pcg" : "dense_cholesky")
+                                      : kKernelNames[k];
+      strncpy(out[w].name, nm, sizeof(out[w].name) - 1);
+      out[w].launches = cnt[k];
+      out[w].total_ms = tot[k];
+      ++w;
+    }
+  }
+  w += batch_stats(h, out + w, max - w);
+  w += server_stats(h, out + w, max - w);
+  if (w == 0) {
+    h->err = "ba_kernel_stats: needs a finished ba_solve with opts.profile = 1, a batched "
+             "solve, or a serving handle";
+    return BA_ERR_STATE;
   }
   *n = w;
   return BA_OK;

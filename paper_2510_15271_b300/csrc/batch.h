@@ -1,0 +1,107 @@
+// Multi-problem engine shared by the batched (ba_solve_batch) and the served
+// (ba_submit / ba_poll) solvers: many small independent bundle-adjustment
+// problems, each solved whole by one CTA of a persistent kernel with a dense
+// Cholesky of its reduced camera system.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ba_internal.h"
+
+namespace ba {
+
+enum : int { kPhaseSetup = 0, kPhaseIter = 1, kPhaseDone = 2 };
+
+// Validation bit of the multi-problem setup beyond the layout flags.
+constexpr int kDuplicateObs = 128;  // a camera observes one point twice
+// Error bit of a problem too large for the launch's shared memory.
+constexpr int kErrTooLarge = 8;
+
+constexpr int kBatchMaxCams = 512;        // dense S of at most 3072 x 3072
+constexpr int kBatchMaxPts = 1 << 18;     // fixed-shape point sums (256 chunks)
+constexpr int kSumChunk = 1024;           // elements per fixed-shape sum chunk
+constexpr int kSumMaxChunks = 256;
+constexpr int kPanel = 32;                // Cholesky panel width
+constexpr int kBatchMaxThreads = 512;
+
+// One problem, device-resident.  Pointers address the engine's arena.
+struct BProb {
+  int C, P, N, iters;
+  Intrinsics K;
+  int phase, status, error, done_iters;
+  // LM control (FP64)
+  double mu, nu, F, F_new, dL, gain;
+  int need_lin, step_ok, iter, n_accepted;
+  double rmse_s, rmse_n;
+  // inputs (copied in) and outputs
+  const int32_t* raw_cam;
+  const int32_t* raw_pt;
+  const double* raw_uv;
+  const double* cam_qt;
+  const double* pts;
+  const uint8_t* fixed;
+  double* cam_qt_out;  // [C][7]
+  double* pts_out;     // [P][3]
+  // layout: observations sorted by (camera, point); point order (point, camera)
+  int32_t* cam_ptr;  // [C + 1]
+  int32_t* pt_ptr;   // [P + 1]
+  int32_t* oc_pt;    // [N] point of each camera-order observation
+  int32_t* q_of;     // [N] point-order position of each camera-order observation
+  int32_t* po_cam;   // [N] camera of each point-order observation
+  void* po_uv;       // [N][2] T, point order
+  // state (FP64 master, FP32 records on the FP32 path), current and trial
+  double *R, *t, *Cc, *R2, *t2, *Cc2, *X, *X2;
+  float *cam32, *cam32b, *X32, *X32b;
+  // linearisation (T) in point order for W
+  void* W;   // [N][W stride]
+  void* U;   // [C][36]
+  void* gc;  // [C][6]
+  void* V;   // [P][6]
+  void* gp;  // [P][3]
+  void* e;   // [P][3]
+  double* Vinv;  // [P][6]
+  // reduced system (T): dense S [n][n], b, x (n = 6C)
+  void* S;
+  void* b;
+  void* x;
+  double* cpart;  // [2C] per-camera partial sums
+  double* ppart;  // [P] per-point partial sums
+  int32_t* scratch;  // setup scratch (aliases W)
+  double cost[BA_MAX_ITERS + 1];
+  double mu_hist[BA_MAX_ITERS];
+  uint8_t accepted[BA_MAX_ITERS];
+};
+
+// Arguments of one launch of the multi-problem kernel.
+struct BatchRun {
+  BProb* probs;
+  const int32_t* work;  // problem indices, in the order CTAs take them
+  int n_work;
+  unsigned* queue;      // work counter (zeroed before the launch)
+  int iters_per_tick;   // <= 0: run every problem to completion
+  double huber_delta, mu0, mu_min;
+};
+
+// Bytes of arena one problem needs (inputs, outputs, work), 256-aligned parts.
+struct ProbBytes {
+  size_t in, out, work;
+};
+ProbBytes prob_bytes(int precision, int C, int P, int64_t N);
+
+// Point a descriptor's arrays into the given input / output / work blocks.
+void assign_prob(int precision, BProb& p, char* in, char* out, char* work);
+
+// Host image of a problem's input block (what assign_prob puts there), so a
+// packed host buffer can be copied with one transfer.
+void pack_inputs(int precision, const ba_problem& src, char* host_in);
+
+// Dynamic shared memory of the kernel for problems of at most max_cams cameras.
+size_t batch_smem_bytes(int precision, int threads, int max_cams);
+// Occupancy-checked launch of the multi-problem kernel.
+cudaError_t launch_batch(int precision, int threads, int grid, size_t smem, const BatchRun& a,
+                         cudaStream_t s);
+// Largest CTAs per SM the kernel supports with this shared memory.
+int batch_max_ctas_per_sm(int precision, int threads, size_t smem);
+
+}  // namespace ba

@@ -1,0 +1,1084 @@
+// Persistent multi-problem kernel: every CTA takes the next problem from a
+// device work counter and runs it whole — layout, Levenberg-Marquardt
+// iterations with a dense Cholesky of the reduced camera system, final RMSE
+// and output state — so hundreds of uneven local-BA windows share one launch.
+//
+// Per LM iteration of one problem (cuSfM Sec. 4.3 objective; Triggs et al.
+// 2000 normal equations and Schur complement; Madsen, Nielsen & Tingleff 2004
+// damping and gain ratio), all inside the CTA:
+//   lin     warp per camera: U_i, g_c,i;  thread per point: V_j, g_p,j and
+//           W_k = w Jc^T Jp stored in point order
+//   damp    thread per point: V*_j^-1 (FP64), e_j = V*_j^-1 g_p,j
+//   schur   warp per camera row i1: S_i1,i2 (i2 >= i1) = [i1=i2] U*_i1 -
+//           sum_j Y_k1 W_k2^T with Y = W V*^-1, accumulated in a shared-memory
+//           row block in a fixed order; b_i1 = -g_c,i1 + sum W e; mirrored
+//   solve   blocked right-looking Cholesky of the dense S, then two blocked
+//           triangular solves
+//   trial   thread per point: back-substitution dp, X + dp;  thread per
+//           camera: Exp(dc) T; model decrease parts; warp per camera: cost
+//   gain    accept / reject, damping update, commit
+//
+// Every reduction has a fixed shape that depends on the problem alone (warp
+// per camera, thread per point, 1024-element chunks), so a problem's result
+// is bit-identical whatever else is in the launch and whatever the CTA size.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "batch.h"
+
+namespace ba {
+namespace {
+
+template <typename T>
+struct WS;
+template <>
+struct WS<float> {
+  static constexpr int v = kWStrideF32;
+};
+template <>
+struct WS<double> {
+  static constexpr int v = kWStrideF64;
+};
+
+template <typename T>
+__device__ __forceinline__ void ld_w(const T* W, int64_t q, T w[18]) {
+  const T* p = W + q * WS<T>::v;
+#pragma unroll
+  for (int a = 0; a < 18; ++a) w[a] = p[a];
+}
+
+template <>
+__device__ __forceinline__ void ld_w<float>(const float* W, int64_t q, float w[18]) {
+  const float4* p = reinterpret_cast<const float4*>(W + q * kWStrideF32);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float4 v = p[i];
+    w[4 * i] = v.x;
+    w[4 * i + 1] = v.y;
+    w[4 * i + 2] = v.z;
+    w[4 * i + 3] = v.w;
+  }
+  const float2 v = *reinterpret_cast<const float2*>(p + 4);
+  w[16] = v.x;
+  w[17] = v.y;
+}
+
+template <typename T>
+__device__ __forceinline__ void st_w(T* W, int64_t q, const T w[18]) {
+  T* p = W + q * WS<T>::v;
+#pragma unroll
+  for (int a = 0; a < 18; ++a) p[a] = w[a];
+}
+
+template <>
+__device__ __forceinline__ void st_w<float>(float* W, int64_t q, const float w[18]) {
+  float4* p = reinterpret_cast<float4*>(W + q * kWStrideF32);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) p[i] = make_float4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
+  p[4] = make_float4(w[16], w[17], 0.f, 0.f);
+}
+
+// State access of one problem (current or trial).  Plain loads: the arrays
+// are written earlier in the same launch.
+template <typename T>
+struct PV;
+
+template <>
+struct PV<double> {
+  const double *R, *t, *X;
+  struct Cam {
+    double R[9], t[3];
+  };
+  __device__ PV(const BProb& p, bool trial)
+      : R(trial ? p.R2 : p.R), t(trial ? p.t2 : p.t), X(trial ? p.X2 : p.X) {}
+  __device__ __forceinline__ void cam(int i, Cam& c) const {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) c.R[a] = R[9 * i + a];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) c.t[a] = t[3 * i + a];
+  }
+  __device__ __forceinline__ void xc(const Cam& c, int j, double out[3]) const {
+    to_camera64(c.R, c.t, X[3 * j], X[3 * j + 1], X[3 * j + 2], out);
+  }
+  __device__ __forceinline__ static const double* rot(const Cam& c) { return c.R; }
+};
+
+template <>
+struct PV<float> {
+  const float *C, *X;
+  struct Cam {
+    float v[kCam32];
+  };
+  __device__ PV(const BProb& p, bool trial) : C(trial ? p.cam32b : p.cam32), X(trial ? p.X32b : p.X32) {}
+  __device__ __forceinline__ void cam(int i, Cam& c) const {
+    const float4* p = reinterpret_cast<const float4*>(C + kCam32 * i);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 v = p[q];
+      c.v[4 * q] = v.x;
+      c.v[4 * q + 1] = v.y;
+      c.v[4 * q + 2] = v.z;
+      c.v[4 * q + 3] = v.w;
+    }
+  }
+  __device__ __forceinline__ void xc(const Cam& c, int j, float out[3]) const {
+    const float2* p = reinterpret_cast<const float2*>(X + kPt32 * j);
+    const float2 a = p[0], b = p[1], e = p[2];
+    const float pt[6] = {a.x, a.y, b.x, b.y, e.x, e.y};
+    to_camera32(c.v, pt, out);
+  }
+  __device__ __forceinline__ static const float* rot(const Cam& c) { return c.v; }
+};
+
+// Sum of v[0..n) with a shape fixed by n alone: chunks of kSumChunk elements,
+// lane l of one warp sums elements l, l+32, ... of a chunk in order, then a
+// butterfly over the lanes; the chunk sums are added in order by every
+// thread.  All threads return the same value.
+__device__ double fixed_sum(const double* v, int n, double* s_chunks) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nch = (n + kSumChunk - 1) / kSumChunk;
+  for (int c = warp; c < nch; c += nw) {
+    double a = 0.0;
+    const int base = c * kSumChunk;
+    for (int m = 0; m < kSumChunk / 32; ++m) {
+      const int i = base + 32 * m + lane;
+      if (i < n) a += v[i];
+    }
+    a = warp_sum(a);
+    if (lane == 0) s_chunks[c] = a;
+  }
+  __syncthreads();
+  double tot = 0.0;
+  for (int c = 0; c < nch; ++c) tot += s_chunks[c];
+  __syncthreads();
+  return tot;
+}
+
+// In-place exclusive prefix sum of a[0..m) (global memory) by the whole CTA.
+__device__ void cta_exclusive_scan(int32_t* a, int m, int* s_warp) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int carry = 0;
+  for (int base = 0; base < m; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const int v = i < m ? a[i] : 0;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      int w = lane < nw ? s_warp[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      if (lane < nw) s_warp[lane] = w;
+    }
+    __syncthreads();
+    const int woff = warp > 0 ? s_warp[warp - 1] : 0;
+    const int total = s_warp[nw - 1];
+    if (i < m) a[i] = carry + woff + x - v;
+    carry += total;
+    __syncthreads();
+  }
+}
+
+struct Smem {
+  double chunks[kSumMaxChunks];
+  int scan[32];
+  int flag;
+  int item;
+  int ok;
+};
+
+// --------------------------------------------------------------------------- setup
+
+// Validate the inputs, sort the observations by (camera, point) and by
+// (point, camera) with stable counting sorts, and load the state.  Sets
+// p.status (0 or validation bits).
+template <typename T>
+__device__ void setup_problem(BProb& p, Smem& sm) {
+  const int C = p.C, P = p.P, N = p.N;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  int32_t* cam_cnt = p.cam_ptr;
+  int32_t* pt_cnt = p.pt_ptr;
+  for (int i = tid; i <= C; i += NT) cam_cnt[i] = 0;
+  for (int j = tid; j <= P; j += NT) pt_cnt[j] = 0;
+  if (tid == 0) sm.flag = 0;
+  __syncthreads();
+  int bad = 0;
+  for (int k = tid; k < N; k += NT) {
+    const int c = p.raw_cam[k], j = p.raw_pt[k];
+    const double u = p.raw_uv[2 * (int64_t)k], v = p.raw_uv[2 * (int64_t)k + 1];
+    const bool okc = c >= 0 && c < C, okp = j >= 0 && j < P;
+    if (!okc) bad |= kBadCamIndex;
+    if (!okp) bad |= kBadPtIndex;
+    if (!isfinite(u) || !isfinite(v)) bad |= kBadUv;
+    if (okc) atomicAdd(&cam_cnt[c], 1);
+    if (okp) atomicAdd(&pt_cnt[j], 1);
+  }
+  if (bad) atomicOr(&sm.flag, bad);
+  __syncthreads();
+  bad = 0;
+  for (int i = tid; i < C; i += NT) {
+    double q2 = 0.0;
+    bool fin = true;
+    for (int a = 0; a < 7; ++a) {
+      const double v = p.cam_qt[7 * i + a];
+      fin = fin && isfinite(v);
+      if (a < 4) q2 += v * v;
+    }
+    if (!fin || !(q2 > 1e-30)) bad |= kBadCamPose;
+    if (cam_cnt[i] == 0 && !p.fixed[i]) bad |= kCameraUnobserved;
+  }
+  for (int j = tid; j < P; j += NT) {
+    const double x = p.pts[3 * j], y = p.pts[3 * j + 1], z = p.pts[3 * j + 2];
+    if (!isfinite(x) || !isfinite(y) || !isfinite(z)) bad |= kBadPoint;
+    if (pt_cnt[j] < 2) bad |= kPointUnderObserved;
+  }
+  if (bad) atomicOr(&sm.flag, bad);
+  __syncthreads();
+  if (sm.flag) {
+    if (tid == 0) p.status = sm.flag;
+    __syncthreads();
+    return;
+  }
+  cta_exclusive_scan(cam_cnt, C + 1, sm.scan);  // -> cam_ptr
+  cta_exclusive_scan(pt_cnt, P + 1, sm.scan);   // -> pt_ptr
+  // point buckets (arbitrary order inside a bucket, fixed below)
+  int32_t* pt_cur = p.scratch;
+  int32_t* po_orig = pt_cur + P;
+  int32_t* tcnt = po_orig + N;
+  for (int j = tid; j < P; j += NT) pt_cur[j] = p.pt_ptr[j];
+  __syncthreads();
+  for (int k = tid; k < N; k += NT) po_orig[atomicAdd(&pt_cur[p.raw_pt[k]], 1)] = k;
+  __syncthreads();
+  // each bucket by (camera, original index): insertion sort, one thread per point
+  bad = 0;
+  for (int j = tid; j < P; j += NT) {
+    const int q0 = p.pt_ptr[j], q1 = p.pt_ptr[j + 1];
+    for (int a = q0 + 1; a < q1; ++a) {
+      const int k = po_orig[a];
+      const int ck = p.raw_cam[k];
+      int b = a - 1;
+      while (b >= q0) {
+        const int kb = po_orig[b];
+        const int cb = p.raw_cam[kb];
+        if (cb < ck || (cb == ck && kb < k)) break;
+        po_orig[b + 1] = kb;
+        --b;
+      }
+      po_orig[b + 1] = k;
+    }
+    for (int a = q0 + 1; a < q1; ++a)
+      if (p.raw_cam[po_orig[a]] == p.raw_cam[po_orig[a - 1]]) bad |= kDuplicateObs;
+  }
+  if (bad) atomicOr(&sm.flag, bad);
+  __syncthreads();
+  if (sm.flag) {
+    if (tid == 0) p.status = sm.flag;
+    __syncthreads();
+    return;
+  }
+  // stable scatter of the point order into camera order: thread t owns the
+  // positions [t*tile, (t+1)*tile) and its own row of per-camera counters
+  const int tile = (N + NT - 1) / NT;
+  for (int e = tid; e < NT * C; e += NT) tcnt[e] = 0;
+  __syncthreads();
+  {
+    const int q0 = tid * tile, q1 = min(N, q0 + tile);
+    for (int q = q0; q < q1; ++q) tcnt[tid * C + p.raw_cam[po_orig[q]]] += 1;
+  }
+  __syncthreads();
+  for (int c = tid; c < C; c += NT) {
+    int run = p.cam_ptr[c];
+    for (int t = 0; t < NT; ++t) {
+      const int v = tcnt[t * C + c];
+      tcnt[t * C + c] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+  {
+    T* uvo = (T*)p.po_uv;
+    const int q0 = tid * tile, q1 = min(N, q0 + tile);
+    for (int q = q0; q < q1; ++q) {
+      const int k = po_orig[q];
+      const int c = p.raw_cam[k];
+      const int r = tcnt[tid * C + c]++;
+      p.oc_pt[r] = p.raw_pt[k];
+      p.q_of[r] = q;
+      p.po_cam[q] = c;
+      uvo[2 * (int64_t)q] = (T)p.raw_uv[2 * (int64_t)k];
+      uvo[2 * (int64_t)q + 1] = (T)p.raw_uv[2 * (int64_t)k + 1];
+    }
+  }
+  // state
+  for (int i = tid; i < C; i += NT) {
+    const double* qt = p.cam_qt + 7 * i;
+    const double q[4] = {qt[0], qt[1], qt[2], qt[3]};
+    double R[9], tt[3] = {qt[4], qt[5], qt[6]}, Cc[3];
+    quat_to_rot(q, R);
+    camera_centre(R, tt, Cc);
+    for (int a = 0; a < 9; ++a) p.R[9 * i + a] = R[a];
+    for (int a = 0; a < 3; ++a) {
+      p.t[3 * i + a] = tt[a];
+      p.Cc[3 * i + a] = Cc[a];
+    }
+    if (p.cam32) write_cam32(R, Cc, p.cam32 + kCam32 * i);
+  }
+  for (int j = tid; j < P; j += NT) {
+    const double x = p.pts[3 * j], y = p.pts[3 * j + 1], z = p.pts[3 * j + 2];
+    p.X[3 * j] = x;
+    p.X[3 * j + 1] = y;
+    p.X[3 * j + 2] = z;
+    if (p.X32) write_pt32(x, y, z, p.X32 + kPt32 * j);
+  }
+  __syncthreads();
+  if (tid == 0) p.status = 0;
+  __syncthreads();
+}
+
+// --------------------------------------------------------------------------- passes
+
+// mode 0: cpart[i] = sum over camera i of 1/2 rho(s) at the current or trial
+// state; mode 1: cpart[i] = sum s, cpart[C + i] = valid count.  Warp per camera.
+template <typename T>
+__device__ void cost_pass(const BProb& p, bool trial, T delta, int mode) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const PV<T> view(p, trial);
+  const T* uv = (const T*)p.po_uv;
+  for (int i = warp; i < p.C; i += nw) {
+    typename PV<T>::Cam cam;
+    view.cam(i, cam);
+    double acc = 0.0, nv = 0.0;
+    for (int k = p.cam_ptr[i] + lane; k < p.cam_ptr[i + 1]; k += 32) {
+      const int j = p.oc_pt[k];
+      const int64_t q = p.q_of[k];
+      T xc[3];
+      view.xc(cam, j, xc);
+      T r0, r1;
+      if (!residual<T>(xc, uv[2 * q], uv[2 * q + 1], p.K, r0, r1)) continue;
+      const T s = fma_rn(r0, r0, mul_rn(r1, r1));
+      if (mode == 0) {
+        acc += 0.5 * (double)huber_rho<T>(s, delta);
+      } else {
+        acc += (double)s;
+        nv += 1.0;
+      }
+    }
+    acc = warp_sum(acc);
+    nv = warp_sum(nv);
+    if (lane == 0) {
+      p.cpart[i] = acc;
+      if (mode == 1) p.cpart[p.C + i] = nv;
+    }
+  }
+}
+
+// U_i, g_c,i: warp per camera.
+template <typename T>
+__device__ void lin_cams(const BProb& p, T delta) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const PV<T> view(p, false);
+  const T* uv = (const T*)p.po_uv;
+  for (int i = warp; i < p.C; i += nw) {
+    T acc[27];
+#pragma unroll
+    for (int a = 0; a < 27; ++a) acc[a] = T(0);
+    if (!p.fixed[i]) {
+      typename PV<T>::Cam cam;
+      view.cam(i, cam);
+      for (int k = p.cam_ptr[i] + lane; k < p.cam_ptr[i + 1]; k += 32) {
+        const int j = p.oc_pt[k];
+        const int64_t q = p.q_of[k];
+        T xc[3];
+        view.xc(cam, j, xc);
+        T r0, r1;
+        if (!residual<T>(xc, uv[2 * q], uv[2 * q + 1], p.K, r0, r1)) continue;
+        const T s = fma_rn(r0, r0, mul_rn(r1, r1));
+        const T w = huber_weight<T>(s, delta);
+        T Jc[2][6], Jp[2][3];
+        jacobians<T>(xc, PV<T>::rot(cam), p.K, Jc, Jp);
+        int u_idx = 0;
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+          const T wa0 = w * Jc[0][a], wa1 = w * Jc[1][a];
+#pragma unroll
+          for (int bb = a; bb < 6; ++bb) {
+            acc[u_idx] += wa0 * Jc[0][bb] + wa1 * Jc[1][bb];
+            ++u_idx;
+          }
+          acc[21 + a] += wa0 * r0 + wa1 * r1;
+        }
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 27; ++a) acc[a] = warp_sum(acc[a]);
+    if (lane == 0) {
+      T* U = (T*)p.U + 36 * i;
+      int u_idx = 0;
+#pragma unroll
+      for (int a = 0; a < 6; ++a)
+#pragma unroll
+        for (int bb = a; bb < 6; ++bb) {
+          U[6 * a + bb] = acc[u_idx];
+          U[6 * bb + a] = acc[u_idx];
+          ++u_idx;
+        }
+      T* g = (T*)p.gc + 6 * i;
+#pragma unroll
+      for (int a = 0; a < 6; ++a) g[a] = acc[21 + a];
+    }
+  }
+}
+
+// V_j, g_p,j and the point-ordered W blocks: thread per point.
+template <typename T>
+__device__ void lin_pts(const BProb& p, T delta) {
+  const PV<T> view(p, false);
+  const T* uv = (const T*)p.po_uv;
+  T* Wg = (T*)p.W;
+  for (int j = threadIdx.x; j < p.P; j += blockDim.x) {
+    T V[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    T g[3] = {T(0), T(0), T(0)};
+    for (int q = p.pt_ptr[j]; q < p.pt_ptr[j + 1]; ++q) {
+      const int c = p.po_cam[q];
+      typename PV<T>::Cam cam;
+      view.cam(c, cam);
+      T xc[3];
+      view.xc(cam, j, xc);
+      T r0, r1;
+      T Wk[18];
+#pragma unroll
+      for (int a = 0; a < 18; ++a) Wk[a] = T(0);
+      if (residual<T>(xc, uv[2 * (int64_t)q], uv[2 * (int64_t)q + 1], p.K, r0, r1)) {
+        const T s = fma_rn(r0, r0, mul_rn(r1, r1));
+        const T w = huber_weight<T>(s, delta);
+        T Jc[2][6], Jp[2][3];
+        jacobians<T>(xc, PV<T>::rot(cam), p.K, Jc, Jp);
+        const T a0 = w * Jp[0][0], a1 = w * Jp[0][1], a2 = w * Jp[0][2];
+        const T b0 = w * Jp[1][0], b1 = w * Jp[1][1], b2 = w * Jp[1][2];
+        V[0] += a0 * Jp[0][0] + b0 * Jp[1][0];
+        V[1] += a0 * Jp[0][1] + b0 * Jp[1][1];
+        V[2] += a0 * Jp[0][2] + b0 * Jp[1][2];
+        V[3] += a1 * Jp[0][1] + b1 * Jp[1][1];
+        V[4] += a1 * Jp[0][2] + b1 * Jp[1][2];
+        V[5] += a2 * Jp[0][2] + b2 * Jp[1][2];
+        g[0] += a0 * r0 + b0 * r1;
+        g[1] += a1 * r0 + b1 * r1;
+        g[2] += a2 * r0 + b2 * r1;
+        if (!p.fixed[c]) {
+#pragma unroll
+          for (int a = 0; a < 6; ++a) {
+            const T wa0 = w * Jc[0][a], wa1 = w * Jc[1][a];
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) Wk[3 * a + cc] = wa0 * Jp[0][cc] + wa1 * Jp[1][cc];
+          }
+        }
+      }
+      st_w<T>(Wg, q, Wk);
+    }
+    T* Vo = (T*)p.V + 6 * j;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) Vo[a] = V[a];
+    T* go = (T*)p.gp + 3 * j;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) go[a] = g[a];
+  }
+}
+
+// V*_j = V_j + mu diag(V_j) (diagonal floored), its FP64 inverse, e = V*^-1 g_p.
+template <typename T>
+__device__ void damp_pts(const BProb& p, double mu) {
+  for (int j = threadIdx.x; j < p.P; j += blockDim.x) {
+    const T* Vi = (const T*)p.V + 6 * j;
+    double m[6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) m[a] = (double)Vi[a];
+    m[0] += mu * fmax(m[0], kDiagMin);
+    m[3] += mu * fmax(m[3], kDiagMin);
+    m[5] += mu * fmax(m[5], kDiagMin);
+    double inv[6];
+    sym3_inverse(m, inv);
+    double* out = p.Vinv + 6 * j;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) out[a] = inv[a];
+    const T* g = (const T*)p.gp + 3 * j;
+    const double g0 = g[0], g1 = g[1], g2 = g[2];
+    T* e = (T*)p.e + 3 * j;
+    e[0] = (T)(inv[0] * g0 + inv[1] * g1 + inv[2] * g2);
+    e[1] = (T)(inv[1] * g0 + inv[3] * g1 + inv[4] * g2);
+    e[2] = (T)(inv[2] * g0 + inv[4] * g1 + inv[5] * g2);
+  }
+}
+
+// Shared memory one Schur row warp uses: the 6 x n row block and Y of 32
+// observations.
+template <typename T>
+__host__ __device__ inline size_t row_warp_bytes(int C) {
+  return ((size_t)6 * 6 * C + 32 * 18) * sizeof(T);
+}
+
+// Row blocks of S and b.  Warp w < nrw handles camera rows w, w + nrw, ...
+// The row's observations k1 are taken 32 at a time (lane l computes Y_k1 =
+// W_k1 V*_j^-1 for its own k1); then, k1 by k1 in order, lanes (p, c) =
+// (lane / 6, lane % 6) add Y_k1 W_k2[c]^T for partner p of k1 (the point's
+// observations in cameras >= i1, all in distinct cameras) into column
+// 6 cam(k2) + c of the row block.  Each output element is updated by one
+// lane at a time in a fixed order.
+template <typename T>
+__device__ void schur_rows(const BProb& p, double mu, T* rows, int nrw) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp >= nrw) return;
+  const int C = p.C, n = 6 * C;
+  T* acc = rows + (size_t)warp * (row_warp_bytes<T>(C) / sizeof(T));
+  T* Ys = acc + (size_t)6 * n;
+  const T* W = (const T*)p.W;
+  const T* eg = (const T*)p.e;
+  const int pg = lane / 6, pc = lane - 6 * (lane / 6);
+  for (int i1 = warp; i1 < C; i1 += nrw) {
+    const bool fixed1 = p.fixed[i1] != 0;
+    for (int e = lane; e < 6 * n; e += 32) acc[e] = T(0);
+    __syncwarp();
+    double bsum = 0.0;  // lane r < 6: row r of sum_k W_k e_j
+    const int kb = p.cam_ptr[i1], ke = p.cam_ptr[i1 + 1];
+    if (!fixed1) {
+      for (int base = kb; base < ke; base += 32) {
+        const int k1 = base + lane;
+        int q1 = 0, qe = 0;
+        double bl[6] = {0, 0, 0, 0, 0, 0};
+        if (k1 < ke) {
+          const int j = p.oc_pt[k1];
+          q1 = p.q_of[k1];
+          qe = p.pt_ptr[j + 1];
+          T Wk[18];
+          ld_w<T>(W, q1, Wk);
+          const double* vi = p.Vinv + 6 * j;
+          const T v00 = (T)vi[0], v01 = (T)vi[1], v02 = (T)vi[2], v11 = (T)vi[3], v12 = (T)vi[4],
+                  v22 = (T)vi[5];
+          const T e0 = eg[3 * j], e1 = eg[3 * j + 1], e2 = eg[3 * j + 2];
+          T* Y = Ys + 18 * lane;
+#pragma unroll
+          for (int a = 0; a < 6; ++a) {
+            const T w0 = Wk[3 * a], w1 = Wk[3 * a + 1], w2 = Wk[3 * a + 2];
+            Y[3 * a] = w0 * v00 + w1 * v01 + w2 * v02;
+            Y[3 * a + 1] = w0 * v01 + w1 * v11 + w2 * v12;
+            Y[3 * a + 2] = w0 * v02 + w1 * v12 + w2 * v22;
+            bl[a] = (double)(w0 * e0 + w1 * e1 + w2 * e2);
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+          const double s = warp_sum(bl[a]);
+          if (lane == a) bsum += s;
+        }
+        __syncwarp();
+        const int nb = min(32, ke - base);
+        for (int t = 0; t < nb; ++t) {
+          const int tq1 = __shfl_sync(0xffffffffu, q1, t);
+          const int m = __shfl_sync(0xffffffffu, qe, t) - tq1;
+          const T* Y = Ys + 18 * t;
+          for (int p0 = 0; p0 < m; p0 += 5) {
+            const int pi = p0 + pg;
+            if (lane < 30 && pi < m) {
+              const int q2 = tq1 + pi;
+              const int c2 = p.po_cam[q2];
+              const T* w2 = W + (int64_t)q2 * WS<T>::v + 3 * pc;
+              const T wa = w2[0], wb = w2[1], wc = w2[2];
+              T* out = acc + 6 * c2 + pc;
+#pragma unroll
+              for (int r = 0; r < 6; ++r)
+                out[r * n] += Y[3 * r] * wa + Y[3 * r + 1] * wb + Y[3 * r + 2] * wc;
+            }
+          }
+          __syncwarp();
+        }
+      }
+    }
+    // write the row block (upper part) and its mirror
+    const T* U = (const T*)p.U + 36 * i1;
+    T* S = (T*)p.S;
+    for (int e = lane; e < 6 * n; e += 32) {
+      const int r = e / n, col = e - r * n;
+      const int i2 = col / 6, c = col - 6 * i2;
+      if (i2 < i1) continue;
+      T val;
+      if (fixed1) {
+        val = (i2 == i1 && r == c) ? T(1) : T(0);
+      } else {
+        val = -acc[e];
+        if (i2 == i1) {
+          T u = U[6 * r + c];
+          if (r == c) u = (T)((double)u + mu * fmax((double)u, kDiagMin));
+          val += u;
+        }
+      }
+      S[(int64_t)(6 * i1 + r) * n + col] = val;
+      if (i2 > i1) S[(int64_t)col * n + 6 * i1 + r] = val;
+    }
+    if (lane < 6) {
+      const double gci = (double)((const T*)p.gc)[6 * i1 + lane];
+      const double bi = fixed1 ? 0.0 : (-gci + bsum);
+      ((T*)p.b)[6 * i1 + lane] = (T)bi;
+      ((T*)p.x)[6 * i1 + lane] = (T)bi;
+    }
+    __syncwarp();
+  }
+}
+
+// Blocked right-looking Cholesky S = L L^T in place (lower triangle), panel
+// width kPanel: warp 0 factors the diagonal block in shared memory, every
+// thread then solves rows of the panel below it and updates 4 x 4 tiles of
+// the trailing lower triangle.  Returns false on a non-positive pivot.
+template <typename T>
+__device__ bool cholesky(T* A, int n, T* sd, Smem& sm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NT = blockDim.x;
+  constexpr int LD = kPanel + 1;
+  if (threadIdx.x == 0) sm.ok = 1;
+  __syncthreads();
+  for (int jb = 0; jb < n; jb += kPanel) {
+    const int pb = min(kPanel, n - jb);
+    if (warp == 0) {
+      if (lane < pb)
+        for (int c = 0; c <= lane; ++c) sd[lane * LD + c] = A[(int64_t)(jb + lane) * n + jb + c];
+      __syncwarp();
+      for (int j = 0; j < pb; ++j) {
+        if (lane == j) {
+          T d = sd[j * LD + j];
+          if (!(d > T(0)) || !isfinite((double)d)) {
+            sm.ok = 0;
+            d = T(1);
+          }
+          sd[j * LD + j] = sqrt(d);
+        }
+        __syncwarp();
+        const T ljj = sd[j * LD + j];
+        if (lane > j && lane < pb) sd[lane * LD + j] /= ljj;
+        __syncwarp();
+        if (lane > j && lane < pb) {
+          const T lrj = sd[lane * LD + j];
+          for (int c = j + 1; c <= lane; ++c) sd[lane * LD + c] -= lrj * sd[c * LD + j];
+        }
+        __syncwarp();
+      }
+      if (lane < pb)
+        for (int c = 0; c <= lane; ++c) A[(int64_t)(jb + lane) * n + jb + c] = sd[lane * LD + c];
+    }
+    __syncthreads();
+    if (!sm.ok) return false;
+    // panel rows below the diagonal block: x L_d^T = a
+    for (int i = jb + pb + threadIdx.x; i < n; i += NT) {
+      T* a = A + (int64_t)i * n + jb;
+      T xr[kPanel];
+#pragma unroll
+      for (int c = 0; c < kPanel; ++c) {
+        if (c < pb) {
+          T s = a[c];
+          for (int m = 0; m < c; ++m) s -= xr[m] * sd[c * LD + m];
+          xr[c] = s / sd[c * LD + c];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < kPanel; ++c)
+        if (c < pb) a[c] = xr[c];
+    }
+    __syncthreads();
+    const int m0 = jb + pb, rem = n - m0;
+    if (rem > 0) {
+      const int nt = (rem + 3) / 4;
+      const int ntiles = nt * (nt + 1) / 2;
+      for (int tt = threadIdx.x; tt < ntiles; tt += NT) {
+        int ti = (int)((sqrt(8.0 * tt + 1.0) - 1.0) * 0.5);
+        while ((ti + 1) * (ti + 2) / 2 <= tt) ++ti;
+        while (ti * (ti + 1) / 2 > tt) --ti;
+        const int tk = tt - ti * (ti + 1) / 2;
+        const int i0 = m0 + 4 * ti, k0 = m0 + 4 * tk;
+        T acc[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[r][c] = T(0);
+        const T* Ai[4];
+        const T* Ak[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          Ai[r] = A + (int64_t)min(i0 + r, n - 1) * n + jb;
+          Ak[r] = A + (int64_t)min(k0 + r, n - 1) * n + jb;
+        }
+        for (int m = 0; m < pb; ++m) {
+          T a[4], b[4];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            a[r] = Ai[r][m];
+            b[r] = Ak[r][m];
+          }
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[r][c] += a[r] * b[c];
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int i = i0 + r, k = k0 + c;
+            if (i < n && k <= i) A[(int64_t)i * n + k] -= acc[r][c];
+          }
+      }
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+// x <- L^-T L^-1 x with blocks of 32: warp 0 solves each diagonal block with
+// shuffles, all threads apply it to the remaining rows.
+template <typename T>
+__device__ void chol_solve(const T* A, int n, T* x) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NT = blockDim.x;
+  for (int jb = 0; jb < n; jb += 32) {
+    const int pb = min(32, n - jb);
+    if (warp == 0) {
+      T yr = lane < pb ? x[jb + lane] : T(0);
+      for (int j = 0; j < pb; ++j) {
+        if (lane == j) yr = yr / A[(int64_t)(jb + j) * n + jb + j];
+        const T yj = __shfl_sync(0xffffffffu, yr, j);
+        if (lane > j && lane < pb) yr -= A[(int64_t)(jb + lane) * n + jb + j] * yj;
+      }
+      if (lane < pb) x[jb + lane] = yr;
+    }
+    __syncthreads();
+    for (int i = jb + pb + threadIdx.x; i < n; i += NT) {
+      const T* a = A + (int64_t)i * n + jb;
+      T s = x[i];
+      for (int m = 0; m < pb; ++m) s -= a[m] * x[jb + m];
+      x[i] = s;
+    }
+    __syncthreads();
+  }
+  for (int jb = ((n - 1) / 32) * 32; jb >= 0; jb -= 32) {
+    const int pb = min(32, n - jb);
+    if (warp == 0) {
+      T xr = lane < pb ? x[jb + lane] : T(0);
+      for (int j = pb - 1; j >= 0; --j) {
+        if (lane == j) xr = xr / A[(int64_t)(jb + j) * n + jb + j];
+        const T xj = __shfl_sync(0xffffffffu, xr, j);
+        if (lane < j) xr -= A[(int64_t)(jb + j) * n + jb + lane] * xj;
+      }
+      if (lane < pb) x[jb + lane] = xr;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < jb; i += NT) {
+      T s = x[i];
+      for (int m = 0; m < pb; ++m) s -= A[(int64_t)(jb + m) * n + i] * x[jb + m];
+      x[i] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// Trial points (back-substitution) and the point part of the model decrease
+// into ppart[j]: thread per point.
+template <typename T>
+__device__ void backsub_pts(const BProb& p, double mu) {
+  const T* Wg = (const T*)p.W;
+  const T* dc = (const T*)p.x;
+  for (int j = threadIdx.x; j < p.P; j += blockDim.x) {
+    const T* gp = (const T*)p.gp + 3 * j;
+    T rhs0 = -gp[0], rhs1 = -gp[1], rhs2 = -gp[2];
+    for (int q = p.pt_ptr[j]; q < p.pt_ptr[j + 1]; ++q) {
+      const int c = p.po_cam[q];
+      if (p.fixed[c]) continue;
+      T Wk[18];
+      ld_w<T>(Wg, q, Wk);
+      const T* xv = dc + 6 * c;
+#pragma unroll
+      for (int a = 0; a < 6; ++a) {
+        const T xa = xv[a];
+        rhs0 -= Wk[3 * a] * xa;
+        rhs1 -= Wk[3 * a + 1] * xa;
+        rhs2 -= Wk[3 * a + 2] * xa;
+      }
+    }
+    const double* vi = p.Vinv + 6 * j;
+    const double r0 = rhs0, r1 = rhs1, r2 = rhs2;
+    const double p0 = vi[0] * r0 + vi[1] * r1 + vi[2] * r2;
+    const double p1 = vi[1] * r0 + vi[3] * r1 + vi[4] * r2;
+    const double p2 = vi[2] * r0 + vi[4] * r1 + vi[5] * r2;
+    const double n0 = p.X[3 * j] + p0, n1 = p.X[3 * j + 1] + p1, n2 = p.X[3 * j + 2] + p2;
+    p.X2[3 * j] = n0;
+    p.X2[3 * j + 1] = n1;
+    p.X2[3 * j + 2] = n2;
+    if (p.X32b) write_pt32(n0, n1, n2, p.X32b + kPt32 * j);
+    const T* V = (const T*)p.V + 6 * j;
+    const double D0 = fmax((double)V[0], kDiagMin), D1 = fmax((double)V[3], kDiagMin),
+                 D2 = fmax((double)V[5], kDiagMin);
+    p.ppart[j] = p0 * (mu * D0 * p0 - (double)gp[0]) + p1 * (mu * D1 * p1 - (double)gp[1]) +
+                 p2 * (mu * D2 * p2 - (double)gp[2]);
+  }
+}
+
+// Trial poses Exp(dc_i) T_i and the camera part of the model decrease into
+// cpart[C + i]: thread per camera.
+template <typename T>
+__device__ void retract_cams(const BProb& p, double mu) {
+  for (int i = threadIdx.x; i < p.C; i += blockDim.x) {
+    const T* xv = (const T*)p.x + 6 * i;
+    const bool fixed = p.fixed[i] != 0;
+    double xi[6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) xi[a] = fixed ? 0.0 : (double)xv[a];
+    double R2[9], t2[3], C2[3];
+    se3_left_retract(xi, p.R + 9 * i, p.t + 3 * i, R2, t2);
+    camera_centre(R2, t2, C2);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) p.R2[9 * i + a] = R2[a];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      p.t2[3 * i + a] = t2[a];
+      p.Cc2[3 * i + a] = C2[a];
+    }
+    if (p.cam32b) write_cam32(R2, C2, p.cam32b + kCam32 * i);
+    double part = 0.0;
+    if (!fixed) {
+      const T* U = (const T*)p.U + 36 * i;
+      const T* g = (const T*)p.gc + 6 * i;
+#pragma unroll
+      for (int a = 0; a < 6; ++a) {
+        const double D = fmax((double)U[7 * a], kDiagMin);
+        part += xi[a] * (mu * D * xi[a] - (double)g[a]);
+      }
+    }
+    p.cpart[p.C + i] = part;
+  }
+}
+
+__device__ void commit_state(const BProb& p) {
+  for (int i = threadIdx.x; i < p.C; i += blockDim.x) {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) p.R[9 * i + a] = p.R2[9 * i + a];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      p.t[3 * i + a] = p.t2[3 * i + a];
+      p.Cc[3 * i + a] = p.Cc2[3 * i + a];
+    }
+    if (p.cam32)
+#pragma unroll
+      for (int a = 0; a < kCam32; ++a) p.cam32[kCam32 * i + a] = p.cam32b[kCam32 * i + a];
+  }
+  for (int j = threadIdx.x; j < p.P; j += blockDim.x) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) p.X[3 * j + a] = p.X2[3 * j + a];
+    if (p.X32)
+#pragma unroll
+      for (int a = 0; a < kPt32; ++a) p.X32[kPt32 * j + a] = p.X32b[kPt32 * j + a];
+  }
+}
+
+// --------------------------------------------------------------------------- LM driver
+
+template <typename T>
+__device__ void lm_begin(BProb& p, const BatchRun& a, Smem& sm) {
+  cost_pass<T>(p, false, (T)a.huber_delta, 0);
+  __syncthreads();
+  const double F = fixed_sum(p.cpart, p.C, sm.chunks);
+  if (threadIdx.x == 0) {
+    p.F = F;
+    p.mu = fmax(a.mu0, a.mu_min);
+    p.nu = 2.0;
+    p.need_lin = 1;
+    p.step_ok = 1;
+    p.iter = 0;
+    p.n_accepted = 0;
+    p.error = isfinite(F) ? 0 : kErrNonFinite;
+    p.cost[0] = F;
+    p.phase = kPhaseIter;
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ void lm_iteration(BProb& p, const BatchRun& a, Smem& sm, T* dyn, int nrw) {
+  const T delta = (T)a.huber_delta;
+  const double mu = fmax(p.mu, a.mu_min);  // damping of the linear system
+  if (p.need_lin) {
+    lin_cams<T>(p, delta);
+    lin_pts<T>(p, delta);
+    __syncthreads();
+  }
+  damp_pts<T>(p, mu);
+  __syncthreads();
+  schur_rows<T>(p, mu, dyn, nrw);
+  __syncthreads();
+  const int n = 6 * p.C;
+  const bool ok = cholesky<T>((T*)p.S, n, dyn, sm);
+  double Fn = 0.0, hp = 0.0, hc = 0.0;
+  if (ok) {
+    chol_solve<T>((const T*)p.S, n, (T*)p.x);
+    backsub_pts<T>(p, mu);
+    retract_cams<T>(p, mu);
+    __syncthreads();
+    hp = fixed_sum(p.ppart, p.P, sm.chunks);
+    hc = fixed_sum(p.cpart + p.C, p.C, sm.chunks);
+    cost_pass<T>(p, true, delta, 0);
+    __syncthreads();
+    Fn = fixed_sum(p.cpart, p.C, sm.chunks);
+  }
+  if (threadIdx.x == 0) {
+    const int it = p.iter;
+    const double dL = 0.5 * (hp + hc);
+    const bool good = ok && isfinite(Fn) && isfinite(dL) && dL > 0.0;
+    const double gain = good ? (p.F - Fn) / dL : -INFINITY;
+    p.mu_hist[it] = p.mu;
+    p.F_new = Fn;
+    p.dL = dL;
+    p.gain = gain;
+    p.step_ok = ok ? 1 : 0;
+    if (good && gain > 0.0) {
+      p.F = Fn;
+      const double t = 2.0 * gain - 1.0;
+      p.mu = fmax(p.mu * fmax(1.0 / 3.0, 1.0 - t * t * t), a.mu_min);
+      p.nu = 2.0;
+      p.need_lin = 1;
+      p.n_accepted += 1;
+      p.accepted[it] = 1;
+    } else {
+      p.mu = p.mu * p.nu;
+      p.nu = 2.0 * p.nu;
+      p.need_lin = 0;
+      p.accepted[it] = 0;
+    }
+    p.cost[it + 1] = p.F;
+    p.iter = it + 1;
+  }
+  __syncthreads();
+  if (p.need_lin) commit_state(p);  // need_lin was just set exactly on acceptance
+  __syncthreads();
+}
+
+template <typename T>
+__device__ void lm_end(BProb& p, const BatchRun& a, Smem& sm) {
+  cost_pass<T>(p, false, (T)a.huber_delta, 1);
+  __syncthreads();
+  const double s = fixed_sum(p.cpart, p.C, sm.chunks);
+  const double nv = fixed_sum(p.cpart + p.C, p.C, sm.chunks);
+  for (int i = threadIdx.x; i < p.C; i += blockDim.x) {
+    double q[4];
+    rot_to_quat(p.R + 9 * i, q);
+    double* o = p.cam_qt_out + 7 * i;
+    for (int c = 0; c < 4; ++c) o[c] = q[c];
+    for (int c = 0; c < 3; ++c) o[4 + c] = p.t[3 * i + c];
+  }
+  for (int j = threadIdx.x; j < p.P; j += blockDim.x)
+    for (int c = 0; c < 3; ++c) p.pts_out[3 * j + c] = p.X[3 * j + c];
+  if (threadIdx.x == 0) {
+    p.rmse_s = s;
+    p.rmse_n = nv;
+    if (!isfinite(p.F)) p.error |= kErrNonFinite;
+    p.phase = kPhaseDone;
+  }
+  __syncthreads();
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_batch(BatchRun a, int dyn_bytes) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ Smem sm;
+  T* dyn = reinterpret_cast<T*>(smem_raw);
+  for (;;) {
+    if (threadIdx.x == 0) sm.item = (int)atomicAdd(a.queue, 1u);
+    __syncthreads();
+    const int w = sm.item;
+    __syncthreads();
+    if (w >= a.n_work) break;
+    BProb& p = a.probs[a.work[w]];
+    if (p.phase == kPhaseDone) continue;
+    if (p.phase == kPhaseSetup) {
+      setup_problem<T>(p, sm);
+      if (p.status != 0) {
+        if (threadIdx.x == 0) p.phase = kPhaseDone;
+        __syncthreads();
+        continue;
+      }
+      lm_begin<T>(p, a, sm);
+    }
+    int todo = p.iters - p.iter;
+    if (a.iters_per_tick > 0 && todo > a.iters_per_tick) todo = a.iters_per_tick;
+    const int nrw = min((int)(NT / 32), (int)(dyn_bytes / row_warp_bytes<T>(p.C)));
+    if (nrw < 1) {  // the host sizes shared memory for its largest problem
+      if (threadIdx.x == 0) {
+        p.error |= kErrTooLarge;
+        p.phase = kPhaseDone;
+      }
+      __syncthreads();
+      continue;
+    }
+    for (int it = 0; it < todo; ++it) lm_iteration<T>(p, a, sm, dyn, nrw);
+    if (p.iter >= p.iters) lm_end<T>(p, a, sm);
+  }
+}
+
+template <typename T, int NT>
+cudaError_t launch_t(int grid, size_t smem, const BatchRun& a, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(k_batch<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  k_batch<T, NT><<<grid, NT, smem, s>>>(a, (int)smem);
+  return cudaGetLastError();
+}
+
+template <typename T, int NT>
+int occupancy_t(size_t smem) {
+  if (cudaFuncSetAttribute(k_batch<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
+    return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<T, NT>, NT, smem) != cudaSuccess)
+    return 0;
+  return n;
+}
+
+}  // namespace
+
+size_t batch_smem_bytes(int precision, int threads, int max_cams) {
+  const size_t per = precision == BA_FP32 ? row_warp_bytes<float>(max_cams)
+                                          : row_warp_bytes<double>(max_cams);
+  const size_t sd = (size_t)kPanel * (kPanel + 1) * (precision == BA_FP32 ? 4 : 8);
+  const size_t want = per * (size_t)(threads / 32);
+  return want > sd ? want : sd;
+}
+
+cudaError_t launch_batch(int precision, int threads, int grid, size_t smem, const BatchRun& a,
+                         cudaStream_t s) {
+  if (precision == BA_FP32) {
+    if (threads == 128) return launch_t<float, 128>(grid, smem, a, s);
+    if (threads == 256) return launch_t<float, 256>(grid, smem, a, s);
+    if (threads == 512) return launch_t<float, 512>(grid, smem, a, s);
+  } else {
+    if (threads == 128) return launch_t<double, 128>(grid, smem, a, s);
+    if (threads == 256) return launch_t<double, 256>(grid, smem, a, s);
+    if (threads == 512) return launch_t<double, 512>(grid, smem, a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int batch_max_ctas_per_sm(int precision, int threads, size_t smem) {
+  if (precision == BA_FP32) {
+    if (threads == 128) return occupancy_t<float, 128>(smem);
+    if (threads == 256) return occupancy_t<float, 256>(smem);
+    if (threads == 512) return occupancy_t<float, 512>(smem);
+  } else {
+    if (threads == 128) return occupancy_t<double, 128>(smem);
+    if (threads == 256) return occupancy_t<double, 256>(smem);
+    if (threads == 512) return occupancy_t<double, 512>(smem);
+  }
+  return 0;
+}
+
+}  // namespace ba

@@ -42,4 +42,8 @@ void dev_free(ba_handle* h, void* p);
 void free_problem(ba_handle* h);
 void destroy_server(ba_handle* h);
 void destroy_batch(ba_handle* h);
+// Timings of the last batched solve / the server so far as kernel-stat
+// entries; return the number written (at most max).
+int batch_stats(ba_handle* h, ba_kernel_stat* out, int max);
+int server_stats(ba_handle* h, ba_kernel_stat* out, int max);
 }  // namespace ba

@@ -1,17 +1,478 @@
-// Served local BA (continuous batching of requests).
+// Served local BA with continuous batching.  A worker thread owns the device
+// side: it admits queued requests into free slots as slot count and arena
+// memory allow (first in, first out; a request waits while the head of the
+// queue does not fit), copies their inputs into their arena blocks, and runs
+// ticks — one launch of the multi-problem kernel in which every resident
+// request advances by one LM iteration (its first tick also lays it out and
+// evaluates the initial cost).  Requests that finish leave after the tick,
+// their memory is freed, and new arrivals join the next tick, so requests of
+// different sizes and arrival times share every launch.  A request's poses,
+// points and LM state stay in its arena block between ticks.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "batch.h"
 #include "handle.h"
 
-struct ba_server {};
+using namespace ba;
 
 namespace ba {
+bool check_problem(const ba_problem& q, std::string& why);
+void fill_result(const BProb& p, ba_result& r);
+bool plan_launch(int device, int precision, int threads, int ctas_per_sm, int max_cams,
+                 size_t& smem, int& grid, std::string& why);
+}  // namespace ba
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Req {
+  uint64_t id = 0;
+  int C = 0, P = 0, N = 0;
+  Intrinsics K{};
+  std::vector<char> in;  // packed input block
+  double* user_q = nullptr;
+  double* user_p = nullptr;
+  ProbBytes bytes{};
+  size_t off = 0;  // arena offset of its block
+  int slot = -1;
+  bool done = false;
+  Clock::time_point t_submit, t_done;
+  ba_result result{};
+  std::vector<double> out_q, out_p;
+};
+
+// First-fit allocator over the arena (offsets).
+struct Arena {
+  size_t size = 0;
+  std::map<size_t, size_t> free_;  // offset -> length
+  void init(size_t n) {
+    size = n;
+    free_.clear();
+    free_[0] = n;
+  }
+  bool alloc(size_t n, size_t& off) {
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= n) {
+        off = it->first;
+        const size_t rest = it->second - n;
+        free_.erase(it);
+        if (rest) free_[off + n] = rest;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t n) {
+    auto it = free_.emplace(off, n).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+};
+
+size_t block_bytes(const ProbBytes& b) { return b.in + b.out + b.work; }
+
+}  // namespace
+
+struct ba_server {
+  ba_handle* h = nullptr;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::thread worker;
+  bool stop = false;
+  std::string fatal;
+  uint64_t next_id = 1;
+  std::deque<Req*> waiting;
+  std::unordered_map<uint64_t, Req*> reqs;
+  std::vector<Req*> slots;
+  Arena arena;
+  char* base = nullptr;
+  BProb* d_probs = nullptr;
+  BProb* h_probs = nullptr;  // pinned, [slots]
+  int32_t* d_work = nullptr;
+  int32_t* h_work = nullptr;  // pinned
+  unsigned* d_queue = nullptr;
+  char* h_stage = nullptr;  // pinned staging of admitted inputs
+  size_t stage_bytes = 0;
+  int threads = 256;
+  // statistics
+  uint64_t ticks = 0, completed = 0;
+  double busy_ms = 0.0;
+};
+
+namespace {
+
+void fail_all(ba_server* s, const std::string& why) {
+  s->fatal = why;
+  for (auto& kv : s->reqs) {
+    Req* r = kv.second;
+    if (!r->done) {
+      r->done = true;
+      r->result.status = BA_ERR_CUDA;
+      r->t_done = Clock::now();
+    }
+  }
+  s->waiting.clear();
+  s->cv.notify_all();
+}
+
+bool grow_stage(ba_server* s, size_t need) {
+  if (s->stage_bytes >= need) return true;
+  if (s->h_stage) cudaFreeHost(s->h_stage);
+  s->h_stage = nullptr;
+  s->stage_bytes = 0;
+  size_t n = std::max(need, (size_t)64 << 20);
+  if (cudaHostAlloc((void**)&s->h_stage, n, cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  s->stage_bytes = n;
+  return true;
+}
+
+// One scheduling step; returns false when the worker should exit.
+bool tick(ba_server* s) {
+  ba_handle* h = s->h;
+  cudaStream_t st = h->stream;
+  const int prec = h->opts.precision;
+  std::vector<Req*> admitted;
+  std::vector<int> resident;
+  {
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (;;) {
+      if (s->stop) return false;
+      // admission: first in, first out, by free slot and arena space
+      while (!s->waiting.empty()) {
+        Req* r = s->waiting.front();
+        int slot = -1;
+        for (int i = 0; i < (int)s->slots.size(); ++i)
+          if (!s->slots[i]) {
+            slot = i;
+            break;
+          }
+        if (slot < 0) break;
+        size_t off = 0;
+        if (!s->arena.alloc(block_bytes(r->bytes), off)) break;
+        r->off = off;
+        r->slot = slot;
+        s->slots[slot] = r;
+        s->waiting.pop_front();
+        admitted.push_back(r);
+      }
+      bool any = false;
+      for (Req* r : s->slots) any = any || r;
+      if (any) break;
+      s->cv.wait(lk);
+    }
+    for (int i = 0; i < (int)s->slots.size(); ++i)
+      if (s->slots[i]) resident.push_back(i);
+  }
+  // copy the admitted requests in and initialise their descriptors
+  size_t need = 0;
+  for (Req* r : admitted) need += r->bytes.in;
+  if (!grow_stage(s, need)) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    fail_all(s, "pinned staging allocation failed");
+    return false;
+  }
+  size_t so = 0;
+  int max_cams = 1;
+  for (int i : resident) max_cams = std::max(max_cams, s->slots[i]->C);
+  for (Req* r : admitted) {
+    memcpy(s->h_stage + so, r->in.data(), r->bytes.in);
+    char* blk = s->base + r->off;
+    cudaMemcpyAsync(blk, s->h_stage + so, r->bytes.in, cudaMemcpyHostToDevice, st);
+    so += r->bytes.in;
+    BProb& p = s->h_probs[r->slot];
+    memset(&p, 0, sizeof(p));
+    p.C = r->C;
+    p.P = r->P;
+    p.N = r->N;
+    p.iters = h->opts.max_lm_iters;
+    p.K = r->K;
+    p.phase = kPhaseSetup;
+    assign_prob(prec, p, blk, blk + r->bytes.in, blk + r->bytes.in + r->bytes.out);
+    cudaMemcpyAsync(s->d_probs + r->slot, &p, sizeof(BProb), cudaMemcpyHostToDevice, st);
+  }
+  // one tick over every resident request (largest first)
+  std::sort(resident.begin(), resident.end(), [&](int a, int b) {
+    const Req* ra = s->slots[a];
+    const Req* rb = s->slots[b];
+    const double wa = 40.0 * ra->N + 36.0 * ra->C * ra->C * ra->C;
+    const double wb = 40.0 * rb->N + 36.0 * rb->C * rb->C * rb->C;
+    return wa > wb || (wa == wb && a < b);
+  });
+  const int nw = (int)resident.size();
+  for (int i = 0; i < nw; ++i) s->h_work[i] = resident[i];
+  cudaMemcpyAsync(s->d_work, s->h_work, sizeof(int32_t) * nw, cudaMemcpyHostToDevice, st);
+  cudaMemsetAsync(s->d_queue, 0, sizeof(unsigned), st);
+  size_t smem = 0;
+  int grid = 0;
+  std::string why;
+  if (!plan_launch(h->device, prec, s->threads, 0, max_cams, smem, grid, why)) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    fail_all(s, why);
+    return false;
+  }
+  BatchRun a{};
+  a.probs = s->d_probs;
+  a.work = s->d_work;
+  a.n_work = nw;
+  a.queue = s->d_queue;
+  a.iters_per_tick = 1;
+  a.huber_delta = h->opts.huber_delta;
+  a.mu0 = h->opts.mu0;
+  a.mu_min = h->opts.mu_min >= 0 ? h->opts.mu_min : (prec == BA_FP32 ? kMuMinFp32 : 0.0);
+  const auto t0 = Clock::now();
+  cudaError_t e = launch_batch(prec, s->threads, std::min(grid, std::max(nw, 1)), smem, a, st);
+  int hi = 0;
+  for (int i : resident) hi = std::max(hi, i + 1);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->h_probs, s->d_probs, sizeof(BProb) * hi, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    fail_all(s, std::string("tick failed: ") + cudaGetErrorString(e));
+    return false;
+  }
+  s->busy_ms += std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+  s->ticks += 1;
+  // finished requests: outputs to the host, memory back to the arena
+  std::vector<Req*> fin;
+  for (int i : resident)
+    if (s->h_probs[i].phase == kPhaseDone) fin.push_back(s->slots[i]);
+  for (Req* r : fin) {
+    const BProb& p = s->h_probs[r->slot];
+    fill_result(p, r->result);
+    if (r->result.status == BA_OK) {
+      r->out_q.resize((size_t)r->C * 7);
+      r->out_p.resize((size_t)r->P * 3);
+      cudaMemcpyAsync(r->out_q.data(), p.cam_qt_out, sizeof(double) * r->out_q.size(),
+                      cudaMemcpyDeviceToHost, st);
+      cudaMemcpyAsync(r->out_p.data(), p.pts_out, sizeof(double) * r->out_p.size(),
+                      cudaMemcpyDeviceToHost, st);
+    }
+  }
+  if (!fin.empty()) {
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      std::lock_guard<std::mutex> lk(s->mu);
+      fail_all(s, std::string("result copy failed: ") + cudaGetErrorString(e));
+      return false;
+    }
+  }
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    const auto now = Clock::now();
+    for (Req* r : fin) {
+      r->t_done = now;
+      r->result.latency_ms = std::chrono::duration<double, std::milli>(now - r->t_submit).count();
+      r->done = true;
+      s->slots[r->slot] = nullptr;
+      s->arena.release(r->off, block_bytes(r->bytes));
+      r->in.clear();
+      r->in.shrink_to_fit();
+      s->completed += 1;
+    }
+  }
+  if (!fin.empty()) s->cv.notify_all();
+  return true;
+}
+
+void worker_main(ba_server* s) {
+  cudaSetDevice(s->h->device);
+  while (tick(s)) {
+  }
+}
+
+}  // namespace
+
+namespace ba {
+
+int server_stats(ba_handle* h, ba_kernel_stat* out, int max) {
+  ba_server* s = h->server;
+  if (!s || max < 1) return 0;
+  std::lock_guard<std::mutex> lk(s->mu);
+  memset(&out[0], 0, sizeof(out[0]));
+  strncpy(out[0].name, "serve_tick", sizeof(out[0].name) - 1);
+  out[0].launches = (int32_t)s->ticks;
+  out[0].total_ms = s->busy_ms;
+  if (max < 2) return 1;
+  memset(&out[1], 0, sizeof(out[1]));
+  strncpy(out[1].name, "serve_completed", sizeof(out[1].name) - 1);
+  out[1].launches = (int32_t)s->completed;
+  return 2;
+}
+
 void destroy_server(ba_handle* h) {
-  delete h->server;
+  ba_server* s = h->server;
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  cudaStreamSynchronize(h->stream);
+  for (auto& kv : s->reqs) delete kv.second;
+  for (Req* r : s->waiting) (void)r;  // owned through reqs
+  dev_free(h, s->base);
+  dev_free(h, s->d_probs);
+  dev_free(h, s->d_work);
+  dev_free(h, s->d_queue);
+  if (s->h_probs) cudaFreeHost(s->h_probs);
+  if (s->h_work) cudaFreeHost(s->h_work);
+  if (s->h_stage) cudaFreeHost(s->h_stage);
+  delete s;
   h->server = nullptr;
 }
+
 }  // namespace ba
 
 extern "C" {
-ba_status ba_create_server(const ba_options*, ba_handle**) { return BA_ERR_STATE; }
-ba_status ba_submit(ba_handle*, const ba_problem*, uint64_t*) { return BA_ERR_STATE; }
-ba_status ba_poll(ba_handle*, uint64_t, ba_result*) { return BA_ERR_STATE; }
+
+ba_status ba_create_server(const ba_options* opts, ba_handle** out) {
+  ba_handle* h = nullptr;
+  ba_status st = ba_create(opts, &h);
+  if (st != BA_OK) return st;
+  if (opts->serve_slots < 1 || opts->serve_slots > 65536 || opts->serve_queue < 1 ||
+      opts->max_lm_iters < 1 || opts->max_lm_iters > BA_MAX_ITERS) {
+    ba_destroy(h);
+    *out = nullptr;
+    return BA_ERR_INVALID_ARG;
+  }
+  h->is_server = true;
+  ba_server* s = new ba_server();
+  s->h = h;
+  h->server = s;
+  size_t bytes = opts->serve_arena_bytes;
+  if (bytes == 0) {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    bytes = std::min<size_t>(fr / 2, (size_t)16 << 30);
+  }
+  const int ns = opts->serve_slots;
+  s->base = (char*)dev_alloc(h, bytes);
+  s->d_probs = (BProb*)dev_alloc(h, sizeof(BProb) * ns);
+  s->d_work = (int32_t*)dev_alloc(h, sizeof(int32_t) * ns);
+  s->d_queue = (unsigned*)dev_alloc(h, 64);
+  if (!s->base || !s->d_probs || !s->d_work || !s->d_queue ||
+      cudaHostAlloc((void**)&s->h_probs, sizeof(BProb) * ns, cudaHostAllocDefault) != cudaSuccess ||
+      cudaHostAlloc((void**)&s->h_work, sizeof(int32_t) * ns, cudaHostAllocDefault) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    ba_destroy(h);
+    *out = nullptr;
+    return BA_ERR_OOM;
+  }
+  s->arena.init(bytes);
+  s->slots.assign(ns, nullptr);
+  s->worker = std::thread(worker_main, s);
+  *out = h;
+  return BA_OK;
 }
+
+ba_status ba_submit(ba_handle* h, const ba_problem* req, uint64_t* req_id) {
+  if (!h || !req || !req_id) return BA_ERR_INVALID_ARG;
+  if (!h->is_server || !h->server) {
+    h->err = "ba_submit: not a serving handle (use ba_create_server)";
+    return BA_ERR_STATE;
+  }
+  ba_server* s = h->server;
+  std::string why;
+  if (!check_problem(*req, why)) {
+    h->err = "ba_submit: " + why;
+    return BA_ERR_INVALID_ARG;
+  }
+  Req* r = new Req();
+  r->C = req->n_cams;
+  r->P = req->n_pts;
+  r->N = (int)req->n_obs;
+  r->K = Intrinsics{req->K.fx, req->K.fy, req->K.cx, req->K.cy};
+  r->bytes = prob_bytes(h->opts.precision, r->C, r->P, req->n_obs);
+  if (block_bytes(r->bytes) > s->arena.size) {
+    delete r;
+    h->err = "ba_submit: request larger than the whole arena";
+    return BA_ERR_OOM;
+  }
+  r->in.resize(r->bytes.in);
+  pack_inputs(h->opts.precision, *req, r->in.data());
+  r->user_q = req->cam_qt_out;
+  r->user_p = req->pts_out;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (!s->fatal.empty()) {
+      delete r;
+      h->err = "ba_submit: server failed: " + s->fatal;
+      return BA_ERR_CUDA;
+    }
+    if ((int)s->waiting.size() >= h->opts.serve_queue) {
+      delete r;
+      h->err = "ba_submit: waiting queue full";
+      return BA_ERR_BUSY;
+    }
+    r->id = s->next_id++;
+    r->t_submit = Clock::now();
+    s->reqs[r->id] = r;
+    s->waiting.push_back(r);
+    *req_id = r->id;
+  }
+  s->cv.notify_all();
+  return BA_OK;
+}
+
+ba_status ba_poll(ba_handle* h, uint64_t req_id, ba_result* out) {
+  if (!h || !out) return BA_ERR_INVALID_ARG;
+  if (!h->is_server || !h->server) {
+    h->err = "ba_poll: not a serving handle";
+    return BA_ERR_STATE;
+  }
+  ba_server* s = h->server;
+  Req* r = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(req_id);
+    if (it == s->reqs.end()) {
+      h->err = "ba_poll: unknown or already collected request id";
+      return BA_ERR_INVALID_ARG;
+    }
+    r = it->second;
+    if (!r->done) return BA_ERR_NOT_READY;
+    s->reqs.erase(it);
+  }
+  *out = r->result;
+  if (r->result.status == BA_OK) {
+    if (r->user_q) memcpy(r->user_q, r->out_q.data(), sizeof(double) * r->out_q.size());
+    if (r->user_p) memcpy(r->user_p, r->out_p.data(), sizeof(double) * r->out_p.size());
+  }
+  const ba_status st = (ba_status)r->result.status;
+  if (st != BA_OK) h->err = "ba_poll: request failed";
+  delete r;
+  return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,173 @@
+"""Batched local BA (ba_solve_batch) against the FP64 CPU oracle.
+
+Each window of a batch is an independent problem; the oracle solves it alone
+with the dense Schur + Cholesky step.  FP64 batch: per-iteration cost within
+1e-9 relative.  FP32 batch: final RMSE within 1 % of the oracle's.  A window's
+result must not depend on the rest of the batch or on the tile schedule.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2510_15271_b300 import ba, scenes
+
+pytestmark = pytest.mark.gpu
+
+COST_RTOL = 1e-9
+RMSE_RTOL = 0.01
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2510_15271_b300 import build
+    build.build()
+    ba.lib()
+
+
+def _windows(n, seed, cams=(10, 24), pts=(300, 1500)):
+    return scenes.make_windows(n, seed=seed, cams=cams, pts=pts)
+
+
+def _oracle(s, iters):
+    prob = O.Problem.from_arrays(s.intrinsics(), s.obs_cam, s.obs_pt, s.obs_uv, s.cam_fixed,
+                                 s.n_cams, s.n_pts)
+    res = O.lm_solve(prob, O.state_from_qt(s.cam_qt, s.pts),
+                     O.LMOptions(huber_delta=s.huber_delta, lm_iters=iters, solver="dense"))
+    return prob, res
+
+
+def _batch(ws, precision, iters=5, schedule=None, **kw):
+    o = ba.options_for_scene(ws[0], precision, max_lm_iters=iters, **kw)
+    arrs = [ba._ProblemArrays.from_scene(s, want_state=True) for s in ws]
+    with ba.ba_create(o) as h:
+        if schedule:
+            ba.ba_set_batch_schedule(h, *schedule)
+        res = ba.ba_solve_batch(h, arrs)
+    return res, arrs
+
+
+def test_fp64_batch_matches_oracle_per_iteration():
+    ws = _windows(5, seed=11)
+    res, arrs = _batch(ws, "fp64", iters=5)
+    for s, r, a in zip(ws, res, arrs):
+        assert r.status == ba.BA_OK
+        prob, ref = _oracle(s, 5)
+        rel = np.abs(r.costs() - ref.costs) / ref.costs
+        assert rel.max() <= COST_RTOL, (rel, r.costs(), ref.costs)
+        st = O.state_from_qt(a.q_out, a.p_out)
+        rot, pos = O.pose_errors(st.R, st.t, ref.state.R, ref.state.t)
+        assert rot.max() < 1e-8 and pos.max() < 1e-8, (rot.max(), pos.max())
+        np.testing.assert_allclose(a.p_out, ref.state.X, atol=1e-7)
+        assert abs(r.rmse_px - O.rmse(prob, ref.state)) <= 1e-9 * max(1.0, r.rmse_px)
+
+
+def test_fp64_batch_ragged_and_fixed_cameras():
+    ws = [scenes.make_scene("window", seed=5, n_cams=7, n_pts=333),
+          scenes.make_scene("window", seed=6, n_cams=33, n_pts=901),
+          scenes.make_scene("window", seed=7, n_cams=11, n_pts=257)]
+    fx = ws[1].cam_fixed.copy()
+    fx[[0, 3, 17]] = 1
+    ws[1].cam_fixed = fx
+    res, _ = _batch(ws, "fp64", iters=4)
+    for s, r in zip(ws, res):
+        _, ref = _oracle(s, 4)
+        rel = np.abs(r.costs() - ref.costs) / ref.costs
+        assert rel.max() <= COST_RTOL, (rel, r.costs(), ref.costs)
+
+
+def test_fp32_batch_rmse_within_one_percent():
+    ws = _windows(6, seed=12)
+    res, arrs = _batch(ws, "fp32", iters=5)
+    for s, r, a in zip(ws, res, arrs):
+        assert r.status == ba.BA_OK
+        prob, ref = _oracle(s, 5)
+        ours = O.rmse(prob, O.state_from_qt(a.q_out, a.p_out))
+        theirs = O.rmse(prob, ref.state)
+        assert abs(ours - theirs) <= RMSE_RTOL * theirs, (ours, theirs)
+        # the device RMSE agrees with the oracle's evaluation of the returned state
+        assert abs(r.rmse_px - ours) <= 1e-4 * ours
+
+
+def test_window_result_independent_of_the_batch():
+    ws = _windows(12, seed=13, cams=(10, 40), pts=(200, 2000))
+    mixed, _ = _batch(ws, "fp32", iters=5)
+    for i in (0, 5, 11):
+        alone, _ = _batch([ws[i]], "fp32", iters=5)
+        assert np.array_equal(alone[0].costs(), mixed[i].costs())
+        assert alone[0].rmse_px == mixed[i].rmse_px
+
+
+@pytest.mark.parametrize("schedule", [(128, 1), (512, 1), (256, 2), (128, 3)])
+def test_result_independent_of_the_schedule(schedule):
+    ws = _windows(7, seed=14, cams=(10, 50), pts=(200, 1500))
+    ref, ra = _batch(ws, "fp32", iters=5, schedule=(256, 1))
+    got, ga = _batch(ws, "fp32", iters=5, schedule=schedule)
+    for r, g, x, y in zip(ref, got, ra, ga):
+        assert np.array_equal(r.costs(), g.costs())
+        assert np.array_equal(x.q_out, y.q_out) and np.array_equal(x.p_out, y.p_out)
+
+
+def test_tuner_picks_a_valid_schedule_and_keeps_results():
+    ws = _windows(20, seed=15, cams=(10, 60), pts=(200, 1200))
+    o = ba.options_for_scene(ws[0], "fp32", max_lm_iters=3)
+    arrs = [ba._ProblemArrays.from_scene(s, want_state=True) for s in ws]
+    with ba.ba_create(o) as h:
+        before = ba.ba_solve_batch(h, arrs)
+        t, c = ba.ba_tune_batch(h, arrs)
+        assert t in (128, 256, 512) and 1 <= c <= 4
+        assert ba.ba_get_batch_schedule(h) == (t, c)
+        after = ba.ba_solve_batch(h, arrs)
+        stats = ba.ba_kernel_stats(h)
+    for a, b in zip(before, after):
+        assert np.array_equal(a.costs(), b.costs())
+    assert stats["batch_kernel"][1] > 0
+
+
+def test_batch_matches_single_problem_path_fp64():
+    s = scenes.make_scene("window", seed=21, n_cams=15, n_pts=700)
+    res, arrs = _batch([s], "fp64", iters=5)
+    rep, q, p = ba.solve_scene(s, "fp64", max_lm_iters=5, solver=ba.BA_SOLVER_DENSE)
+    rel = np.abs(res[0].costs() - rep["costs"]) / rep["costs"]
+    assert rel.max() <= COST_RTOL
+
+
+def test_invalid_window_is_reported_and_others_solved():
+    ws = _windows(3, seed=16)
+    bad = ws[1]
+    cam = bad.obs_cam.copy()
+    cam[7] = bad.n_cams + 3          # out of range: caught on the device
+    arrs = [ba._ProblemArrays.from_scene(s, want_state=True) for s in ws]
+    arrs[1] = ba._ProblemArrays(bad.cam_qt, bad.pts, cam, bad.obs_pt, bad.obs_uv,
+                                bad.intrinsics(), bad.cam_fixed, want_state=True)
+    o = ba.options_for_scene(ws[0], "fp32", max_lm_iters=3)
+    with ba.ba_create(o) as h:
+        n = len(arrs)
+        arr = (ba.Problem * n)(*[a.st for a in arrs])
+        out = (ba.Result * n)()
+        st = ba.lib().ba_solve_batch(h.ptr, n, arr, out)
+        assert st == ba.BA_ERR_INVALID_ARG
+        assert b"camera index out of range" in ba.lib().ba_last_error(h.ptr)
+    assert out[1].status == ba.BA_ERR_INVALID_ARG
+    assert out[0].status == ba.BA_OK and out[2].status == ba.BA_OK
+
+
+def test_duplicate_observation_is_rejected():
+    s = scenes.make_scene("window", seed=17, n_cams=10, n_pts=200)
+    cam = np.concatenate([s.obs_cam, s.obs_cam[:1]])
+    pt = np.concatenate([s.obs_pt, s.obs_pt[:1]])
+    uv = np.concatenate([s.obs_uv, s.obs_uv[:1]])
+    a = ba._ProblemArrays(s.cam_qt, s.pts, cam, pt, uv, s.intrinsics(), s.cam_fixed)
+    with ba.ba_create(ba.options_for_scene(s, "fp32")) as h:
+        with pytest.raises(ba.BAError, match="observes a point twice"):
+            ba.ba_solve_batch(h, [a])
+
+
+def test_host_side_argument_checks():
+    s = scenes.make_scene("window", seed=18, n_cams=10, n_pts=200)
+    with ba.ba_create(ba.options_for_scene(s, "fp32")) as h:
+        a = ba._ProblemArrays.from_scene(s)
+        a.st.n_cams = 600                # more cameras than the batched solver takes
+        with pytest.raises(ba.BAError, match="cameras"):
+            ba.ba_solve_batch(h, [a])
+        with pytest.raises(ba.BAError):
+            ba.ba_set_batch_schedule(h, 96, 1)
