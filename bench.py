@@ -340,6 +340,161 @@ def measured_traffic(s, name):
     return None
 
 
+# --------------------------------------------------------------------------- batched / served
+
+def pose_errors_qt(qa, qb):
+    """Per-camera rotation angle of R_a R_b^T (rad) and centre distance (m)
+    between two pose arrays (qw, qx, qy, qz, tx, ty, tz), world to camera."""
+    from scipy.spatial.transform import Rotation
+    Ra = Rotation.from_quat(qa[:, [1, 2, 3, 0]])
+    Rb = Rotation.from_quat(qb[:, [1, 2, 3, 0]])
+    rot = (Ra * Rb.inv()).magnitude()
+    Ca = -Ra.inv().apply(qa[:, 4:])
+    Cb = -Rb.inv().apply(qb[:, 4:])
+    return rot, np.linalg.norm(Ca - Cb, axis=1)
+
+
+def run_batched(args, local_rank):
+    """Batched local BA: the window workload (independent ring windows) in one
+    persistent launch per step, FP32 with FP64 islands, schedule from the
+    autotuner; beside it the same batch in FP64 and the plain FP64
+    single-problem path on a sample of the windows."""
+    from paper_2510_15271_b300 import ba, scenes
+    t0 = time.perf_counter()
+    ws = scenes.make_windows(args.windows, seed=4)
+    gen_s = time.perf_counter() - t0
+    iters = ws[0].lm_iters
+    n_obs = int(sum(len(w.obs_cam) for w in ws))
+    work = n_obs * iters
+    arrs = [ba._ProblemArrays.from_scene(w, want_state=True) for w in ws]
+
+    def timed(precision, steps, tune):
+        o = ba.options_for_scene(ws[0], precision, device=local_rank)
+        with ba.ba_create(o) as h:
+            sched = ba.ba_tune_batch(h, arrs) if tune else ba.ba_get_batch_schedule(h)
+            for _ in range(max(1, args.warmup)):
+                ba.ba_solve_batch(h, arrs)
+            call, kern, h2d, d2h = [], [], [], []
+            for _ in range(steps):
+                t = time.perf_counter()
+                res = ba.ba_solve_batch(h, arrs)
+                call.append(time.perf_counter() - t)
+                st = ba.ba_kernel_stats(h)
+                kern.append(st["batch_kernel"][1] / 1e3)
+                h2d.append(st["batch_h2d"][1] / 1e3)
+                d2h.append(st["batch_d2h"][1] / 1e3)
+        return res, sched, call, kern, h2d, d2h, [(a.q_out.copy(), a.p_out.copy()) for a in arrs]
+
+    res32, sched, call, kern, h2d, d2h, st32 = timed("fp32", args.steps, True)
+    # one more (untimed) solve with per-phase clocks, for the phase split
+    o = ba.options_for_scene(ws[0], "fp32", device=local_rank, profile=1)
+    with ba.ba_create(o) as h:
+        ba.ba_set_batch_schedule(h, *sched)
+        ba.ba_solve_batch(h, arrs)
+        ph = {k[3:]: round(v[1], 1) for k, v in ba.ba_kernel_stats(h).items() if k.startswith("ph_")}
+    res64, _, call64, kern64, _, _, st64 = timed("fp64", max(1, args.steps // 2), False)
+    r32 = np.array([r.rmse_px for r in res32])
+    r64 = np.array([r.rmse_px for r in res64])
+    bad = [i for i, r in enumerate(res32) if r.status != 0]
+    rot_err, pos_err = [], []
+    for (q32, _), (q64, _) in zip(st32, st64):
+        rr, pp = pose_errors_qt(q32, q64)
+        rot_err.append(rr.max())
+        pos_err.append(pp.max())
+    # plain FP64 single-problem path on a sample of the windows
+    sample = ws[:args.plain_sample]
+    plain_s, plain_obs = 0.0, 0
+    for w in sample:
+        o = ba.options_for_scene(w, "fp64", device=local_rank, solver=ba.BA_SOLVER_DENSE)
+        with ba.ba_create(o) as h:
+            ba.ba_set_problem(h, w.cam_qt, w.pts, w.obs_cam, w.obs_pt, w.obs_uv, w.intrinsics(),
+                              w.cam_fixed)
+            ba.ba_solve(h)
+            ba.ba_set_state(h, w.cam_qt, w.pts)
+            rep = ba.ba_solve(h)
+        plain_s += rep["solve_ms"] / 1e3
+        plain_obs += len(w.obs_cam)
+    mean = lambda v: float(np.mean(v))
+    return {
+        "workload": f"{len(ws)} ring windows, cameras U{{10..60}}, points U{{500..8000}}, "
+                    f"track length U{{3..10}}, {iters} LM iterations each, dense Schur + "
+                    "Cholesky per window, FP32 with FP64 cost / gain / damping / 3x3 inverses",
+        "n_windows": len(ws), "n_obs": n_obs, "n_cams": int(sum(w.n_cams for w in ws)),
+        "n_pts": int(sum(w.n_pts for w in ws)), "lm_iters": iters,
+        "value": work / mean(kern), "unit": UNIT, "ms_per_step": 1e3 * mean(kern),
+        "e2e": {"value": work / mean(call), "unit": UNIT, "ms_per_step": 1e3 * mean(call),
+                "h2d_ms": 1e3 * mean(h2d), "d2h_ms": 1e3 * mean(d2h)},
+        "schedule": {"threads": sched[0], "ctas_per_sm": sched[1]},
+        "phase_cta_ms": ph,
+        "fp64_batched": {"value": work / mean(kern64), "ms_per_step": 1e3 * mean(kern64)},
+        "plain_fp64_path": {"value": plain_obs * iters / plain_s, "unit": UNIT,
+                            "sample": f"{len(sample)} windows solved one at a time "
+                                      "(ba_solve, dense, graph replay)"},
+        "rmse_fp32_vs_fp64_max_rel": float(np.max(np.abs(r32 - r64) / r64)),
+        "pose_err_fp32_vs_fp64_max": {"rad": float(np.max(rot_err)), "m": float(np.max(pos_err))},
+        "failed_windows": bad, "generate_s": round(gen_s, 1),
+    }
+
+
+def run_served(args, local_rank):
+    """Served local BA: Poisson arrivals replaying a pool of seeded requests
+    (cameras log-uniform [10, 200], points log-uniform [1k, 40k], track length
+    2 + Geometric(mean 3)); p50 / p99 of submit-to-result latency."""
+    from paper_2510_15271_b300 import ba, scenes
+    pool = [scenes.make_request(5000 + i) for i in range(args.serve_pool)]
+    arrs = [ba._ProblemArrays.from_scene(r) for r in pool]
+    arrivals = scenes.poisson_arrivals(args.serve_rate, args.serve_seconds, seed=5)
+    o = ba.options_for_scene(pool[0], "fp32", device=local_rank)
+    o.serve_slots = args.serve_slots
+    o.serve_queue = 1 << 20
+    o.serve_arena_bytes = args.serve_arena_gb << 30
+    lat, obs_done = [], 0
+    with ba.ba_create_server(o) as h:
+        for a in arrs[:8]:  # warm-up
+            rid = ba.ba_submit(h, a)
+            while ba.ba_poll(h, rid) is None:
+                time.sleep(1e-4)
+        pending = {}
+        t0 = time.perf_counter()
+        for i, ta in enumerate(arrivals):
+            while True:
+                now = time.perf_counter() - t0
+                if now >= ta:
+                    break
+                if pending and len(pending) > 64:
+                    for rid in list(pending)[:16]:
+                        r = ba.ba_poll(h, rid)
+                        if r is not None:
+                            lat.append(r.latency_ms)
+                            obs_done += pending.pop(rid)
+                else:
+                    time.sleep(min(ta - now, 2e-4))
+            j = i % len(arrs)
+            pending[ba.ba_submit(h, arrs[j])] = len(pool[j].obs_cam)
+        while pending:
+            for rid in list(pending):
+                r = ba.ba_poll(h, rid)
+                if r is not None:
+                    lat.append(r.latency_ms)
+                    obs_done += pending.pop(rid)
+            time.sleep(2e-4)
+        span = time.perf_counter() - t0
+        st = ba.ba_kernel_stats(h)
+    lat = np.array(lat)
+    return {
+        "workload": f"Poisson arrivals at {args.serve_rate:g} req/s for {args.serve_seconds:g} s "
+                    f"({len(arrivals)} requests replaying {len(pool)} seeded requests: cameras "
+                    "log-uniform [10, 200], points log-uniform [1k, 40k], track 2 + Geometric(3)), "
+                    f"{pool[0].lm_iters} LM iterations, FP32 with FP64 gain / damping",
+        "requests": int(lat.size), "p50_ms": float(np.percentile(lat, 50)),
+        "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()),
+        "throughput_req_s": lat.size / span, "value": obs_done * pool[0].lm_iters / span,
+        "unit": UNIT, "ticks": int(st["serve_tick"][0]),
+        "gpu_busy_frac": st["serve_tick"][1] / 1e3 / span,
+        "mean_obs_per_request": float(np.mean([len(r.obs_cam) for r in pool])),
+    }
+
+
 # --------------------------------------------------------------------------- reference arm
 
 def run_reference(args):
@@ -402,6 +557,15 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=2)
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--windows", type=int, default=512)
+    ap.add_argument("--plain-sample", type=int, default=16)
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-pool", type=int, default=96)
+    ap.add_argument("--serve-slots", type=int, default=1024)
+    ap.add_argument("--serve-arena-gb", type=int, default=32)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -449,6 +613,10 @@ def main():
                   "pcg_iters": [int(v) for v in res["reps"][-1]["pcg_iters"]],
                   "accepted": int(res["reps"][-1]["n_accepted"])},
     }
+    if not args.no_batched:
+        line["batched"] = run_batched(args, 0)
+    if not args.no_served:
+        line["served"] = run_served(args, 0)
     if not args.no_cpu:
         v, dt = cpu_baseline(s, args.cpu_iters)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": len(os.sched_getaffinity(0)),

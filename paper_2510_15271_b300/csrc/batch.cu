@@ -70,7 +70,11 @@ void carve_out(Carve& c, BProb& p, int C, int P) {
   p.pts_out = c.take<double>((size_t)P * 3);
 }
 
-void carve_work(Carve& c, BProb& p, int precision, int C, int P, int64_t N) {
+int items_cap(int C, int64_t npairs) {
+  return (int)((npairs + kPairItem - 1) / kPairItem + (int64_t)C * C + 1);
+}
+
+void carve_work(Carve& c, BProb& p, int precision, int C, int P, int64_t N, int64_t npairs) {
   const size_t t = precision == BA_FP32 ? 4 : 8;
   const size_t ws = precision == BA_FP32 ? kWStrideF32 : kWStrideF64;
   const size_t n = (size_t)6 * C;
@@ -113,17 +117,37 @@ void carve_work(Carve& c, BProb& p, int precision, int C, int P, int64_t N) {
   p.x = c.take_bytes(n * t);
   p.cpart = c.take<double>((size_t)C * 2);
   p.ppart = c.take<double>((size_t)P);
+  p.npairs = npairs;
+  p.nitems_cap = items_cap(C, npairs);
+  p.pair_k1 = c.take<int32_t>((size_t)npairs);
+  p.pair_q2 = c.take<int32_t>((size_t)npairs);
+  p.blk_ptr = c.take<int32_t>((size_t)C * C + 1);
+  p.blk_item = c.take<int32_t>((size_t)C * C + 1);
+  p.item_beg = c.take<int32_t>((size_t)p.nitems_cap);
+  p.Y = c.take_bytes((size_t)N * ws * t);
+  p.part = c.take_bytes((size_t)p.nitems_cap * 36 * t);
 }
 
 }  // namespace
 
-ProbBytes prob_bytes(int precision, int C, int P, int64_t N) {
+int64_t count_pairs(const ba_problem& q) {
+  std::vector<int32_t> L((size_t)q.n_pts, 0);
+  for (int64_t k = 0; k < q.n_obs; ++k) {
+    const int j = q.obs_pt[k];
+    if (j >= 0 && j < q.n_pts) ++L[j];
+  }
+  int64_t s = 0;
+  for (int32_t l : L) s += (int64_t)l * (l + 1) / 2;
+  return s;
+}
+
+ProbBytes prob_bytes(int precision, int C, int P, int64_t N, int64_t npairs) {
   ProbBytes b;
   Carve ci(nullptr), co(nullptr), cw(nullptr);
   carve_in(ci, C, P, N);
   BProb tmp{};
   carve_out(co, tmp, C, P);
-  carve_work(cw, tmp, precision, C, P, N);
+  carve_work(cw, tmp, precision, C, P, N, npairs);
   b.in = ci.off;
   b.out = co.off;
   b.work = cw.off;
@@ -140,7 +164,7 @@ void assign_prob(int precision, BProb& p, char* in, char* out, char* work) {
   p.raw_pt = r.pt;
   p.fixed = r.fixed;
   carve_out(co, p, p.C, p.P);
-  carve_work(cw, p, precision, p.C, p.P, p.N);
+  carve_work(cw, p, precision, p.C, p.P, p.N, p.npairs);
 }
 
 void pack_inputs(int /*precision*/, const ba_problem& src, char* host_in) {
@@ -244,6 +268,8 @@ struct ba_batch {
   int32_t* d_work = nullptr;
   size_t work_cap = 0;
   unsigned* d_queue = nullptr;
+  unsigned long long* d_phase = nullptr;  // per-phase CTA-ns (opts.profile)
+  unsigned long long* h_phase = nullptr;  // pinned mirror
   // pinned host mirrors
   char* h_in = nullptr;
   size_t h_in_bytes = 0;
@@ -279,6 +305,8 @@ void destroy_batch(ba_handle* h) {
   dev_free(h, b->d_probs);
   dev_free(h, b->d_work);
   dev_free(h, b->d_queue);
+  dev_free(h, b->d_phase);
+  if (b->h_phase) cudaFreeHost(b->h_phase);
   if (b->h_in) cudaFreeHost(b->h_in);
   if (b->h_out) cudaFreeHost(b->h_out);
   if (b->h_probs) cudaFreeHost(b->h_probs);
@@ -298,6 +326,19 @@ int batch_stats(ba_handle* h, ba_kernel_stat* out, int max) {
     strncpy(out[w].name, names[i], sizeof(out[w].name) - 1);
     out[w].launches = 1;
     out[w].total_ms = ms[i];
+  }
+  if (b->d_phase) {
+    // CTA-milliseconds per phase of the multi-problem kernel
+    static const char* ph[kPhaseCount] = {"ph_idle",   "ph_setup",    "ph_lin",
+                                          "ph_damp",   "ph_schur",    "ph_cholesky",
+                                          "ph_solve",  "ph_trial",    "ph_cost",
+                                          "ph_gain"};
+    for (int i = 0; i < kPhaseCount && w < max; ++i, ++w) {
+      memset(&out[w], 0, sizeof(out[w]));
+      strncpy(out[w].name, ph[i], sizeof(out[w].name) - 1);
+      out[w].launches = 0;
+      out[w].total_ms = b->h_phase[i] * 1e-6;
+    }
   }
   return w;
 }
@@ -321,13 +362,19 @@ size_t smem_per_block_optin(int device) {
   return (size_t)v;
 }
 
+// Shared memory the kernel declares statically (sums, scan and flags), with
+// room to spare.
+constexpr size_t kStaticSmemReserve = 8192;
+
 // Shared memory and grid of a schedule; false if the largest problem does
 // not fit.
 bool plan_launch(int device, int precision, int threads, int ctas_per_sm, int max_cams,
                  size_t& smem, int& grid, std::string& why) {
   const size_t want = batch_smem_bytes(precision, threads, max_cams);
   const size_t one = batch_smem_bytes(precision, 32, max_cams);  // one row warp
-  const size_t cap = smem_per_block_optin(device);
+  // the opt-in limit covers static and dynamic shared memory together
+  const size_t optin = smem_per_block_optin(device);
+  const size_t cap = optin > kStaticSmemReserve ? optin - kStaticSmemReserve : 0;
   size_t budget = cap;
   if (ctas_per_sm > 0) {
     // the SM's shared memory split between the CTAs (1 KB reserved per CTA)
@@ -432,10 +479,16 @@ ba_status prepare(ba_handle* h, ba_batch* b, int32_t n, const ba_problem* pr) {
   b->in_off.assign(n, 0);
   b->out_off.assign(n, 0);
   std::vector<size_t> work_off(n);
+  std::vector<int64_t> npairs(n);
   size_t in = 0, out = 0, work = 0;
   int max_cams = 1;
   for (int i = 0; i < n; ++i) {
-    const ProbBytes pb = prob_bytes(prec, pr[i].n_cams, pr[i].n_pts, pr[i].n_obs);
+    npairs[i] = count_pairs(pr[i]);
+    if (npairs[i] > (int64_t)INT32_MAX - 64) {
+      h->err = "ba_solve_batch: problem " + std::to_string(i) + " has too many point pairs";
+      return BA_ERR_INVALID_ARG;
+    }
+    const ProbBytes pb = prob_bytes(prec, pr[i].n_cams, pr[i].n_pts, pr[i].n_obs, npairs[i]);
     b->in_off[i] = in;
     b->out_off[i] = out;
     work_off[i] = work;
@@ -471,9 +524,20 @@ ba_status prepare(ba_handle* h, ba_batch* b, int32_t n, const ba_problem* pr) {
     h->err = "ba_solve_batch: pinned host allocation failed";
     return BA_ERR_OOM;
   }
+  if (h->opts.profile && !b->d_phase) {
+    b->d_phase = (unsigned long long*)dev_alloc(h, sizeof(unsigned long long) * kPhaseCount);
+    if (cudaHostAlloc((void**)&b->h_phase, sizeof(unsigned long long) * kPhaseCount,
+                      cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      dev_free(h, b->d_phase);
+      b->d_phase = nullptr;
+      b->h_phase = nullptr;
+    }
+  }
   if (!grow_dev(h, b->d_probs, b->probs_cap, (size_t)n) ||
       !grow_dev(h, b->d_work, b->work_cap, (size_t)n) ||
-      (!b->d_queue && !(b->d_queue = (unsigned*)dev_alloc(h, 64)))) {
+      (!b->d_queue && !(b->d_queue = (unsigned*)dev_alloc(h, 64))) ||
+      (h->opts.profile && !b->d_phase)) {
     h->err = "ba_solve_batch: out of device memory";
     return BA_ERR_OOM;
   }
@@ -490,6 +554,7 @@ ba_status prepare(ba_handle* h, ba_batch* b, int32_t n, const ba_problem* pr) {
     p.iters = iters;
     p.K = Intrinsics{pr[i].K.fx, pr[i].K.fy, pr[i].K.cx, pr[i].K.cy};
     p.phase = kPhaseSetup;
+    p.npairs = npairs[i];
     assign_prob(prec, p, din + b->in_off[i], dout + b->out_off[i], dwork + work_off[i]);
   }
   std::vector<int32_t> ord(n);
@@ -503,8 +568,14 @@ ba_status prepare(ba_handle* h, ba_batch* b, int32_t n, const ba_problem* pr) {
   return BA_OK;
 }
 
+// An event record that becomes an event node when the stream is captured.
+cudaError_t record(cudaEvent_t e, cudaStream_t s, bool capturing) {
+  return capturing ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) : cudaEventRecord(e, s);
+}
+
 // Record the copy-in, launch and copy-out on the handle's stream.
-ba_status enqueue(ba_handle* h, ba_batch* b, int threads, int ctas_per_sm, bool copies) {
+ba_status enqueue(ba_handle* h, ba_batch* b, int threads, int ctas_per_sm, bool copies,
+                  bool capturing) {
   size_t smem = 0;
   int grid = 0;
   std::string why;
@@ -515,29 +586,35 @@ ba_status enqueue(ba_handle* h, ba_batch* b, int threads, int ctas_per_sm, bool 
   }
   cudaStream_t s = h->stream;
   if (copies) {
-    BCK(cudaEventRecordWithFlags(b->ev[0], s, cudaEventRecordExternal));
+    BCK(record(b->ev[0], s, capturing));
     BCK(cudaMemcpyAsync(b->arena, b->h_in, b->in_bytes, cudaMemcpyHostToDevice, s));
   }
   BCK(cudaMemcpyAsync(b->d_probs, b->h_probs, sizeof(BProb) * b->n, cudaMemcpyHostToDevice, s));
   BCK(cudaMemcpyAsync(b->d_work, b->h_work, sizeof(int32_t) * b->n, cudaMemcpyHostToDevice, s));
   BCK(cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned), s));
-  if (copies) BCK(cudaEventRecordWithFlags(b->ev[1], s, cudaEventRecordExternal));
+  if (b->d_phase)
+    BCK(cudaMemsetAsync(b->d_phase, 0, sizeof(unsigned long long) * kPhaseCount, s));
+  if (copies) BCK(record(b->ev[1], s, capturing));
   BatchRun a{};
   a.probs = b->d_probs;
   a.work = b->d_work;
   a.n_work = b->n;
   a.queue = b->d_queue;
   a.iters_per_tick = 0;
+  a.phase_ns = b->d_phase;
   a.huber_delta = h->opts.huber_delta;
   a.mu0 = h->opts.mu0;
   a.mu_min = h->opts.mu_min >= 0 ? h->opts.mu_min
                                  : (h->opts.precision == BA_FP32 ? kMuMinFp32 : 0.0);
   BCK(launch_batch(h->opts.precision, threads, grid, smem, a, s));
-  if (copies) BCK(cudaEventRecordWithFlags(b->ev[2], s, cudaEventRecordExternal));
+  if (copies) BCK(record(b->ev[2], s, capturing));
   BCK(cudaMemcpyAsync(b->h_probs, b->d_probs, sizeof(BProb) * b->n, cudaMemcpyDeviceToHost, s));
+  if (b->d_phase)
+    BCK(cudaMemcpyAsync(b->h_phase, b->d_phase, sizeof(unsigned long long) * kPhaseCount,
+                        cudaMemcpyDeviceToHost, s));
   if (copies) {
     BCK(cudaMemcpyAsync(b->h_out, b->arena + b->in_bytes, b->out_bytes, cudaMemcpyDeviceToHost, s));
-    BCK(cudaEventRecordWithFlags(b->ev[3], s, cudaEventRecordExternal));
+    BCK(record(b->ev[3], s, capturing));
   }
   return BA_OK;
 }
@@ -545,7 +622,7 @@ ba_status enqueue(ba_handle* h, ba_batch* b, int threads, int ctas_per_sm, bool 
 ba_status run(ba_handle* h, ba_batch* b, int threads, int ctas_per_sm, bool copies) {
   const bool graph = h->opts.use_graph && copies;
   if (!graph) {
-    ba_status st = enqueue(h, b, threads, ctas_per_sm, copies);
+    ba_status st = enqueue(h, b, threads, ctas_per_sm, copies, false);
     if (st != BA_OK) return st;
     BCK(cudaStreamSynchronize(h->stream));
     return BA_OK;
@@ -562,7 +639,7 @@ ba_status run(ba_handle* h, ba_batch* b, int threads, int ctas_per_sm, bool copi
     // the kernel's smem attribute is set outside capture by a plain plan
     cudaGraph_t g = nullptr;
     BCK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    ba_status st = enqueue(h, b, threads, ctas_per_sm, copies);
+    ba_status st = enqueue(h, b, threads, ctas_per_sm, copies, true);
     cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     if (st != BA_OK) {
       if (g) cudaGraphDestroy(g);
@@ -718,7 +795,7 @@ ba_status ba_tune_batch(ba_handle* h, int32_t n, const ba_problem* problems,
         for (int rep = 0; rep < 3 && ok; ++rep) {
           std::copy(fresh.begin(), fresh.end(), b->h_probs);
           cudaEventRecord(e0, h->stream);
-          if (enqueue(h, b, th, cps, false) != BA_OK) ok = false;
+          if (enqueue(h, b, th, cps, false, false) != BA_OK) ok = false;
           cudaEventRecord(e1, h->stream);
           if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
             cudaEventDestroy(e0);

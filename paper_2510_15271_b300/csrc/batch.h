@@ -23,6 +23,7 @@ constexpr int kBatchMaxPts = 1 << 18;     // fixed-shape point sums (256 chunks)
 constexpr int kSumChunk = 1024;           // elements per fixed-shape sum chunk
 constexpr int kSumMaxChunks = 256;
 constexpr int kPanel = 32;                // Cholesky panel width
+constexpr int kPairItem = 32;             // pairs per Schur work item
 constexpr int kBatchMaxThreads = 512;
 
 // One problem, device-resident.  Pointers address the engine's arena.
@@ -68,6 +69,19 @@ struct BProb {
   double* cpart;  // [2C] per-camera partial sums
   double* ppart;  // [P] per-point partial sums
   int32_t* scratch;  // setup scratch (aliases W)
+  // Schur pair list, built once per problem: every (k1, k2) with k1 in
+  // camera i1, k2 an observation of the same point in camera i2 >= i1,
+  // grouped by output block (i1, i2) (row-major), and cut into items of at
+  // most kPairItem pairs (one thread accumulates one item)
+  int64_t npairs;
+  int nitems_cap;
+  int32_t* pair_k1;   // [npairs] camera-order index of k1
+  int32_t* pair_q2;   // [npairs] point-order index of k2
+  int32_t* blk_ptr;   // [C*C + 1] first pair of block i1*C + i2
+  int32_t* blk_item;  // [C*C + 1] first item of each block
+  int32_t* item_beg;  // [nitems_cap] first pair of each item
+  void* Y;            // [N][W stride] Y_k = W_k V*_j^-1, camera order
+  void* part;         // [nitems_cap][36] item sums
   double cost[BA_MAX_ITERS + 1];
   double mu_hist[BA_MAX_ITERS];
   uint8_t accepted[BA_MAX_ITERS];
@@ -81,13 +95,34 @@ struct BatchRun {
   unsigned* queue;      // work counter (zeroed before the launch)
   int iters_per_tick;   // <= 0: run every problem to completion
   double huber_delta, mu0, mu_min;
+  int32_t* done_list;       // optional: ids of problems finished by this launch
+  unsigned* done_count;     //   and their count (zeroed before the launch)
+  unsigned long long* phase_ns;  // optional: [kPhaseCount] CTA-ns per phase
+};
+
+// Phases of the per-phase timing.
+enum : int {
+  kPhIdle = 0,   // taking work
+  kPhSetup,      // validation, sorts, state
+  kPhLin,        // U, g_c, V, g_p, W
+  kPhDamp,       // V*^-1, e
+  kPhSchur,      // S, b
+  kPhCholesky,   // S = L L^T
+  kPhSolve,      // triangular solves
+  kPhTrial,      // back-substitution, retraction, model decrease
+  kPhCost,       // cost passes (initial, trial, final) and outputs
+  kPhGain,       // accept / reject, commit
+  kPhaseCount
 };
 
 // Bytes of arena one problem needs (inputs, outputs, work), 256-aligned parts.
 struct ProbBytes {
   size_t in, out, work;
 };
-ProbBytes prob_bytes(int precision, int C, int P, int64_t N);
+ProbBytes prob_bytes(int precision, int C, int P, int64_t N, int64_t npairs);
+// sum over points of L (L + 1) / 2 (L = observations of the point; indices
+// out of range are skipped: the device rejects such problems)
+int64_t count_pairs(const ba_problem& q);
 
 // Point a descriptor's arrays into the given input / output / work blocks.
 void assign_prob(int precision, BProb& p, char* in, char* out, char* work);

@@ -194,6 +194,30 @@ struct Smem {
   int flag;
   int item;
   int ok;
+  int done;
+};
+
+__device__ __forceinline__ unsigned long long gtime_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Optional per-phase wall time (thread 0 of each CTA adds the time since its
+// previous mark to acc[phase]); off when acc is null.
+struct PhaseClock {
+  unsigned long long* acc;
+  unsigned long long t;
+  __device__ explicit PhaseClock(unsigned long long* a) : acc(a), t(0) {
+    if (acc && threadIdx.x == 0) t = gtime_ns();
+  }
+  __device__ __forceinline__ void mark(int phase) {
+    if (acc && threadIdx.x == 0) {
+      const unsigned long long now = gtime_ns();
+      atomicAdd(acc + phase, now - t);
+      t = now;
+    }
+  }
 };
 
 // --------------------------------------------------------------------------- setup
@@ -201,8 +225,10 @@ struct Smem {
 // Validate the inputs, sort the observations by (camera, point) and by
 // (point, camera) with stable counting sorts, and load the state.  Sets
 // p.status (0 or validation bits).
+__device__ void build_pairs(BProb& p, int* wsm, Smem& sm);
+
 template <typename T>
-__device__ void setup_problem(BProb& p, Smem& sm) {
+__device__ void setup_problem(BProb& p, Smem& sm, int* wsm) {
   const int C = p.C, P = p.P, N = p.N;
   const int tid = threadIdx.x, NT = blockDim.x;
   int32_t* cam_cnt = p.cam_ptr;
@@ -340,6 +366,7 @@ __device__ void setup_problem(BProb& p, Smem& sm) {
     if (p.X32) write_pt32(x, y, z, p.X32 + kPt32 * j);
   }
   __syncthreads();
+  build_pairs(p, wsm, sm);
   if (tid == 0) p.status = 0;
   __syncthreads();
 }
@@ -518,118 +545,208 @@ __device__ void damp_pts(const BProb& p, double mu) {
   }
 }
 
-// Shared memory one Schur row warp uses: the 6 x n row block and Y of 32
-// observations.
+// Dynamic shared memory of the kernel: the Cholesky diagonal block, or the
+// per-warp column counters of the pair-list build, whichever is larger.
 template <typename T>
-__host__ __device__ inline size_t row_warp_bytes(int C) {
-  return ((size_t)6 * 6 * C + 32 * 18) * sizeof(T);
+__host__ __device__ inline size_t batch_dyn_bytes(int threads, int C) {
+  const size_t sd = (size_t)kPanel * (kPanel + 1) * sizeof(T);
+  const size_t cnt = (size_t)(threads / 32) * C * sizeof(int);
+  return sd > cnt ? sd : cnt;
 }
 
-// Row blocks of S and b.  Warp w < nrw handles camera rows w, w + nrw, ...
-// The row's observations k1 are taken 32 at a time (lane l computes Y_k1 =
-// W_k1 V*_j^-1 for its own k1); then, k1 by k1 in order, lanes (p, c) =
-// (lane / 6, lane % 6) add Y_k1 W_k2[c]^T for partner p of k1 (the point's
-// observations in cameras >= i1, all in distinct cameras) into column
-// 6 cam(k2) + c of the row block.  Each output element is updated by one
-// lane at a time in a fixed order.
+// Y_k = W_k V*_j^-1 for every observation (camera order) and b_i = -g_c,i +
+// sum_k W_k e_j: warp per camera, lanes strided over its observations.
 template <typename T>
-__device__ void schur_rows(const BProb& p, double mu, T* rows, int nrw) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (warp >= nrw) return;
-  const int C = p.C, n = 6 * C;
-  T* acc = rows + (size_t)warp * (row_warp_bytes<T>(C) / sizeof(T));
-  T* Ys = acc + (size_t)6 * n;
+__device__ void schur_y(const BProb& p) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const T* W = (const T*)p.W;
   const T* eg = (const T*)p.e;
-  const int pg = lane / 6, pc = lane - 6 * (lane / 6);
-  for (int i1 = warp; i1 < C; i1 += nrw) {
-    const bool fixed1 = p.fixed[i1] != 0;
-    for (int e = lane; e < 6 * n; e += 32) acc[e] = T(0);
-    __syncwarp();
-    double bsum = 0.0;  // lane r < 6: row r of sum_k W_k e_j
-    const int kb = p.cam_ptr[i1], ke = p.cam_ptr[i1 + 1];
-    if (!fixed1) {
-      for (int base = kb; base < ke; base += 32) {
-        const int k1 = base + lane;
-        int q1 = 0, qe = 0;
-        double bl[6] = {0, 0, 0, 0, 0, 0};
-        if (k1 < ke) {
-          const int j = p.oc_pt[k1];
-          q1 = p.q_of[k1];
-          qe = p.pt_ptr[j + 1];
-          T Wk[18];
-          ld_w<T>(W, q1, Wk);
-          const double* vi = p.Vinv + 6 * j;
-          const T v00 = (T)vi[0], v01 = (T)vi[1], v02 = (T)vi[2], v11 = (T)vi[3], v12 = (T)vi[4],
-                  v22 = (T)vi[5];
-          const T e0 = eg[3 * j], e1 = eg[3 * j + 1], e2 = eg[3 * j + 2];
-          T* Y = Ys + 18 * lane;
-#pragma unroll
-          for (int a = 0; a < 6; ++a) {
-            const T w0 = Wk[3 * a], w1 = Wk[3 * a + 1], w2 = Wk[3 * a + 2];
-            Y[3 * a] = w0 * v00 + w1 * v01 + w2 * v02;
-            Y[3 * a + 1] = w0 * v01 + w1 * v11 + w2 * v12;
-            Y[3 * a + 2] = w0 * v02 + w1 * v12 + w2 * v22;
-            bl[a] = (double)(w0 * e0 + w1 * e1 + w2 * e2);
-          }
-        }
+  T* Yg = (T*)p.Y;
+  for (int i = warp; i < p.C; i += nw) {
+    const bool fixed = p.fixed[i] != 0;
+    double bl[6] = {0, 0, 0, 0, 0, 0};
+    if (!fixed) {
+      for (int k = p.cam_ptr[i] + lane; k < p.cam_ptr[i + 1]; k += 32) {
+        const int j = p.oc_pt[k];
+        T Wk[18], Y[18];
+        ld_w<T>(W, p.q_of[k], Wk);
+        const double* vi = p.Vinv + 6 * j;
+        const T v00 = (T)vi[0], v01 = (T)vi[1], v02 = (T)vi[2], v11 = (T)vi[3], v12 = (T)vi[4],
+                v22 = (T)vi[5];
+        const T e0 = eg[3 * j], e1 = eg[3 * j + 1], e2 = eg[3 * j + 2];
 #pragma unroll
         for (int a = 0; a < 6; ++a) {
-          const double s = warp_sum(bl[a]);
-          if (lane == a) bsum += s;
+          const T w0 = Wk[3 * a], w1 = Wk[3 * a + 1], w2 = Wk[3 * a + 2];
+          Y[3 * a] = w0 * v00 + w1 * v01 + w2 * v02;
+          Y[3 * a + 1] = w0 * v01 + w1 * v11 + w2 * v12;
+          Y[3 * a + 2] = w0 * v02 + w1 * v12 + w2 * v22;
+          bl[a] += (double)(w0 * e0 + w1 * e1 + w2 * e2);
         }
-        __syncwarp();
-        const int nb = min(32, ke - base);
-        for (int t = 0; t < nb; ++t) {
-          const int tq1 = __shfl_sync(0xffffffffu, q1, t);
-          const int m = __shfl_sync(0xffffffffu, qe, t) - tq1;
-          const T* Y = Ys + 18 * t;
-          for (int p0 = 0; p0 < m; p0 += 5) {
-            const int pi = p0 + pg;
-            if (lane < 30 && pi < m) {
-              const int q2 = tq1 + pi;
-              const int c2 = p.po_cam[q2];
-              const T* w2 = W + (int64_t)q2 * WS<T>::v + 3 * pc;
-              const T wa = w2[0], wb = w2[1], wc = w2[2];
-              T* out = acc + 6 * c2 + pc;
-#pragma unroll
-              for (int r = 0; r < 6; ++r)
-                out[r * n] += Y[3 * r] * wa + Y[3 * r + 1] * wb + Y[3 * r + 2] * wc;
-            }
-          }
-          __syncwarp();
-        }
+        st_w<T>(Yg, k, Y);
       }
     }
-    // write the row block (upper part) and its mirror
+#pragma unroll
+    for (int a = 0; a < 6; ++a) bl[a] = warp_sum(bl[a]);
+    if (lane < 6) {
+      double bi = 0.0;
+#pragma unroll
+      for (int a = 0; a < 6; ++a)
+        if (lane == a) bi = bl[a];
+      const double gci = (double)((const T*)p.gc)[6 * i + lane];
+      const double v = fixed ? 0.0 : (-gci + bi);
+      ((T*)p.b)[6 * i + lane] = (T)v;
+      ((T*)p.x)[6 * i + lane] = (T)v;
+    }
+  }
+}
+
+// Item sums: thread per item, sum over its pairs of Y_k1 W_k2^T (6 x 6) in a
+// fixed order into part[item].
+template <typename T>
+__device__ void schur_items(const BProb& p) {
+  const int C = p.C;
+  const int nitems = p.blk_item[C * C];
+  const T* Yg = (const T*)p.Y;
+  const T* W = (const T*)p.W;
+  T* part = (T*)p.part;
+  for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
+    const int pb = p.item_beg[it];
+    // the item's block: the last block whose first item is <= it
+    int lo = 0, hi = C * C - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (p.blk_item[mid] <= it) lo = mid;
+      else hi = mid - 1;
+    }
+    const int pe = min(pb + kPairItem, p.blk_ptr[lo + 1]);
+    T acc[36];
+#pragma unroll
+    for (int e = 0; e < 36; ++e) acc[e] = T(0);
+    for (int q = pb; q < pe; ++q) {
+      T y[18], w[18];
+      ld_w<T>(Yg, p.pair_k1[q], y);
+      ld_w<T>(W, p.pair_q2[q], w);
+#pragma unroll
+      for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+          acc[6 * r + c] += y[3 * r] * w[3 * c] + y[3 * r + 1] * w[3 * c + 1] + y[3 * r + 2] * w[3 * c + 2];
+    }
+    T* o = part + (int64_t)it * 36;
+#pragma unroll
+    for (int e = 0; e < 36; ++e) o[e] = acc[e];
+  }
+}
+
+// S from the item sums: thread per (upper block, row); the items of a block
+// are added in order.  Diagonal blocks get U*; fixed cameras identity rows.
+template <typename T>
+__device__ void schur_blocks(const BProb& p, double mu) {
+  const int C = p.C, n = 6 * C;
+  const T* part = (const T*)p.part;
+  T* S = (T*)p.S;
+  for (int t = threadIdx.x; t < 6 * C * C; t += blockDim.x) {
+    const int blk = t / 6, r = t - 6 * blk;
+    const int i1 = blk / C, i2 = blk - C * i1;
+    if (i2 < i1) continue;
+    const bool fixed1 = p.fixed[i1] != 0;
+    T row[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    if (!fixed1)
+      for (int it = p.blk_item[blk]; it < p.blk_item[blk + 1]; ++it) {
+        const T* o = part + (int64_t)it * 36 + 6 * r;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) row[c] += o[c];
+      }
     const T* U = (const T*)p.U + 36 * i1;
-    T* S = (T*)p.S;
-    for (int e = lane; e < 6 * n; e += 32) {
-      const int r = e / n, col = e - r * n;
-      const int i2 = col / 6, c = col - 6 * i2;
-      if (i2 < i1) continue;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
       T val;
       if (fixed1) {
         val = (i2 == i1 && r == c) ? T(1) : T(0);
       } else {
-        val = -acc[e];
+        val = -row[c];
         if (i2 == i1) {
           T u = U[6 * r + c];
           if (r == c) u = (T)((double)u + mu * fmax((double)u, kDiagMin));
           val += u;
         }
       }
-      S[(int64_t)(6 * i1 + r) * n + col] = val;
-      if (i2 > i1) S[(int64_t)col * n + 6 * i1 + r] = val;
+      const int gr = 6 * i1 + r, gc = 6 * i2 + c;
+      S[(int64_t)gr * n + gc] = val;
+      if (i2 > i1) S[(int64_t)gc * n + gr] = val;
     }
-    if (lane < 6) {
-      const double gci = (double)((const T*)p.gc)[6 * i1 + lane];
-      const double bi = fixed1 ? 0.0 : (-gci + bsum);
-      ((T*)p.b)[6 * i1 + lane] = (T)bi;
-      ((T*)p.x)[6 * i1 + lane] = (T)bi;
+  }
+}
+
+// Schur pair list (once per problem, after the layout): warp per camera row
+// i1 counts its pairs per column block in shared memory, a CTA scan gives
+// the block offsets, then each row places its pairs: k1 taken 32 at a time,
+// partner p of every lane at step p, lanes with the same block ranked by
+// lane (match_any), so the order inside a block is fixed by the data.
+// Finally the blocks are cut into items of at most kPairItem pairs.
+__device__ void build_pairs(BProb& p, int* wsm, Smem& sm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int C = p.C;
+  int* cnt = wsm + warp * C;  // this warp's per-column counters
+  for (int i1 = warp; i1 < C; i1 += nw) {
+    for (int c = lane; c < C; c += 32) cnt[c] = 0;
+    __syncwarp();
+    for (int k = p.cam_ptr[i1] + lane; k < p.cam_ptr[i1 + 1]; k += 32) {
+      const int q1 = p.q_of[k], qe = p.pt_ptr[p.oc_pt[k] + 1];
+      for (int q = q1; q < qe; ++q) atomicAdd(&cnt[p.po_cam[q]], 1);
+    }
+    __syncwarp();
+    for (int c = lane; c < C; c += 32) p.blk_ptr[i1 * C + c] = cnt[c];
+    __syncwarp();
+  }
+  if (threadIdx.x == 0) p.blk_ptr[C * C] = 0;
+  __syncthreads();
+  cta_exclusive_scan(p.blk_ptr, C * C + 1, sm.scan);
+  for (int i1 = warp; i1 < C; i1 += nw) {
+    for (int c = lane; c < C; c += 32) cnt[c] = p.blk_ptr[i1 * C + c];
+    __syncwarp();
+    const int kb = p.cam_ptr[i1], ke = p.cam_ptr[i1 + 1];
+    for (int base = kb; base < ke; base += 32) {
+      const int k1 = base + lane;
+      int q1 = 0, m = 0;
+      if (k1 < ke) {
+        q1 = p.q_of[k1];
+        m = p.pt_ptr[p.oc_pt[k1] + 1] - q1;
+      }
+      int mmax = m;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mmax = max(mmax, __shfl_xor_sync(0xffffffffu, mmax, o));
+      for (int s = 0; s < mmax; ++s) {
+        const bool has = s < m;
+        const int c2 = has ? p.po_cam[q1 + s] : -1 - lane;
+        const unsigned peers = __match_any_sync(0xffffffffu, c2);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        if (has) {
+          const int pos = cnt[c2] + rank;
+          p.pair_k1[pos] = k1;
+          p.pair_q2[pos] = q1 + s;
+        }
+        __syncwarp();
+        if (has && rank == 0) cnt[c2] += __popc(peers);
+        __syncwarp();
+      }
     }
     __syncwarp();
   }
+  __syncthreads();
+  // items
+  for (int b = threadIdx.x; b < C * C; b += blockDim.x) {
+    const int len = p.blk_ptr[b + 1] - p.blk_ptr[b];
+    p.blk_item[b] = (len + kPairItem - 1) / kPairItem;
+  }
+  if (threadIdx.x == 0) p.blk_item[C * C] = 0;
+  __syncthreads();
+  cta_exclusive_scan(p.blk_item, C * C + 1, sm.scan);
+  for (int b = threadIdx.x; b < C * C; b += blockDim.x) {
+    const int i0 = p.blk_item[b], i1 = p.blk_item[b + 1];
+    for (int t = i0; t < i1; ++t) p.item_beg[t] = p.blk_ptr[b] + (t - i0) * kPairItem;
+  }
+  __syncthreads();
 }
 
 // Blocked right-looking Cholesky S = L L^T in place (lower triangle), panel
@@ -904,7 +1021,7 @@ __device__ void lm_begin(BProb& p, const BatchRun& a, Smem& sm) {
 }
 
 template <typename T>
-__device__ void lm_iteration(BProb& p, const BatchRun& a, Smem& sm, T* dyn, int nrw) {
+__device__ void lm_iteration(BProb& p, const BatchRun& a, Smem& sm, T* dyn, PhaseClock& pc) {
   const T delta = (T)a.huber_delta;
   const double mu = fmax(p.mu, a.mu_min);  // damping of the linear system
   if (p.need_lin) {
@@ -912,23 +1029,34 @@ __device__ void lm_iteration(BProb& p, const BatchRun& a, Smem& sm, T* dyn, int 
     lin_pts<T>(p, delta);
     __syncthreads();
   }
+  pc.mark(kPhLin);
   damp_pts<T>(p, mu);
   __syncthreads();
-  schur_rows<T>(p, mu, dyn, nrw);
+  pc.mark(kPhDamp);
+  schur_y<T>(p);
   __syncthreads();
+  schur_items<T>(p);
+  __syncthreads();
+  schur_blocks<T>(p, mu);
+  __syncthreads();
+  pc.mark(kPhSchur);
   const int n = 6 * p.C;
   const bool ok = cholesky<T>((T*)p.S, n, dyn, sm);
+  pc.mark(kPhCholesky);
   double Fn = 0.0, hp = 0.0, hc = 0.0;
   if (ok) {
     chol_solve<T>((const T*)p.S, n, (T*)p.x);
+    pc.mark(kPhSolve);
     backsub_pts<T>(p, mu);
     retract_cams<T>(p, mu);
     __syncthreads();
     hp = fixed_sum(p.ppart, p.P, sm.chunks);
     hc = fixed_sum(p.cpart + p.C, p.C, sm.chunks);
+    pc.mark(kPhTrial);
     cost_pass<T>(p, true, delta, 0);
     __syncthreads();
     Fn = fixed_sum(p.cpart, p.C, sm.chunks);
+    pc.mark(kPhCost);
   }
   if (threadIdx.x == 0) {
     const int it = p.iter;
@@ -960,6 +1088,7 @@ __device__ void lm_iteration(BProb& p, const BatchRun& a, Smem& sm, T* dyn, int 
   __syncthreads();
   if (p.need_lin) commit_state(p);  // need_lin was just set exactly on acceptance
   __syncthreads();
+  pc.mark(kPhGain);
 }
 
 template <typename T>
@@ -986,41 +1115,56 @@ __device__ void lm_end(BProb& p, const BatchRun& a, Smem& sm) {
   __syncthreads();
 }
 
+// Record a finished problem in the launch's done list (when there is one).
+__device__ void note_done(const BatchRun& a, int id) {
+  if (a.done_list && threadIdx.x == 0) a.done_list[atomicAdd(a.done_count, 1u)] = id;
+}
+
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) k_batch(BatchRun a, int dyn_bytes) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ Smem sm;
   T* dyn = reinterpret_cast<T*>(smem_raw);
+  PhaseClock pc(a.phase_ns);
   for (;;) {
     if (threadIdx.x == 0) sm.item = (int)atomicAdd(a.queue, 1u);
     __syncthreads();
     const int w = sm.item;
     __syncthreads();
     if (w >= a.n_work) break;
-    BProb& p = a.probs[a.work[w]];
+    const int id = a.work[w];
+    BProb& p = a.probs[id];
     if (p.phase == kPhaseDone) continue;
+    pc.mark(kPhIdle);
     if (p.phase == kPhaseSetup) {
-      setup_problem<T>(p, sm);
+      setup_problem<T>(p, sm, reinterpret_cast<int*>(smem_raw));
+      pc.mark(kPhSetup);
       if (p.status != 0) {
         if (threadIdx.x == 0) p.phase = kPhaseDone;
         __syncthreads();
+        note_done(a, id);
         continue;
       }
       lm_begin<T>(p, a, sm);
+      pc.mark(kPhCost);
     }
     int todo = p.iters - p.iter;
     if (a.iters_per_tick > 0 && todo > a.iters_per_tick) todo = a.iters_per_tick;
-    const int nrw = min((int)(NT / 32), (int)(dyn_bytes / row_warp_bytes<T>(p.C)));
-    if (nrw < 1) {  // the host sizes shared memory for its largest problem
+    if ((size_t)dyn_bytes < batch_dyn_bytes<T>(NT, p.C)) {  // sized by the host
       if (threadIdx.x == 0) {
         p.error |= kErrTooLarge;
         p.phase = kPhaseDone;
       }
       __syncthreads();
+      note_done(a, id);
       continue;
     }
-    for (int it = 0; it < todo; ++it) lm_iteration<T>(p, a, sm, dyn, nrw);
-    if (p.iter >= p.iters) lm_end<T>(p, a, sm);
+    for (int it = 0; it < todo; ++it) lm_iteration<T>(p, a, sm, dyn, pc);
+    if (p.iter >= p.iters) {
+      lm_end<T>(p, a, sm);
+      pc.mark(kPhCost);
+      note_done(a, id);
+    }
   }
 }
 
@@ -1047,11 +1191,8 @@ int occupancy_t(size_t smem) {
 }  // namespace
 
 size_t batch_smem_bytes(int precision, int threads, int max_cams) {
-  const size_t per = precision == BA_FP32 ? row_warp_bytes<float>(max_cams)
-                                          : row_warp_bytes<double>(max_cams);
-  const size_t sd = (size_t)kPanel * (kPanel + 1) * (precision == BA_FP32 ? 4 : 8);
-  const size_t want = per * (size_t)(threads / 32);
-  return want > sd ? want : sd;
+  return precision == BA_FP32 ? batch_dyn_bytes<float>(threads, max_cams)
+                              : batch_dyn_bytes<double>(threads, max_cams);
 }
 
 cudaError_t launch_batch(int precision, int threads, int grid, size_t smem, const BatchRun& a,

@@ -43,8 +43,11 @@ using Clock = std::chrono::steady_clock;
 struct Req {
   uint64_t id = 0;
   int C = 0, P = 0, N = 0;
+  int64_t npairs = 0;
   Intrinsics K{};
-  std::vector<char> in;  // packed input block
+  std::vector<char> in;  // packed input block (when the pinned pool is full)
+  char* pin = nullptr;   // packed input block in the pinned pool
+  size_t pin_off = 0;
   double* user_q = nullptr;
   double* user_p = nullptr;
   ProbBytes bytes{};
@@ -118,6 +121,11 @@ struct ba_server {
   unsigned* d_queue = nullptr;
   char* h_stage = nullptr;  // pinned staging of admitted inputs
   size_t stage_bytes = 0;
+  char* h_pool = nullptr;   // pinned pool the submitting threads pack inputs into
+  Arena pool;
+  int32_t* d_done = nullptr;   // ids finished by a tick, and their count
+  unsigned* d_done_count = nullptr;
+  int32_t* h_done = nullptr;   // pinned: [0] count, [1..] ids
   int threads = 256;
   // statistics
   uint64_t ticks = 0, completed = 0;
@@ -193,7 +201,8 @@ bool tick(ba_server* s) {
   }
   // copy the admitted requests in and initialise their descriptors
   size_t need = 0;
-  for (Req* r : admitted) need += r->bytes.in;
+  for (Req* r : admitted)
+    if (!r->pin) need += r->bytes.in;
   if (!grow_stage(s, need)) {
     std::lock_guard<std::mutex> lk(s->mu);
     fail_all(s, "pinned staging allocation failed");
@@ -203,10 +212,14 @@ bool tick(ba_server* s) {
   int max_cams = 1;
   for (int i : resident) max_cams = std::max(max_cams, s->slots[i]->C);
   for (Req* r : admitted) {
-    memcpy(s->h_stage + so, r->in.data(), r->bytes.in);
     char* blk = s->base + r->off;
-    cudaMemcpyAsync(blk, s->h_stage + so, r->bytes.in, cudaMemcpyHostToDevice, st);
-    so += r->bytes.in;
+    if (r->pin) {
+      cudaMemcpyAsync(blk, r->pin, r->bytes.in, cudaMemcpyHostToDevice, st);
+    } else {
+      memcpy(s->h_stage + so, r->in.data(), r->bytes.in);
+      cudaMemcpyAsync(blk, s->h_stage + so, r->bytes.in, cudaMemcpyHostToDevice, st);
+      so += r->bytes.in;
+    }
     BProb& p = s->h_probs[r->slot];
     memset(&p, 0, sizeof(p));
     p.C = r->C;
@@ -215,6 +228,7 @@ bool tick(ba_server* s) {
     p.iters = h->opts.max_lm_iters;
     p.K = r->K;
     p.phase = kPhaseSetup;
+    p.npairs = r->npairs;
     assign_prob(prec, p, blk, blk + r->bytes.in, blk + r->bytes.in + r->bytes.out);
     cudaMemcpyAsync(s->d_probs + r->slot, &p, sizeof(BProb), cudaMemcpyHostToDevice, st);
   }
@@ -230,6 +244,7 @@ bool tick(ba_server* s) {
   for (int i = 0; i < nw; ++i) s->h_work[i] = resident[i];
   cudaMemcpyAsync(s->d_work, s->h_work, sizeof(int32_t) * nw, cudaMemcpyHostToDevice, st);
   cudaMemsetAsync(s->d_queue, 0, sizeof(unsigned), st);
+  cudaMemsetAsync(s->d_done_count, 0, sizeof(unsigned), st);
   size_t smem = 0;
   int grid = 0;
   std::string why;
@@ -244,16 +259,28 @@ bool tick(ba_server* s) {
   a.n_work = nw;
   a.queue = s->d_queue;
   a.iters_per_tick = 1;
+  a.done_list = s->d_done;
+  a.done_count = s->d_done_count;
   a.huber_delta = h->opts.huber_delta;
   a.mu0 = h->opts.mu0;
   a.mu_min = h->opts.mu_min >= 0 ? h->opts.mu_min : (prec == BA_FP32 ? kMuMinFp32 : 0.0);
   const auto t0 = Clock::now();
   cudaError_t e = launch_batch(prec, s->threads, std::min(grid, std::max(nw, 1)), smem, a, st);
-  int hi = 0;
-  for (int i : resident) hi = std::max(hi, i + 1);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(s->h_probs, s->d_probs, sizeof(BProb) * hi, cudaMemcpyDeviceToHost, st);
+    e = cudaMemcpyAsync(s->h_done, s->d_done_count, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->h_done + 1, s->d_done, sizeof(int32_t) * nw, cudaMemcpyDeviceToHost,
+                        st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  // the admitted requests' pinned input blocks are on the device now
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (Req* r : admitted)
+      if (r->pin) {
+        s->pool.release(r->pin_off, r->bytes.in);
+        r->pin = nullptr;
+      }
+  }
   if (e != cudaSuccess) {
     std::lock_guard<std::mutex> lk(s->mu);
     fail_all(s, std::string("tick failed: ") + cudaGetErrorString(e));
@@ -263,8 +290,22 @@ bool tick(ba_server* s) {
   s->ticks += 1;
   // finished requests: outputs to the host, memory back to the arena
   std::vector<Req*> fin;
-  for (int i : resident)
-    if (s->h_probs[i].phase == kPhaseDone) fin.push_back(s->slots[i]);
+  const int ndone = std::min((int)(unsigned)s->h_done[0], nw);
+  for (int i = 0; i < ndone; ++i) {
+    const int slot = s->h_done[1 + i];
+    if (slot >= 0 && slot < (int)s->slots.size() && s->slots[slot]) fin.push_back(s->slots[slot]);
+  }
+  for (Req* r : fin)
+    cudaMemcpyAsync(&s->h_probs[r->slot], s->d_probs + r->slot, sizeof(BProb),
+                    cudaMemcpyDeviceToHost, st);
+  if (!fin.empty()) {
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      std::lock_guard<std::mutex> lk(s->mu);
+      fail_all(s, std::string("descriptor copy failed: ") + cudaGetErrorString(e));
+      return false;
+    }
+  }
   for (Req* r : fin) {
     const BProb& p = s->h_probs[r->slot];
     fill_result(p, r->result);
@@ -344,6 +385,10 @@ void destroy_server(ba_handle* h) {
   dev_free(h, s->d_probs);
   dev_free(h, s->d_work);
   dev_free(h, s->d_queue);
+  dev_free(h, s->d_done);
+  dev_free(h, s->d_done_count);
+  if (s->h_done) cudaFreeHost(s->h_done);
+  if (s->h_pool) cudaFreeHost(s->h_pool);
   if (s->h_probs) cudaFreeHost(s->h_probs);
   if (s->h_work) cudaFreeHost(s->h_work);
   if (s->h_stage) cudaFreeHost(s->h_stage);
@@ -380,7 +425,19 @@ ba_status ba_create_server(const ba_options* opts, ba_handle** out) {
   s->d_probs = (BProb*)dev_alloc(h, sizeof(BProb) * ns);
   s->d_work = (int32_t*)dev_alloc(h, sizeof(int32_t) * ns);
   s->d_queue = (unsigned*)dev_alloc(h, 64);
-  if (!s->base || !s->d_probs || !s->d_work || !s->d_queue ||
+  s->d_done = (int32_t*)dev_alloc(h, sizeof(int32_t) * ns);
+  s->d_done_count = (unsigned*)dev_alloc(h, 64);
+  // pinned pool for packed inputs: a quarter of the arena, at most 2 GiB
+  const size_t pool_bytes = std::min<size_t>(bytes / 4, (size_t)2 << 30);
+  if (cudaHostAlloc((void**)&s->h_pool, pool_bytes, cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    s->h_pool = nullptr;
+  } else {
+    s->pool.init(pool_bytes);
+  }
+  if (!s->base || !s->d_probs || !s->d_work || !s->d_queue || !s->d_done || !s->d_done_count ||
+      cudaHostAlloc((void**)&s->h_done, sizeof(int32_t) * (ns + 1), cudaHostAllocDefault) !=
+          cudaSuccess ||
       cudaHostAlloc((void**)&s->h_probs, sizeof(BProb) * ns, cudaHostAllocDefault) != cudaSuccess ||
       cudaHostAlloc((void**)&s->h_work, sizeof(int32_t) * ns, cudaHostAllocDefault) !=
           cudaSuccess) {
@@ -413,27 +470,42 @@ ba_status ba_submit(ba_handle* h, const ba_problem* req, uint64_t* req_id) {
   r->P = req->n_pts;
   r->N = (int)req->n_obs;
   r->K = Intrinsics{req->K.fx, req->K.fy, req->K.cx, req->K.cy};
-  r->bytes = prob_bytes(h->opts.precision, r->C, r->P, req->n_obs);
+  r->npairs = count_pairs(*req);
+  if (r->npairs > (int64_t)INT32_MAX - 64) {
+    delete r;
+    h->err = "ba_submit: too many point pairs";
+    return BA_ERR_INVALID_ARG;
+  }
+  r->bytes = prob_bytes(h->opts.precision, r->C, r->P, req->n_obs, r->npairs);
   if (block_bytes(r->bytes) > s->arena.size) {
     delete r;
     h->err = "ba_submit: request larger than the whole arena";
     return BA_ERR_OOM;
   }
-  r->in.resize(r->bytes.in);
-  pack_inputs(h->opts.precision, *req, r->in.data());
+  if (s->h_pool) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    size_t off = 0;
+    if (s->pool.alloc(r->bytes.in, off)) {
+      r->pin = s->h_pool + off;
+      r->pin_off = off;
+    }
+  }
+  if (r->pin) {
+    pack_inputs(h->opts.precision, *req, r->pin);
+  } else {
+    r->in.resize(r->bytes.in);
+    pack_inputs(h->opts.precision, *req, r->in.data());
+  }
   r->user_q = req->cam_qt_out;
   r->user_p = req->pts_out;
   {
     std::lock_guard<std::mutex> lk(s->mu);
-    if (!s->fatal.empty()) {
+    if (!s->fatal.empty() || (int)s->waiting.size() >= h->opts.serve_queue) {
+      if (r->pin) s->pool.release(r->pin_off, r->bytes.in);
+      const bool failed = !s->fatal.empty();
+      h->err = failed ? "ba_submit: server failed: " + s->fatal : "ba_submit: waiting queue full";
       delete r;
-      h->err = "ba_submit: server failed: " + s->fatal;
-      return BA_ERR_CUDA;
-    }
-    if ((int)s->waiting.size() >= h->opts.serve_queue) {
-      delete r;
-      h->err = "ba_submit: waiting queue full";
-      return BA_ERR_BUSY;
+      return failed ? BA_ERR_CUDA : BA_ERR_BUSY;
     }
     r->id = s->next_id++;
     r->t_submit = Clock::now();
@@ -470,7 +542,11 @@ ba_status ba_poll(ba_handle* h, uint64_t req_id, ba_result* out) {
     if (r->user_p) memcpy(r->user_p, r->out_p.data(), sizeof(double) * r->out_p.size());
   }
   const ba_status st = (ba_status)r->result.status;
-  if (st != BA_OK) h->err = "ba_poll: request failed";
+  if (st != BA_OK) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    h->err = s->fatal.empty() ? "ba_poll: request failed validation or produced a non-finite cost"
+                              : "ba_poll: server failed: " + s->fatal;
+  }
   delete r;
   return st;
 }

@@ -171,3 +171,11 @@ def test_host_side_argument_checks():
             ba.ba_solve_batch(h, [a])
         with pytest.raises(ba.BAError):
             ba.ba_set_batch_schedule(h, 96, 1)
+
+
+def test_eager_and_graph_launches_agree():
+    ws = _windows(4, seed=19)
+    g, _ = _batch(ws, "fp32", iters=3)
+    e, _ = _batch(ws, "fp32", iters=3, use_graph=0)
+    for a, b in zip(g, e):
+        assert np.array_equal(a.costs(), b.costs())
