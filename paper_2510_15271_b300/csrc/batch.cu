@@ -83,7 +83,9 @@ void carve_work(Carve& c, BProb& p, int precision, int C, int P, int64_t N, int6
   p.oc_pt = c.take<int32_t>((size_t)N);
   p.q_of = c.take<int32_t>((size_t)N);
   p.po_cam = c.take<int32_t>((size_t)N);
+  p.po_k = c.take<int32_t>((size_t)N);
   p.po_uv = c.take_bytes((size_t)N * 2 * t);
+  p.oc_uv = c.take_bytes((size_t)N * 2 * t);
   p.R = c.take<double>((size_t)C * 9);
   p.t = c.take<double>((size_t)C * 3);
   p.Cc = c.take<double>((size_t)C * 3);
@@ -120,7 +122,7 @@ void carve_work(Carve& c, BProb& p, int precision, int C, int P, int64_t N, int6
   p.npairs = npairs;
   p.nitems_cap = items_cap(C, npairs);
   p.pair_k1 = c.take<int32_t>((size_t)npairs);
-  p.pair_q2 = c.take<int32_t>((size_t)npairs);
+  p.pair_k2 = c.take<int32_t>((size_t)npairs);
   p.blk_ptr = c.take<int32_t>((size_t)C * C + 1);
   p.blk_item = c.take<int32_t>((size_t)C * C + 1);
   p.item_beg = c.take<int32_t>((size_t)p.nitems_cap);
@@ -370,8 +372,8 @@ constexpr size_t kStaticSmemReserve = 8192;
 // not fit.
 bool plan_launch(int device, int precision, int threads, int ctas_per_sm, int max_cams,
                  size_t& smem, int& grid, std::string& why) {
-  const size_t want = batch_smem_bytes(precision, threads, max_cams);
-  const size_t one = batch_smem_bytes(precision, 32, max_cams);  // one row warp
+  const size_t want = batch_smem_want(precision, threads, max_cams);
+  const size_t one = batch_smem_bytes(precision, threads, max_cams);  // the minimum
   // the opt-in limit covers static and dynamic shared memory together
   const size_t optin = smem_per_block_optin(device);
   const size_t cap = optin > kStaticSmemReserve ? optin - kStaticSmemReserve : 0;

@@ -50,12 +50,14 @@ struct BProb {
   int32_t* oc_pt;    // [N] point of each camera-order observation
   int32_t* q_of;     // [N] point-order position of each camera-order observation
   int32_t* po_cam;   // [N] camera of each point-order observation
+  int32_t* po_k;     // [N] camera-order index of each point-order observation
   void* po_uv;       // [N][2] T, point order
+  void* oc_uv;       // [N][2] T, camera order
   // state (FP64 master, FP32 records on the FP32 path), current and trial
   double *R, *t, *Cc, *R2, *t2, *Cc2, *X, *X2;
   float *cam32, *cam32b, *X32, *X32b;
-  // linearisation (T) in point order for W
-  void* W;   // [N][W stride]
+  // linearisation (T)
+  void* W;   // [N][W stride], camera order
   void* U;   // [C][36]
   void* gc;  // [C][6]
   void* V;   // [P][6]
@@ -76,7 +78,7 @@ struct BProb {
   int64_t npairs;
   int nitems_cap;
   int32_t* pair_k1;   // [npairs] camera-order index of k1
-  int32_t* pair_q2;   // [npairs] point-order index of k2
+  int32_t* pair_k2;   // [npairs] camera-order index of k2
   int32_t* blk_ptr;   // [C*C + 1] first pair of block i1*C + i2
   int32_t* blk_item;  // [C*C + 1] first item of each block
   int32_t* item_beg;  // [nitems_cap] first pair of each item
@@ -131,8 +133,10 @@ void assign_prob(int precision, BProb& p, char* in, char* out, char* work);
 // packed host buffer can be copied with one transfer.
 void pack_inputs(int precision, const ba_problem& src, char* host_in);
 
-// Dynamic shared memory of the kernel for problems of at most max_cams cameras.
+// Dynamic shared memory the kernel needs for problems of at most max_cams
+// cameras, and what it can use (the Cholesky panel in shared memory).
 size_t batch_smem_bytes(int precision, int threads, int max_cams);
+size_t batch_smem_want(int precision, int threads, int max_cams);
 // Occupancy-checked launch of the multi-problem kernel.
 cudaError_t launch_batch(int precision, int threads, int grid, size_t smem, const BatchRun& a,
                          cudaStream_t s);

@@ -332,16 +332,21 @@ __device__ void setup_problem(BProb& p, Smem& sm, int* wsm) {
   __syncthreads();
   {
     T* uvo = (T*)p.po_uv;
+    T* uvc = (T*)p.oc_uv;
     const int q0 = tid * tile, q1 = min(N, q0 + tile);
     for (int q = q0; q < q1; ++q) {
       const int k = po_orig[q];
       const int c = p.raw_cam[k];
       const int r = tcnt[tid * C + c]++;
+      const T u = (T)p.raw_uv[2 * (int64_t)k], v = (T)p.raw_uv[2 * (int64_t)k + 1];
       p.oc_pt[r] = p.raw_pt[k];
       p.q_of[r] = q;
       p.po_cam[q] = c;
-      uvo[2 * (int64_t)q] = (T)p.raw_uv[2 * (int64_t)k];
-      uvo[2 * (int64_t)q + 1] = (T)p.raw_uv[2 * (int64_t)k + 1];
+      p.po_k[q] = r;
+      uvo[2 * (int64_t)q] = u;
+      uvo[2 * (int64_t)q + 1] = v;
+      uvc[2 * (int64_t)r] = u;
+      uvc[2 * (int64_t)r + 1] = v;
     }
   }
   // state
@@ -379,18 +384,17 @@ template <typename T>
 __device__ void cost_pass(const BProb& p, bool trial, T delta, int mode) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const PV<T> view(p, trial);
-  const T* uv = (const T*)p.po_uv;
+  const T* uv = (const T*)p.oc_uv;
   for (int i = warp; i < p.C; i += nw) {
     typename PV<T>::Cam cam;
     view.cam(i, cam);
     double acc = 0.0, nv = 0.0;
     for (int k = p.cam_ptr[i] + lane; k < p.cam_ptr[i + 1]; k += 32) {
       const int j = p.oc_pt[k];
-      const int64_t q = p.q_of[k];
       T xc[3];
       view.xc(cam, j, xc);
       T r0, r1;
-      if (!residual<T>(xc, uv[2 * q], uv[2 * q + 1], p.K, r0, r1)) continue;
+      if (!residual<T>(xc, uv[2 * (int64_t)k], uv[2 * (int64_t)k + 1], p.K, r0, r1)) continue;
       const T s = fma_rn(r0, r0, mul_rn(r1, r1));
       if (mode == 0) {
         acc += 0.5 * (double)huber_rho<T>(s, delta);
@@ -413,7 +417,7 @@ template <typename T>
 __device__ void lin_cams(const BProb& p, T delta) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const PV<T> view(p, false);
-  const T* uv = (const T*)p.po_uv;
+  const T* uv = (const T*)p.oc_uv;
   for (int i = warp; i < p.C; i += nw) {
     T acc[27];
 #pragma unroll
@@ -423,11 +427,10 @@ __device__ void lin_cams(const BProb& p, T delta) {
       view.cam(i, cam);
       for (int k = p.cam_ptr[i] + lane; k < p.cam_ptr[i + 1]; k += 32) {
         const int j = p.oc_pt[k];
-        const int64_t q = p.q_of[k];
         T xc[3];
         view.xc(cam, j, xc);
         T r0, r1;
-        if (!residual<T>(xc, uv[2 * q], uv[2 * q + 1], p.K, r0, r1)) continue;
+        if (!residual<T>(xc, uv[2 * (int64_t)k], uv[2 * (int64_t)k + 1], p.K, r0, r1)) continue;
         const T s = fma_rn(r0, r0, mul_rn(r1, r1));
         const T w = huber_weight<T>(s, delta);
         T Jc[2][6], Jp[2][3];
@@ -509,7 +512,7 @@ __device__ void lin_pts(const BProb& p, T delta) {
           }
         }
       }
-      st_w<T>(Wg, q, Wk);
+      st_w<T>(Wg, p.po_k[q], Wk);
     }
     T* Vo = (T*)p.V + 6 * j;
 #pragma unroll
@@ -569,7 +572,7 @@ __device__ void schur_y(const BProb& p) {
       for (int k = p.cam_ptr[i] + lane; k < p.cam_ptr[i + 1]; k += 32) {
         const int j = p.oc_pt[k];
         T Wk[18], Y[18];
-        ld_w<T>(W, p.q_of[k], Wk);
+        ld_w<T>(W, k, Wk);
         const double* vi = p.Vinv + 6 * j;
         const T v00 = (T)vi[0], v01 = (T)vi[1], v02 = (T)vi[2], v11 = (T)vi[3], v12 = (T)vi[4],
                 v22 = (T)vi[5];
@@ -625,7 +628,7 @@ __device__ void schur_items(const BProb& p) {
     for (int q = pb; q < pe; ++q) {
       T y[18], w[18];
       ld_w<T>(Yg, p.pair_k1[q], y);
-      ld_w<T>(W, p.pair_q2[q], w);
+      ld_w<T>(W, p.pair_k2[q], w);
 #pragma unroll
       for (int r = 0; r < 6; ++r)
 #pragma unroll
@@ -724,7 +727,7 @@ __device__ void build_pairs(BProb& p, int* wsm, Smem& sm) {
         if (has) {
           const int pos = cnt[c2] + rank;
           p.pair_k1[pos] = k1;
-          p.pair_q2[pos] = q1 + s;
+          p.pair_k2[pos] = p.po_k[q1 + s];
         }
         __syncwarp();
         if (has && rank == 0) cnt[c2] += __popc(peers);
@@ -751,12 +754,16 @@ __device__ void build_pairs(BProb& p, int* wsm, Smem& sm) {
 
 // Blocked right-looking Cholesky S = L L^T in place (lower triangle), panel
 // width kPanel: warp 0 factors the diagonal block in shared memory, every
-// thread then solves rows of the panel below it and updates 4 x 4 tiles of
-// the trailing lower triangle.  Returns false on a non-positive pivot.
+// thread then solves rows of the panel below it (kept in shared memory as
+// well when it fits) and updates 4 x 4 tiles of the trailing lower
+// triangle.  Returns false on a non-positive pivot.
 template <typename T>
-__device__ bool cholesky(T* A, int n, T* sd, Smem& sm) {
+__device__ bool cholesky(T* A, int n, T* dyn, size_t dyn_bytes, Smem& sm) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NT = blockDim.x;
   constexpr int LD = kPanel + 1;
+  T* sd = dyn;
+  T* Ps = dyn + kPanel * LD;  // panel rows below the diagonal block
+  const bool panel_smem = (size_t)(kPanel * LD + (size_t)n * LD) * sizeof(T) <= dyn_bytes;
   if (threadIdx.x == 0) sm.ok = 1;
   __syncthreads();
   for (int jb = 0; jb < n; jb += kPanel) {
@@ -789,8 +796,9 @@ __device__ bool cholesky(T* A, int n, T* sd, Smem& sm) {
     }
     __syncthreads();
     if (!sm.ok) return false;
+    const int m0 = jb + pb, rem = n - m0;
     // panel rows below the diagonal block: x L_d^T = a
-    for (int i = jb + pb + threadIdx.x; i < n; i += NT) {
+    for (int i = m0 + threadIdx.x; i < n; i += NT) {
       T* a = A + (int64_t)i * n + jb;
       T xr[kPanel];
 #pragma unroll
@@ -801,12 +809,15 @@ __device__ bool cholesky(T* A, int n, T* sd, Smem& sm) {
           xr[c] = s / sd[c * LD + c];
         }
       }
+      T* ps = Ps + (int64_t)(i - m0) * LD;
 #pragma unroll
       for (int c = 0; c < kPanel; ++c)
-        if (c < pb) a[c] = xr[c];
+        if (c < pb) {
+          a[c] = xr[c];
+          if (panel_smem) ps[c] = xr[c];
+        }
     }
     __syncthreads();
-    const int m0 = jb + pb, rem = n - m0;
     if (rem > 0) {
       const int nt = (rem + 3) / 4;
       const int ntiles = nt * (nt + 1) / 2;
@@ -815,31 +826,53 @@ __device__ bool cholesky(T* A, int n, T* sd, Smem& sm) {
         while ((ti + 1) * (ti + 2) / 2 <= tt) ++ti;
         while (ti * (ti + 1) / 2 > tt) --ti;
         const int tk = tt - ti * (ti + 1) / 2;
-        const int i0 = m0 + 4 * ti, k0 = m0 + 4 * tk;
         T acc[4][4];
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
           for (int c = 0; c < 4; ++c) acc[r][c] = T(0);
-        const T* Ai[4];
-        const T* Ak[4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          Ai[r] = A + (int64_t)min(i0 + r, n - 1) * n + jb;
-          Ak[r] = A + (int64_t)min(k0 + r, n - 1) * n + jb;
-        }
-        for (int m = 0; m < pb; ++m) {
-          T a[4], b[4];
+        if (panel_smem) {
+          const T* Ai[4];
+          const T* Ak[4];
 #pragma unroll
           for (int r = 0; r < 4; ++r) {
-            a[r] = Ai[r][m];
-            b[r] = Ak[r][m];
+            Ai[r] = Ps + (int64_t)min(4 * ti + r, rem - 1) * LD;
+            Ak[r] = Ps + (int64_t)min(4 * tk + r, rem - 1) * LD;
           }
+          for (int m = 0; m < pb; ++m) {
+            T a[4], b[4];
 #pragma unroll
-          for (int r = 0; r < 4; ++r)
+            for (int r = 0; r < 4; ++r) {
+              a[r] = Ai[r][m];
+              b[r] = Ak[r][m];
+            }
 #pragma unroll
-            for (int c = 0; c < 4; ++c) acc[r][c] += a[r] * b[c];
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+              for (int c = 0; c < 4; ++c) acc[r][c] += a[r] * b[c];
+          }
+        } else {
+          const T* Ai[4];
+          const T* Ak[4];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            Ai[r] = A + (int64_t)min(m0 + 4 * ti + r, n - 1) * n + jb;
+            Ak[r] = A + (int64_t)min(m0 + 4 * tk + r, n - 1) * n + jb;
+          }
+          for (int m = 0; m < pb; ++m) {
+            T a[4], b[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+              a[r] = Ai[r][m];
+              b[r] = Ak[r][m];
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+              for (int c = 0; c < 4; ++c) acc[r][c] += a[r] * b[c];
+          }
         }
+        const int i0 = m0 + 4 * ti, k0 = m0 + 4 * tk;
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -854,19 +887,27 @@ __device__ bool cholesky(T* A, int n, T* sd, Smem& sm) {
   return true;
 }
 
-// x <- L^-T L^-1 x with blocks of 32: warp 0 solves each diagonal block with
-// shuffles, all threads apply it to the remaining rows.
+// x <- L^-T L^-1 x with blocks of 32: warp 0 holds each diagonal block in
+// registers (lane r: row r for the forward sweep, column r for the backward
+// one) and solves it with shuffles; all threads apply it to the other rows.
 template <typename T>
 __device__ void chol_solve(const T* A, int n, T* x) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NT = blockDim.x;
   for (int jb = 0; jb < n; jb += 32) {
     const int pb = min(32, n - jb);
     if (warp == 0) {
+      T L[32];
+      const T* row = A + (int64_t)(jb + min(lane, pb - 1)) * n + jb;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) L[j] = j < pb ? row[j] : T(1);
       T yr = lane < pb ? x[jb + lane] : T(0);
-      for (int j = 0; j < pb; ++j) {
-        if (lane == j) yr = yr / A[(int64_t)(jb + j) * n + jb + j];
-        const T yj = __shfl_sync(0xffffffffu, yr, j);
-        if (lane > j && lane < pb) yr -= A[(int64_t)(jb + lane) * n + jb + j] * yj;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        if (j < pb) {
+          if (lane == j) yr = yr / L[j];
+          const T yj = __shfl_sync(0xffffffffu, yr, j);
+          if (lane > j && lane < pb) yr -= L[j] * yj;
+        }
       }
       if (lane < pb) x[jb + lane] = yr;
     }
@@ -882,11 +923,18 @@ __device__ void chol_solve(const T* A, int n, T* x) {
   for (int jb = ((n - 1) / 32) * 32; jb >= 0; jb -= 32) {
     const int pb = min(32, n - jb);
     if (warp == 0) {
+      T L[32];  // L[j] = A[jb + j][jb + lane]
+      const int cl = min(lane, pb - 1);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) L[j] = j < pb ? A[(int64_t)(jb + j) * n + jb + cl] : T(1);
       T xr = lane < pb ? x[jb + lane] : T(0);
-      for (int j = pb - 1; j >= 0; --j) {
-        if (lane == j) xr = xr / A[(int64_t)(jb + j) * n + jb + j];
-        const T xj = __shfl_sync(0xffffffffu, xr, j);
-        if (lane < j) xr -= A[(int64_t)(jb + j) * n + jb + lane] * xj;
+#pragma unroll
+      for (int j = 31; j >= 0; --j) {
+        if (j < pb) {
+          if (lane == j) xr = xr / L[j];
+          const T xj = __shfl_sync(0xffffffffu, xr, j);
+          if (lane < j) xr -= L[j] * xj;
+        }
       }
       if (lane < pb) x[jb + lane] = xr;
     }
@@ -913,7 +961,7 @@ __device__ void backsub_pts(const BProb& p, double mu) {
       const int c = p.po_cam[q];
       if (p.fixed[c]) continue;
       T Wk[18];
-      ld_w<T>(Wg, q, Wk);
+      ld_w<T>(Wg, p.po_k[q], Wk);
       const T* xv = dc + 6 * c;
 #pragma unroll
       for (int a = 0; a < 6; ++a) {
@@ -1021,7 +1069,8 @@ __device__ void lm_begin(BProb& p, const BatchRun& a, Smem& sm) {
 }
 
 template <typename T>
-__device__ void lm_iteration(BProb& p, const BatchRun& a, Smem& sm, T* dyn, PhaseClock& pc) {
+__device__ void lm_iteration(BProb& p, const BatchRun& a, Smem& sm, T* dyn, size_t dyn_bytes,
+                             PhaseClock& pc) {
   const T delta = (T)a.huber_delta;
   const double mu = fmax(p.mu, a.mu_min);  // damping of the linear system
   if (p.need_lin) {
@@ -1041,7 +1090,7 @@ __device__ void lm_iteration(BProb& p, const BatchRun& a, Smem& sm, T* dyn, Phas
   __syncthreads();
   pc.mark(kPhSchur);
   const int n = 6 * p.C;
-  const bool ok = cholesky<T>((T*)p.S, n, dyn, sm);
+  const bool ok = cholesky<T>((T*)p.S, n, dyn, dyn_bytes, sm);
   pc.mark(kPhCholesky);
   double Fn = 0.0, hp = 0.0, hc = 0.0;
   if (ok) {
@@ -1121,7 +1170,7 @@ __device__ void note_done(const BatchRun& a, int id) {
 }
 
 template <typename T, int NT>
-__global__ void __launch_bounds__(NT) k_batch(BatchRun a, int dyn_bytes) {
+__global__ void __launch_bounds__(NT, (NT >= 512 ? 1 : (NT >= 256 ? 2 : 3))) k_batch(BatchRun a, int dyn_bytes) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ Smem sm;
   T* dyn = reinterpret_cast<T*>(smem_raw);
@@ -1159,7 +1208,7 @@ __global__ void __launch_bounds__(NT) k_batch(BatchRun a, int dyn_bytes) {
       note_done(a, id);
       continue;
     }
-    for (int it = 0; it < todo; ++it) lm_iteration<T>(p, a, sm, dyn, pc);
+    for (int it = 0; it < todo; ++it) lm_iteration<T>(p, a, sm, dyn, (size_t)dyn_bytes, pc);
     if (p.iter >= p.iters) {
       lm_end<T>(p, a, sm);
       pc.mark(kPhCost);
@@ -1193,6 +1242,13 @@ int occupancy_t(size_t smem) {
 size_t batch_smem_bytes(int precision, int threads, int max_cams) {
   return precision == BA_FP32 ? batch_dyn_bytes<float>(threads, max_cams)
                               : batch_dyn_bytes<double>(threads, max_cams);
+}
+
+size_t batch_smem_want(int precision, int threads, int max_cams) {
+  const size_t t = precision == BA_FP32 ? 4 : 8;
+  const size_t panel = ((size_t)kPanel * (kPanel + 1) + (size_t)6 * max_cams * (kPanel + 1)) * t;
+  const size_t need = batch_smem_bytes(precision, threads, max_cams);
+  return panel > need ? panel : need;
 }
 
 cudaError_t launch_batch(int precision, int threads, int grid, size_t smem, const BatchRun& a,
