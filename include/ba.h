@@ -91,9 +91,15 @@ typedef struct {
   int serve_queue;          /* maximum requests waiting for admission        */
   int profile;              /* record per-kernel device times (CUDA events
                                between the kernels of the captured loop)      */
-  int pcg_variant;          /* 0 or 1: standard PCG (two grid barriers per
-                               iteration); 2: pipelined PCG (one barrier per
-                               iteration; in FP32 it converges less well)    */
+  int pcg_variant;          /* PCG kernel.  0: auto (1); 1: standard PCG on
+                               a cooperative grid
+                               (two grid barriers per iteration); 2:
+                               pipelined PCG (one grid barrier per iteration;
+                               in FP32 it converges less well); 3: standard
+                               PCG in one thread-block cluster (hardware
+                               cluster barriers, exchanges through
+                               distributed shared memory; falls back to 1
+                               when S does not fit, or with refinement)      */
   double mu_min;            /* floor of the damping used in the linear system;
                                < 0: auto (1e-4 for BA_FP32, where rounding in
                                the FP32 Schur complement otherwise exceeds its

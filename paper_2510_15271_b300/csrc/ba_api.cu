@@ -142,8 +142,8 @@ static ba_status check_options(const ba_options* o, std::string& err) {
     err = "precision must be BA_FP64 or BA_FP32";
     return BA_ERR_INVALID_ARG;
   }
-  if (o->pcg_variant < 0 || o->pcg_variant > 2) {
-    err = "pcg_variant must be 0 (auto), 1 (standard) or 2 (pipelined)";
+  if (o->pcg_variant < 0 || o->pcg_variant > 3) {
+    err = "pcg_variant must be 0 (auto), 1 (standard), 2 (pipelined) or 3 (cluster)";
     return BA_ERR_INVALID_ARG;
   }
   if (o->solver < BA_SOLVER_AUTO || o->solver > BA_SOLVER_PCG) {
@@ -640,6 +640,28 @@ ba_status ba_set_problem(ba_handle* h, int32_t n_cams, int32_t n_pts, int64_t n_
     CK(cudaMemcpy(d.pcg_uptr, plan.uptr.data(), plan.uptr.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d.pcg_lcol, plan.lcol.data(), plan.lcol.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d.pcg_lown, plan.lown.data(), plan.lown.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    // one thread-block cluster instead of the grid kernel, when asked for
+    // (measured no faster than the grid kernel on this part: about 13 us per
+    // iteration either way, so auto keeps the grid kernel)
+    const int var = h->opts.pcg_variant;
+    PccPlan pc;
+    if (var == 3 && !cfg.refine &&
+        plan_pcg_cluster(prec, h->device, hrp, hcol, cfg, pc)) {
+      auto up = [&](int32_t*& dst, const std::vector<int32_t>& v) {
+        if (!keep(h, dst, std::max<size_t>(v.size(), 1) * sizeof(int32_t))) return false;
+        return v.empty() ||
+               cudaMemcpy(dst, v.data(), v.size() * sizeof(int32_t), cudaMemcpyHostToDevice) ==
+                   cudaSuccess;
+      };
+      if (!(up(d.pcc_rows, pc.rows) && up(d.pcc_nres, pc.nres) && up(d.pcc_uptr, pc.uptr) &&
+            up(d.pcc_src, pc.src) && up(d.pcc_lcol, pc.lcol) && up(d.pcc_lown, pc.lown))) {
+        h->err = "ba_set_problem: out of device memory (cluster PCG plan)";
+        free_problem(h);
+        return BA_ERR_OOM;
+      }
+    } else {
+      cfg.pcc_cs = 0;
+    }
   }
   cfg.schur_colcap = schur_colcap(prec, d.max_row_nnz, d.max_chunk_subs, smax - 2048);
   set_schur_smem_attr(prec, schur_smem(prec, cfg.schur_colcap, d.max_chunk_subs));

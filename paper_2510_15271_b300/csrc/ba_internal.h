@@ -118,6 +118,13 @@ struct DevProblem {
   int32_t* pcg_uptr = nullptr;  // [G + 1]
   int32_t* pcg_lcol = nullptr;  // [nnzb] list index of each block's column
   int32_t* pcg_lown = nullptr;  // [C] list index of each row's own column
+  // cluster PCG plan
+  int32_t* pcc_rows = nullptr;  // [cs + 1] first block row of each CTA
+  int32_t* pcc_nres = nullptr;  // [cs] blocks of S each CTA keeps in shared memory
+  int32_t* pcc_uptr = nullptr;  // [cs + 1] first listed column of each CTA
+  int32_t* pcc_src = nullptr;   // [listed] owner rank << 20 | row within the owner
+  int32_t* pcc_lcol = nullptr;  // [nnzb] list index of each block's column
+  int32_t* pcc_lown = nullptr;  // [C] list index of each row's own column
   // linearisation (T)
   void* W = nullptr;    // [N][W_STRIDE]
   void* U = nullptr;    // [C][36]

@@ -48,6 +48,10 @@ struct SolveConfig {
   int pcg_maxnnz = 0;      // most blocks of S held by one CTA
   int pcg_maxu = 0;        // most distinct columns referenced by one CTA
   size_t pcg_smem = 0;     // dynamic shared memory (0: rows of S read from global)
+  int pcc_cs = 0;          // cluster PCG: CTAs in the cluster (0: grid kernel)
+  int pcc_rw = 1;          // cluster PCG: rows per warp (kernel variant)
+  size_t pcc_smem = 0;     // cluster PCG: dynamic shared memory per CTA
+  int pcc_rmax = 0, pcc_umax = 0, pcc_nnzmax = 0;  // cluster PCG: layout sizes
   size_t dense_smem = 0;   // dynamic shared memory of the dense solver (0: global workspace)
   Marks* marks = nullptr;
 };
@@ -75,6 +79,15 @@ struct PcgPlan {
   std::vector<int32_t> lcol;  // [nnzb] list index of each block's column
   std::vector<int32_t> lown;  // [C] list index of each row's own column
 };
+// Plan of the cluster PCG kernel (pcg_cluster.cu): row split over the
+// cluster's CTAs, resident blocks, column lists and their owners.
+struct PccPlan {
+  std::vector<int32_t> rows, nres, uptr, src, lcol, lown;
+};
+bool plan_pcg_cluster(int precision, int device, const std::vector<int32_t>& rowptr,
+                      const std::vector<int32_t>& col, SolveConfig& cfg, PccPlan& plan);
+void launch_pcg_cluster(const DevProblem& d, const SolveConfig& cfg, cudaStream_t s);
+
 bool plan_pcg(int precision, int device, const std::vector<int32_t>& rowptr,
               const std::vector<int32_t>& col, size_t smem_limit, SolveConfig& cfg,
               PcgPlan& plan);

@@ -206,13 +206,25 @@ __device__ __forceinline__ T pick6(const T v[6], int lane) {
   return r;
 }
 
-// Sum of per-warp FP64 values over the CTA into slot[blockIdx.x * stride + k].
+// Sum over the CTA of FP64 values held by lanes 0..5 of each warp (every
+// caller accumulates its dot products in the lanes that own the 6 elements
+// of a block row; the other lanes hold zeros) into slot[blockIdx.x * stride
+// + k].  Lane 0 adds its warp's six values: FP64 is slow on this part, so
+// no 32-lane butterfly.
 template <int NT, int NV>
 __device__ __forceinline__ void cta_partials(double (&v)[NV], double* red, double* slot,
                                              int stride) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+  for (int k = 0; k < NV; ++k) {
+    double s = v[k];
+#pragma unroll
+    for (int l = 1; l < 6; ++l) {
+      const double o = __shfl_sync(0xffffffffu, v[k], l);
+      if (lane == 0) s += o;
+    }
+    v[k] = s;
+  }
   if (lane == 0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) red[warp * NV + k] = v[k];
@@ -293,15 +305,24 @@ __device__ int pcg_solve(const DevProblem& d, const RowSet<T>& rs, const T* __re
   grid_barrier(d.barrier, nb, err);
   double tot[2];
   all_partials<2>(partB, 2, nb, tot);
+  // scalars of the recurrence: computed by thread 0 (FP64 is slow on this
+  // part, so it is not repeated in every thread) and broadcast; decisions
+  // are uniform in the CTA, and equal in all CTAs (same sums, same order)
+  __shared__ T s_al, s_bt;
+  __shared__ int s_go, s_stop;
   double rz = tot[0], rr = tot[1];
   const double bnorm = sqrt(rr);
-  double beta = 0.0;
   int k = 0;
-  while (k < max_iters && sqrt(rr) > tol * bnorm && !ld_err(err)) {
+  if (threadIdx.x == 0) {
+    s_bt = T(0);
+    s_go = (max_iters > 0 && sqrt(rr) > tol * bnorm && !ld_err(err)) ? 1 : 0;
+  }
+  __syncthreads();
+  while (s_go) {
     const int cur = k & 1;
     T* pn = pb[cur];
     const T* po = pb[cur ^ 1];
-    const T bt = (T)beta;
+    const T bt = s_bt;
     // phase A: p_k = z + beta p_{k-1}; q = S p_k; partial p.q
     if (STAGED) stage<T, NT>(rs, z, po, bt);
     double pq_loc[1] = {0.0};
@@ -329,10 +350,14 @@ __device__ int pcg_solve(const DevProblem& d, const RowSet<T>& rs, const T* __re
     grid_barrier(d.barrier, nb, err);
     double pqt[1];
     all_partials<1>(partA, 1, nb, pqt);
-    const double pq = pqt[0];
-    if (!(pq > 0.0)) break;  // S not numerically positive definite along p
-    const double alpha = rz / pq;
-    const T al = (T)alpha;
+    if (threadIdx.x == 0) {
+      const double pq = pqt[0];
+      s_stop = (pq > 0.0) ? 0 : 1;  // S not numerically positive definite along p
+      s_al = (T)(rz / pq);
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const T al = s_al;
     // phase B: x += alpha p; r -= alpha q; z = M r; partial r.z, r.r
     double l2[2] = {0.0, 0.0};
 #pragma unroll
@@ -356,10 +381,15 @@ __device__ int pcg_solve(const DevProblem& d, const RowSet<T>& rs, const T* __re
     grid_barrier(d.barrier, nb, err);
     all_partials<2>(partB, 2, nb, tot);
     ++k;
-    beta = tot[0] / rz;
-    rz = tot[0];
-    rr = tot[1];
+    if (threadIdx.x == 0) {
+      s_bt = (T)(tot[0] / rz);
+      rz = tot[0];
+      rr = tot[1];
+      s_go = (k < max_iters && sqrt(rr) > tol * bnorm && !ld_err(err)) ? 1 : 0;
+    }
+    __syncthreads();
   }
+  // rr (and so *rel) is current in thread 0 only
 #pragma unroll
   for (int m = 0; m < RW; ++m) {
     const int i = rs.r0 + warp + m * NW;
@@ -844,6 +874,10 @@ template <typename T>
 static void linear_solve_t(const DevProblem& d, const SolveConfig& cfg, cudaStream_t s) {
   if (cfg.solver == BA_SOLVER_DENSE) {
     k_dense<T, kDenseThreads><<<1, kDenseThreads, cfg.dense_smem, s>>>(d, cfg.dense_smem > 0);
+    return;
+  }
+  if (cfg.pcc_cs > 0) {
+    launch_pcg_cluster(d, cfg, s);
     return;
   }
   cudaMemsetAsync(d.barrier, 0, sizeof(unsigned), s);  // arrival counter only

@@ -1,9 +1,12 @@
-"""Full-size checks of the driving workload (1,000 cameras, 200k points,
-~1.21M observations) in the configuration the benchmark times.
+"""Full-size checks of the sparse workloads in the configuration the
+benchmark times: driving (1,000 cameras, 200k points, ~1.21M observations,
+FP32) and city (5,000 cameras, 1M points, ~7.9M observations, FP32 with FP64
+refinement of the PCG residual).
 
-Expected values come from tests/golden/driving_seed2_oracle.json, written by
-tests/golden/make_golden.py with the FP64 CPU oracle only.
+Expected values come from tests/golden/<workload>_seed<seed>_oracle.json,
+written by tests/golden/make_golden.py with the FP64 CPU oracle only.
 """
+import glob
 import json
 import os
 
@@ -16,12 +19,12 @@ from paper_2510_15271_b300 import ba, scenes
 pytestmark = pytest.mark.gpu
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-GOLDEN = os.path.join(HERE, "golden", "driving_seed2_oracle.json")
+GOLDENS = sorted(glob.glob(os.path.join(HERE, "golden", "*_oracle.json")))
 
 
-@pytest.fixture(scope="module")
-def golden():
-    with open(GOLDEN) as f:
+@pytest.fixture(scope="module", params=GOLDENS, ids=lambda p: os.path.basename(p).split("_")[0])
+def golden(request):
+    with open(request.param) as f:
         return json.load(f)
 
 

@@ -83,13 +83,16 @@ def _driving_small(seed=3, **kw):
     return scenes.make_scene("driving", seed=seed, **base)
 
 
-def test_driving_fp64_pcg_matches_oracle_pcg():
+@pytest.mark.parametrize("variant", [1, 3])
+def test_driving_fp64_pcg_matches_oracle_pcg(variant):
     """Production PCG settings (tol 1e-6, max 100) on both sides.  Two CG
     runs that round differently agree only to about the solve tolerance, so
     the per-iteration costs are compared at PCG_COST_RTOL; the 1e-9 gate is
-    held by the exact-enough solves below."""
+    held by the exact-enough solves below.  Variant 1 is the grid kernel,
+    3 the one-cluster kernel."""
     s = _driving_small()
-    rep, q, p = ba.solve_scene(s, "fp64", max_lm_iters=8, solver=ba.BA_SOLVER_PCG)
+    rep, q, p = ba.solve_scene(s, "fp64", max_lm_iters=8, solver=ba.BA_SOLVER_PCG,
+                               pcg_variant=variant)
     _, ref = _oracle(s, 8, "pcg")
     rel = np.abs(rep["costs"] - ref.costs) / ref.costs
     assert rel.max() <= PCG_COST_RTOL, (rel, rep["costs"], ref.costs)
@@ -97,12 +100,13 @@ def test_driving_fp64_pcg_matches_oracle_pcg():
     print("per-iteration cost rel diff (production PCG):", rel)
 
 
-def test_driving_fp64_tight_pcg_matches_oracle_cholesky():
+@pytest.mark.parametrize("variant", [1, 3])
+def test_driving_fp64_tight_pcg_matches_oracle_cholesky(variant):
     """An exact-enough PCG solve reproduces the direct-solve LM path."""
     s = _driving_small(seed=4)
     n = 6 * s.n_cams
     rep, q, p = ba.solve_scene(s, "fp64", max_lm_iters=6, solver=ba.BA_SOLVER_PCG,
-                               pcg_tol=1e-13, pcg_max_iters=4 * n)
+                               pcg_tol=1e-13, pcg_max_iters=4 * n, pcg_variant=variant)
     _, ref = _oracle(s, 6, "dense")
     rel = np.abs(rep["costs"] - ref.costs) / ref.costs
     assert rel.max() <= COST_RTOL, (rel, rep["costs"], ref.costs)
@@ -126,6 +130,35 @@ def test_pipelined_pcg_matches_oracle_pcg():
     _, ref = _oracle(s, 6, "dense")
     rel = np.abs(rep["costs"] - ref.costs) / ref.costs
     assert rel.max() <= COST_RTOL, (rel, rep["costs"], ref.costs)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_cluster_pcg_with_streamed_blocks(prec):
+    """Large enough that each CTA of the cluster keeps only part of its rows
+    of S in shared memory and reads the rest from global memory every
+    product: same iterates as the grid kernel up to rounding."""
+    s = _driving_small(seed=6, n_cams=500, n_pts=100000, length_m=1000.0)
+    rg, _, _ = ba.solve_scene(s, prec, max_lm_iters=3, solver=ba.BA_SOLVER_PCG, pcg_variant=1)
+    rc, _, _ = ba.solve_scene(s, prec, max_lm_iters=3, solver=ba.BA_SOLVER_PCG, pcg_variant=3)
+    tol = 1e-6 if prec == "fp64" else 1e-4
+    np.testing.assert_allclose(rc["costs"], rg["costs"], rtol=tol)
+    assert np.abs(rc["pcg_iters"] - rg["pcg_iters"]).max() <= 3
+    if prec == "fp64":
+        # exact-enough cluster solves reproduce the oracle's direct-solve path
+        n = 6 * s.n_cams
+        rt, _, _ = ba.solve_scene(s, prec, max_lm_iters=3, solver=ba.BA_SOLVER_PCG,
+                                  pcg_variant=3, pcg_tol=1e-12, pcg_max_iters=4 * n)
+        _, ref = _oracle(s, 3, "dense")
+        rel = np.abs(rt["costs"] - ref.costs) / ref.costs
+        assert rel.max() <= COST_RTOL, (rel, rt["costs"], ref.costs)
+
+
+def test_cluster_pcg_falls_back_on_tiny_problems():
+    s = _driving_small(seed=7, n_cams=7, n_pts=700, length_m=14.0)
+    rep, _, _ = ba.solve_scene(s, "fp64", max_lm_iters=3, solver=ba.BA_SOLVER_PCG, pcg_variant=3)
+    _, ref = _oracle(s, 3, "pcg")
+    rel = np.abs(rep["costs"] - ref.costs) / ref.costs
+    assert rel.max() <= PCG_COST_RTOL
 
 
 def test_fp64_dense_and_pcg_agree_on_the_gpu():
