@@ -97,6 +97,30 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+# --------------------------------------------------------------------------- replicas
+
+def replica_seed(seed, rank):
+    """Each rank solves its own independent problem of the same recipe."""
+    return seed + rank
+
+
+def max_over_ranks(ms, world, device):
+    """The slowest rank's time (ms) on every rank (an all-reduce MAX over the
+    process group: NCCL on GPUs, gloo on CPU)."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(work_per_step, steps, world, ms_max):
+    """obs*iters/s of the whole job: every rank's work over the slowest rank's
+    time (weak scaling: each rank has a full problem)."""
+    return work_per_step * steps * world / (ms_max / 1e3)
+
+
 # --------------------------------------------------------------------------- workload
 
 def make_workload(name, seed):
@@ -154,7 +178,7 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    s = make_workload(args.workload, args.seed + rank)
+    s = make_workload(args.workload, replica_seed(args.seed, rank))
     iters = s.lm_iters
     work = s.n_obs * iters  # obs*iters per step
 
@@ -197,11 +221,8 @@ def run_ours(args, rank, world, local_rank):
             reps.append(ba.ba_solve(h))
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
+        ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
         if world > 1:
-            t = torch.tensor([ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
             torch.distributed.barrier()
         return ms, reps
 
@@ -368,10 +389,16 @@ def run_batched(args, local_rank):
     work = n_obs * iters
     arrs = [ba._ProblemArrays.from_scene(w, want_state=True) for w in ws]
 
+    fixed = tuple(int(v) for v in args.batch_schedule.split(",")) if args.batch_schedule else None
+
     def timed(precision, steps, tune):
         o = ba.options_for_scene(ws[0], precision, device=local_rank)
         with ba.ba_create(o) as h:
-            sched = ba.ba_tune_batch(h, arrs) if tune else ba.ba_get_batch_schedule(h)
+            if fixed:
+                ba.ba_set_batch_schedule(h, *fixed)
+                sched = fixed
+            else:
+                sched = ba.ba_tune_batch(h, arrs) if tune else ba.ba_get_batch_schedule(h)
             for _ in range(max(1, args.warmup)):
                 ba.ba_solve_batch(h, arrs)
             call, kern, h2d, d2h = [], [], [], []
@@ -560,6 +587,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--windows", type=int, default=512)
+    ap.add_argument("--batch-schedule", default="",
+                    help="threads,ctas_per_sm for the batched solver instead of the autotuner")
     ap.add_argument("--plain-sample", type=int, default=16)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-seconds", type=float, default=5.0)
@@ -597,7 +626,7 @@ def main():
         return
     peak, peak_kind = _peaks()
     s = res["s"]
-    value = res["work"] * args.steps * world / (res["ms32"] / 1e3)
+    value = whole_job_value(res["work"], args.steps, world, res["ms32"])
     line = {
         "impl": "ours", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms32"] / args.steps,
@@ -617,6 +646,8 @@ def main():
         line["batched"] = run_batched(args, 0)
     if not args.no_served:
         line["served"] = run_served(args, 0)
+        line["local_ba_p50_ms"] = line["served"]["p50_ms"]
+        line["local_ba_p99_ms"] = line["served"]["p99_ms"]
     if not args.no_cpu:
         v, dt = cpu_baseline(s, args.cpu_iters)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": len(os.sched_getaffinity(0)),

@@ -1,0 +1,54 @@
+"""Host logic of bench.py's multi-GPU leg (independent replicas, no data-path
+collective): the max-over-ranks timing and the whole-job rate, run as two
+gloo ranks on the CPU."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+import bench
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ms = 10.0 + 5.0 * rank          # rank 1 is the slow one
+        m = bench.max_over_ranks(ms, world, "cpu")
+        v = bench.whole_job_value(1000, 4, world, m)
+        out.put((rank, m, v, bench.replica_seed(7, rank)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_replicas_take_the_slowest_rank_and_sum_the_work():
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, m, v, seed in res:
+        assert m == 15.0
+        assert v == pytest.approx(1000 * 4 * 2 / 0.015)
+        assert seed == 7 + rank
+    assert res[0][3] != res[1][3]
+
+
+def test_single_rank_needs_no_process_group():
+    assert bench.max_over_ranks(12.5, 1, "cpu") == 12.5
+    assert bench.whole_job_value(100, 2, 1, 50.0) == pytest.approx(4000.0)
