@@ -126,6 +126,8 @@ void carve_work(Carve& c, BProb& p, int precision, int C, int P, int64_t N, int6
   p.blk_ptr = c.take<int32_t>((size_t)C * C + 1);
   p.blk_item = c.take<int32_t>((size_t)C * C + 1);
   p.item_beg = c.take<int32_t>((size_t)p.nitems_cap);
+  p.item_blk = c.take<int32_t>((size_t)p.nitems_cap);
+  p.VinvT = c.take_bytes((size_t)P * 6 * t);
   p.Y = c.take_bytes((size_t)N * ws * t);
   p.part = c.take_bytes((size_t)p.nitems_cap * 36 * t);
 }
@@ -331,10 +333,10 @@ int batch_stats(ba_handle* h, ba_kernel_stat* out, int max) {
   }
   if (b->d_phase) {
     // CTA-milliseconds per phase of the multi-problem kernel
-    static const char* ph[kPhaseCount] = {"ph_idle",   "ph_setup",    "ph_lin",
-                                          "ph_damp",   "ph_schur",    "ph_cholesky",
-                                          "ph_solve",  "ph_trial",    "ph_cost",
-                                          "ph_gain"};
+    static const char* ph[kPhaseCount] = {"ph_idle",         "ph_setup",   "ph_lin",
+                                          "ph_damp",         "ph_schur_y", "ph_schur_items",
+                                          "ph_schur_blocks", "ph_cholesky", "ph_solve",
+                                          "ph_trial",        "ph_cost",    "ph_gain"};
     for (int i = 0; i < kPhaseCount && w < max; ++i, ++w) {
       memset(&out[w], 0, sizeof(out[w]));
       strncpy(out[w].name, ph[i], sizeof(out[w].name) - 1);
@@ -482,10 +484,24 @@ ba_status prepare(ba_handle* h, ba_batch* b, int32_t n, const ba_problem* pr) {
   b->out_off.assign(n, 0);
   std::vector<size_t> work_off(n);
   std::vector<int64_t> npairs(n);
+  {
+    // pair counts need a pass over every problem's observations: host threads
+    int nth = (int)std::min<unsigned>(8, std::max(1u, std::thread::hardware_concurrency()));
+    if (n < 16) nth = 1;
+    auto job = [&](int t) {
+      for (int i = t; i < n; i += nth) npairs[i] = count_pairs(pr[i]);
+    };
+    if (nth == 1) {
+      job(0);
+    } else {
+      std::vector<std::thread> th;
+      for (int t = 0; t < nth; ++t) th.emplace_back(job, t);
+      for (auto& x : th) x.join();
+    }
+  }
   size_t in = 0, out = 0, work = 0;
   int max_cams = 1;
   for (int i = 0; i < n; ++i) {
-    npairs[i] = count_pairs(pr[i]);
     if (npairs[i] > (int64_t)INT32_MAX - 64) {
       h->err = "ba_solve_batch: problem " + std::to_string(i) + " has too many point pairs";
       return BA_ERR_INVALID_ARG;

@@ -64,6 +64,7 @@ struct BProb {
   void* gp;  // [P][3]
   void* e;   // [P][3]
   double* Vinv;  // [P][6]
+  void* VinvT;    // [P][6] T copy of Vinv (applied per observation)
   // reduced system (T): dense S [n][n], b, x (n = 6C)
   void* S;
   void* b;
@@ -82,6 +83,7 @@ struct BProb {
   int32_t* blk_ptr;   // [C*C + 1] first pair of block i1*C + i2
   int32_t* blk_item;  // [C*C + 1] first item of each block
   int32_t* item_beg;  // [nitems_cap] first pair of each item
+  int32_t* item_blk;  // [nitems_cap] output block of each item
   void* Y;            // [N][W stride] Y_k = W_k V*_j^-1, camera order
   void* part;         // [nitems_cap][36] item sums
   double cost[BA_MAX_ITERS + 1];
@@ -108,7 +110,9 @@ enum : int {
   kPhSetup,      // validation, sorts, state
   kPhLin,        // U, g_c, V, g_p, W
   kPhDamp,       // V*^-1, e
-  kPhSchur,      // S, b
+  kPhSchurY,     // Y = W V*^-1, b
+  kPhSchurItems, // pair sums of the items
+  kPhSchurBlocks,// S from the item sums
   kPhCholesky,   // S = L L^T
   kPhSolve,      // triangular solves
   kPhTrial,      // back-substitution, retraction, model decrease

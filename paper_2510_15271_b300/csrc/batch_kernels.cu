@@ -537,8 +537,12 @@ __device__ void damp_pts(const BProb& p, double mu) {
     double inv[6];
     sym3_inverse(m, inv);
     double* out = p.Vinv + 6 * j;
+    T* outT = (T*)p.VinvT + 6 * j;
 #pragma unroll
-    for (int a = 0; a < 6; ++a) out[a] = inv[a];
+    for (int a = 0; a < 6; ++a) {
+      out[a] = inv[a];
+      outT[a] = (T)inv[a];
+    }
     const T* g = (const T*)p.gp + 3 * j;
     const double g0 = g[0], g1 = g[1], g2 = g[2];
     T* e = (T*)p.e + 3 * j;
@@ -567,15 +571,15 @@ __device__ void schur_y(const BProb& p) {
   T* Yg = (T*)p.Y;
   for (int i = warp; i < p.C; i += nw) {
     const bool fixed = p.fixed[i] != 0;
-    double bl[6] = {0, 0, 0, 0, 0, 0};
+    // b accumulates in T (FP32 on the FP32 path: no FP64 per observation)
+    T bl[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
     if (!fixed) {
       for (int k = p.cam_ptr[i] + lane; k < p.cam_ptr[i + 1]; k += 32) {
         const int j = p.oc_pt[k];
         T Wk[18], Y[18];
         ld_w<T>(W, k, Wk);
-        const double* vi = p.Vinv + 6 * j;
-        const T v00 = (T)vi[0], v01 = (T)vi[1], v02 = (T)vi[2], v11 = (T)vi[3], v12 = (T)vi[4],
-                v22 = (T)vi[5];
+        const T* vi = (const T*)p.VinvT + 6 * j;
+        const T v00 = vi[0], v01 = vi[1], v02 = vi[2], v11 = vi[3], v12 = vi[4], v22 = vi[5];
         const T e0 = eg[3 * j], e1 = eg[3 * j + 1], e2 = eg[3 * j + 2];
 #pragma unroll
         for (int a = 0; a < 6; ++a) {
@@ -583,7 +587,7 @@ __device__ void schur_y(const BProb& p) {
           Y[3 * a] = w0 * v00 + w1 * v01 + w2 * v02;
           Y[3 * a + 1] = w0 * v01 + w1 * v11 + w2 * v12;
           Y[3 * a + 2] = w0 * v02 + w1 * v12 + w2 * v22;
-          bl[a] += (double)(w0 * e0 + w1 * e1 + w2 * e2);
+          bl[a] += w0 * e0 + w1 * e1 + w2 * e2;
         }
         st_w<T>(Yg, k, Y);
       }
@@ -594,7 +598,7 @@ __device__ void schur_y(const BProb& p) {
       double bi = 0.0;
 #pragma unroll
       for (int a = 0; a < 6; ++a)
-        if (lane == a) bi = bl[a];
+        if (lane == a) bi = (double)bl[a];
       const double gci = (double)((const T*)p.gc)[6 * i + lane];
       const double v = fixed ? 0.0 : (-gci + bi);
       ((T*)p.b)[6 * i + lane] = (T)v;
@@ -603,8 +607,8 @@ __device__ void schur_y(const BProb& p) {
   }
 }
 
-// Item sums: thread per item, sum over its pairs of Y_k1 W_k2^T (6 x 6) in a
-// fixed order into part[item].
+// Item sums: thread per item, sum over its pairs of Y_k1 W_k2^T (6 x 6) in
+// a fixed order into part[item].
 template <typename T>
 __device__ void schur_items(const BProb& p) {
   const int C = p.C;
@@ -614,14 +618,7 @@ __device__ void schur_items(const BProb& p) {
   T* part = (T*)p.part;
   for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
     const int pb = p.item_beg[it];
-    // the item's block: the last block whose first item is <= it
-    int lo = 0, hi = C * C - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (p.blk_item[mid] <= it) lo = mid;
-      else hi = mid - 1;
-    }
-    const int pe = min(pb + kPairItem, p.blk_ptr[lo + 1]);
+    const int pe = min(pb + kPairItem, p.blk_ptr[p.item_blk[it] + 1]);
     T acc[36];
 #pragma unroll
     for (int e = 0; e < 36; ++e) acc[e] = T(0);
@@ -747,7 +744,10 @@ __device__ void build_pairs(BProb& p, int* wsm, Smem& sm) {
   cta_exclusive_scan(p.blk_item, C * C + 1, sm.scan);
   for (int b = threadIdx.x; b < C * C; b += blockDim.x) {
     const int i0 = p.blk_item[b], i1 = p.blk_item[b + 1];
-    for (int t = i0; t < i1; ++t) p.item_beg[t] = p.blk_ptr[b] + (t - i0) * kPairItem;
+    for (int t = i0; t < i1; ++t) {
+      p.item_beg[t] = p.blk_ptr[b] + (t - i0) * kPairItem;
+      p.item_blk[t] = b;
+    }
   }
   __syncthreads();
 }
@@ -1084,11 +1084,13 @@ __device__ void lm_iteration(BProb& p, const BatchRun& a, Smem& sm, T* dyn, size
   pc.mark(kPhDamp);
   schur_y<T>(p);
   __syncthreads();
+  pc.mark(kPhSchurY);
   schur_items<T>(p);
   __syncthreads();
+  pc.mark(kPhSchurItems);
   schur_blocks<T>(p, mu);
   __syncthreads();
-  pc.mark(kPhSchur);
+  pc.mark(kPhSchurBlocks);
   const int n = 6 * p.C;
   const bool ok = cholesky<T>((T*)p.S, n, dyn, dyn_bytes, sm);
   pc.mark(kPhCholesky);
