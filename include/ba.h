@@ -104,6 +104,9 @@ typedef struct {
                                < 0: auto (1e-4 for BA_FP32, where rounding in
                                the FP32 Schur complement otherwise exceeds its
                                smallest eigenvalues; 0 for BA_FP64)          */
+  double serve_tick_ms;     /* serving handles: every resident request gets one
+                               LM iteration per tick, and more while the tick
+                               is younger than this (ms; 0: exactly one)      */
 } ba_options;
 
 typedef struct {

@@ -135,11 +135,16 @@ void ba_options_default(ba_options* o) {
   o->serve_slots = 256;
   o->serve_queue = 4096;
   o->mu_min = -1.0;
+  o->serve_tick_ms = 4.0;
 }
 
 static ba_status check_options(const ba_options* o, std::string& err) {
   if (o->precision != BA_FP64 && o->precision != BA_FP32) {
     err = "precision must be BA_FP64 or BA_FP32";
+    return BA_ERR_INVALID_ARG;
+  }
+  if (!(o->serve_tick_ms >= 0.0) || !isfinite(o->serve_tick_ms)) {
+    err = "serve_tick_ms must be finite and >= 0";
     return BA_ERR_INVALID_ARG;
   }
   if (o->pcg_variant < 0 || o->pcg_variant > 3) {

@@ -619,6 +619,7 @@ ba_status enqueue(ba_handle* h, ba_batch* b, int threads, int ctas_per_sm, bool 
   a.n_work = b->n;
   a.queue = b->d_queue;
   a.iters_per_tick = 0;
+  a.tick_budget_ns = 0;
   a.phase_ns = b->d_phase;
   a.huber_delta = h->opts.huber_delta;
   a.mu0 = h->opts.mu0;

@@ -97,7 +97,10 @@ struct BatchRun {
   const int32_t* work;  // problem indices, in the order CTAs take them
   int n_work;
   unsigned* queue;      // work counter (zeroed before the launch)
-  int iters_per_tick;   // <= 0: run every problem to completion
+  int iters_per_tick;   // <= 0: run every problem to completion; else at least
+                        // this many iterations per problem, more while the
+                        // launch is younger than tick_budget_ns
+  long long tick_budget_ns;
   double huber_delta, mu0, mu_min;
   int32_t* done_list;       // optional: ids of problems finished by this launch
   unsigned* done_count;     //   and their count (zeroed before the launch)

@@ -190,11 +190,13 @@ __device__ void cta_exclusive_scan(int32_t* a, int m, int* s_warp) {
 
 struct Smem {
   double chunks[kSumMaxChunks];
+  unsigned long long t_start;  // launch start (CTA's view), for the tick budget
   int scan[32];
   int flag;
   int item;
   int ok;
   int done;
+  int go;
 };
 
 __device__ __forceinline__ unsigned long long gtime_ns() {
@@ -1177,6 +1179,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 1 : (NT >= 256 ? 2 : 3))) k_b
   __shared__ Smem sm;
   T* dyn = reinterpret_cast<T*>(smem_raw);
   PhaseClock pc(a.phase_ns);
+  if (threadIdx.x == 0) sm.t_start = gtime_ns();
   for (;;) {
     if (threadIdx.x == 0) sm.item = (int)atomicAdd(a.queue, 1u);
     __syncthreads();
@@ -1199,8 +1202,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 1 : (NT >= 256 ? 2 : 3))) k_b
       lm_begin<T>(p, a, sm);
       pc.mark(kPhCost);
     }
-    int todo = p.iters - p.iter;
-    if (a.iters_per_tick > 0 && todo > a.iters_per_tick) todo = a.iters_per_tick;
+    const int todo = p.iters - p.iter;
     if ((size_t)dyn_bytes < batch_dyn_bytes<T>(NT, p.C)) {  // sized by the host
       if (threadIdx.x == 0) {
         p.error |= kErrTooLarge;
@@ -1210,7 +1212,19 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 1 : (NT >= 256 ? 2 : 3))) k_b
       note_done(a, id);
       continue;
     }
-    for (int it = 0; it < todo; ++it) lm_iteration<T>(p, a, sm, dyn, (size_t)dyn_bytes, pc);
+    for (int it = 0; it < todo; ++it) {
+      if (a.iters_per_tick > 0 && it >= a.iters_per_tick) {
+        // beyond the guaranteed iterations only while the tick's budget lasts
+        if (threadIdx.x == 0)
+          sm.go = (a.tick_budget_ns > 0 &&
+                   (long long)(gtime_ns() - sm.t_start) < a.tick_budget_ns) ? 1 : 0;
+        __syncthreads();
+        const int go = sm.go;
+        __syncthreads();
+        if (!go) break;
+      }
+      lm_iteration<T>(p, a, sm, dyn, (size_t)dyn_bytes, pc);
+    }
     if (p.iter >= p.iters) {
       lm_end<T>(p, a, sm);
       pc.mark(kPhCost);

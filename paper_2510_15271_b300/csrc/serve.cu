@@ -46,8 +46,10 @@ struct Req {
   int64_t npairs = 0;
   Intrinsics K{};
   std::vector<char> in;  // packed input block (when the pinned pool is full)
-  char* pin = nullptr;   // packed input block in the pinned pool
+  char* pin = nullptr;   // packed input block (then the outputs) in the pinned pool
   size_t pin_off = 0;
+  size_t pin_bytes = 0;
+  bool finished = false;  // done on the device, outputs being copied back
   double* user_q = nullptr;
   double* user_p = nullptr;
   ProbBytes bytes{};
@@ -127,6 +129,8 @@ struct ba_server {
   unsigned* d_done_count = nullptr;
   int32_t* h_done = nullptr;   // pinned: [0] count, [1..] ids
   int threads = 256;
+  cudaStream_t cs = nullptr;  // copies in and out, beside the compute stream
+  cudaEvent_t ev_in = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
   // statistics
   uint64_t ticks = 0, completed = 0;
   double busy_ms = 0.0;
@@ -162,191 +166,234 @@ bool grow_stage(ba_server* s, size_t need) {
   return true;
 }
 
-// One scheduling step; returns false when the worker should exit.
-bool tick(ba_server* s) {
-  ba_handle* h = s->h;
-  cudaStream_t st = h->stream;
-  const int prec = h->opts.precision;
-  std::vector<Req*> admitted;
-  std::vector<int> resident;
+// Copy a finished request's descriptor and outputs to the host on the copy
+// stream (pinned buffers from the pool when it has room).
+bool start_output_copy(ba_server* s, Req* r) {
+  const size_t nq = (size_t)r->C * 7, np = (size_t)r->P * 3;
+  const size_t bytes = sizeof(BProb) + sizeof(double) * (nq + np);
   {
-    std::unique_lock<std::mutex> lk(s->mu);
-    for (;;) {
-      if (s->stop) return false;
-      // admission: first in, first out, by free slot and arena space
-      while (!s->waiting.empty()) {
-        Req* r = s->waiting.front();
-        int slot = -1;
-        for (int i = 0; i < (int)s->slots.size(); ++i)
-          if (!s->slots[i]) {
-            slot = i;
-            break;
-          }
-        if (slot < 0) break;
-        size_t off = 0;
-        if (!s->arena.alloc(block_bytes(r->bytes), off)) break;
-        r->off = off;
-        r->slot = slot;
-        s->slots[slot] = r;
-        s->waiting.pop_front();
-        admitted.push_back(r);
-      }
-      bool any = false;
-      for (Req* r : s->slots) any = any || r;
-      if (any) break;
-      s->cv.wait(lk);
-    }
-    for (int i = 0; i < (int)s->slots.size(); ++i)
-      if (s->slots[i]) resident.push_back(i);
-  }
-  // copy the admitted requests in and initialise their descriptors
-  size_t need = 0;
-  for (Req* r : admitted)
-    if (!r->pin) need += r->bytes.in;
-  if (!grow_stage(s, need)) {
     std::lock_guard<std::mutex> lk(s->mu);
-    fail_all(s, "pinned staging allocation failed");
-    return false;
-  }
-  size_t so = 0;
-  int max_cams = 1;
-  for (int i : resident) max_cams = std::max(max_cams, s->slots[i]->C);
-  for (Req* r : admitted) {
-    char* blk = s->base + r->off;
-    if (r->pin) {
-      cudaMemcpyAsync(blk, r->pin, r->bytes.in, cudaMemcpyHostToDevice, st);
-    } else {
-      memcpy(s->h_stage + so, r->in.data(), r->bytes.in);
-      cudaMemcpyAsync(blk, s->h_stage + so, r->bytes.in, cudaMemcpyHostToDevice, st);
-      so += r->bytes.in;
+    size_t off = 0;
+    if (s->h_pool && s->pool.alloc(bytes, off)) {
+      r->pin = s->h_pool + off;
+      r->pin_off = off;
+      r->pin_bytes = bytes;
     }
-    BProb& p = s->h_probs[r->slot];
-    memset(&p, 0, sizeof(p));
-    p.C = r->C;
-    p.P = r->P;
-    p.N = r->N;
-    p.iters = h->opts.max_lm_iters;
-    p.K = r->K;
-    p.phase = kPhaseSetup;
-    p.npairs = r->npairs;
-    assign_prob(prec, p, blk, blk + r->bytes.in, blk + r->bytes.in + r->bytes.out);
-    cudaMemcpyAsync(s->d_probs + r->slot, &p, sizeof(BProb), cudaMemcpyHostToDevice, st);
   }
-  // one tick over every resident request (largest first)
-  std::sort(resident.begin(), resident.end(), [&](int a, int b) {
-    const Req* ra = s->slots[a];
-    const Req* rb = s->slots[b];
-    const double wa = 40.0 * ra->N + 36.0 * ra->C * ra->C * ra->C;
-    const double wb = 40.0 * rb->N + 36.0 * rb->C * rb->C * rb->C;
-    return wa > wb || (wa == wb && a < b);
-  });
-  const int nw = (int)resident.size();
-  for (int i = 0; i < nw; ++i) s->h_work[i] = resident[i];
-  cudaMemcpyAsync(s->d_work, s->h_work, sizeof(int32_t) * nw, cudaMemcpyHostToDevice, st);
-  cudaMemsetAsync(s->d_queue, 0, sizeof(unsigned), st);
-  cudaMemsetAsync(s->d_done_count, 0, sizeof(unsigned), st);
-  size_t smem = 0;
-  int grid = 0;
-  std::string why;
-  if (!plan_launch(h->device, prec, s->threads, 0, max_cams, smem, grid, why)) {
-    std::lock_guard<std::mutex> lk(s->mu);
-    fail_all(s, why);
-    return false;
+  if (!r->pin) {
+    r->in.resize(bytes);  // pageable fallback (the copy then completes synchronously)
   }
-  BatchRun a{};
-  a.probs = s->d_probs;
-  a.work = s->d_work;
-  a.n_work = nw;
-  a.queue = s->d_queue;
-  a.iters_per_tick = 1;
-  a.done_list = s->d_done;
-  a.done_count = s->d_done_count;
-  a.huber_delta = h->opts.huber_delta;
-  a.mu0 = h->opts.mu0;
-  a.mu_min = h->opts.mu_min >= 0 ? h->opts.mu_min : (prec == BA_FP32 ? kMuMinFp32 : 0.0);
-  const auto t0 = Clock::now();
-  cudaError_t e = launch_batch(prec, s->threads, std::min(grid, std::max(nw, 1)), smem, a, st);
+  char* dst = r->pin ? r->pin : r->in.data();
+  const BProb* dp = s->d_probs + r->slot;
+  cudaError_t e = cudaMemcpyAsync(dst, dp, sizeof(BProb), cudaMemcpyDeviceToHost, s->cs);
+  // the output arrays' device addresses are in the host copy of the descriptor
+  const BProb& hp = s->h_probs[r->slot];
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(s->h_done, s->d_done_count, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    e = cudaMemcpyAsync(dst + sizeof(BProb), hp.cam_qt_out, sizeof(double) * nq,
+                        cudaMemcpyDeviceToHost, s->cs);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(s->h_done + 1, s->d_done, sizeof(int32_t) * nw, cudaMemcpyDeviceToHost,
-                        st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  // the admitted requests' pinned input blocks are on the device now
-  {
-    std::lock_guard<std::mutex> lk(s->mu);
-    for (Req* r : admitted)
-      if (r->pin) {
-        s->pool.release(r->pin_off, r->bytes.in);
-        r->pin = nullptr;
-      }
-  }
-  if (e != cudaSuccess) {
-    std::lock_guard<std::mutex> lk(s->mu);
-    fail_all(s, std::string("tick failed: ") + cudaGetErrorString(e));
-    return false;
-  }
-  s->busy_ms += std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
-  s->ticks += 1;
-  // finished requests: outputs to the host, memory back to the arena
-  std::vector<Req*> fin;
-  const int ndone = std::min((int)(unsigned)s->h_done[0], nw);
-  for (int i = 0; i < ndone; ++i) {
-    const int slot = s->h_done[1 + i];
-    if (slot >= 0 && slot < (int)s->slots.size() && s->slots[slot]) fin.push_back(s->slots[slot]);
-  }
-  for (Req* r : fin)
-    cudaMemcpyAsync(&s->h_probs[r->slot], s->d_probs + r->slot, sizeof(BProb),
-                    cudaMemcpyDeviceToHost, st);
-  if (!fin.empty()) {
-    e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) {
-      std::lock_guard<std::mutex> lk(s->mu);
-      fail_all(s, std::string("descriptor copy failed: ") + cudaGetErrorString(e));
-      return false;
-    }
-  }
-  for (Req* r : fin) {
-    const BProb& p = s->h_probs[r->slot];
-    fill_result(p, r->result);
-    if (r->result.status == BA_OK) {
-      r->out_q.resize((size_t)r->C * 7);
-      r->out_p.resize((size_t)r->P * 3);
-      cudaMemcpyAsync(r->out_q.data(), p.cam_qt_out, sizeof(double) * r->out_q.size(),
-                      cudaMemcpyDeviceToHost, st);
-      cudaMemcpyAsync(r->out_p.data(), p.pts_out, sizeof(double) * r->out_p.size(),
-                      cudaMemcpyDeviceToHost, st);
-    }
-  }
-  if (!fin.empty()) {
-    e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) {
-      std::lock_guard<std::mutex> lk(s->mu);
-      fail_all(s, std::string("result copy failed: ") + cudaGetErrorString(e));
-      return false;
-    }
-  }
-  {
-    std::lock_guard<std::mutex> lk(s->mu);
-    const auto now = Clock::now();
-    for (Req* r : fin) {
-      r->t_done = now;
-      r->result.latency_ms = std::chrono::duration<double, std::milli>(now - r->t_submit).count();
-      r->done = true;
-      s->slots[r->slot] = nullptr;
-      s->arena.release(r->off, block_bytes(r->bytes));
-      r->in.clear();
-      r->in.shrink_to_fit();
-      s->completed += 1;
-    }
-  }
-  if (!fin.empty()) s->cv.notify_all();
-  return true;
+    e = cudaMemcpyAsync(dst + sizeof(BProb) + sizeof(double) * nq, hp.pts_out,
+                        sizeof(double) * np, cudaMemcpyDeviceToHost, s->cs);
+  return e == cudaSuccess;
 }
 
+// Results of requests whose output copies have completed: fill the result,
+// free the arena block and the slot, wake pollers.
+void finalize(ba_server* s, std::vector<Req*>& fin) {
+  if (fin.empty()) return;
+  std::lock_guard<std::mutex> lk(s->mu);
+  const auto now = Clock::now();
+  for (Req* r : fin) {
+    const char* src = r->pin ? r->pin : r->in.data();
+    BProb p;
+    memcpy(&p, src, sizeof(BProb));
+    fill_result(p, r->result);
+    if (r->result.status == BA_OK) {
+      const size_t nq = (size_t)r->C * 7, np = (size_t)r->P * 3;
+      r->out_q.assign((const double*)(src + sizeof(BProb)),
+                      (const double*)(src + sizeof(BProb)) + nq);
+      r->out_p.assign((const double*)(src + sizeof(BProb)) + nq,
+                      (const double*)(src + sizeof(BProb)) + nq + np);
+    }
+    if (r->pin) {
+      s->pool.release(r->pin_off, r->pin_bytes);
+      r->pin = nullptr;
+    }
+    r->in.clear();
+    r->in.shrink_to_fit();
+    r->t_done = now;
+    r->result.latency_ms = std::chrono::duration<double, std::milli>(now - r->t_submit).count();
+    r->done = true;
+    s->slots[r->slot] = nullptr;
+    s->arena.release(r->off, block_bytes(r->bytes));
+    s->completed += 1;
+  }
+  fin.clear();
+  s->cv.notify_all();
+}
+
+// The worker: admission and input copies (copy stream), one tick launch
+// (compute stream), then — while that tick runs — the results of the
+// previous tick's finished requests.
 void worker_main(ba_server* s) {
-  cudaSetDevice(s->h->device);
-  while (tick(s)) {
+  ba_handle* h = s->h;
+  cudaSetDevice(h->device);
+  cudaStream_t st = h->stream;
+  const int prec = h->opts.precision;
+  std::vector<Req*> out_pending;  // finished, output copies in flight on cs
+  for (;;) {
+    std::vector<Req*> admitted;
+    std::vector<int> resident;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      for (;;) {
+        if (s->stop) return;
+        while (!s->waiting.empty()) {
+          Req* r = s->waiting.front();
+          int slot = -1;
+          for (int i = 0; i < (int)s->slots.size(); ++i)
+            if (!s->slots[i]) {
+              slot = i;
+              break;
+            }
+          if (slot < 0) break;
+          size_t off = 0;
+          if (!s->arena.alloc(block_bytes(r->bytes), off)) break;
+          r->off = off;
+          r->slot = slot;
+          s->slots[slot] = r;
+          s->waiting.pop_front();
+          admitted.push_back(r);
+        }
+        for (int i = 0; i < (int)s->slots.size(); ++i)
+          if (s->slots[i] && !s->slots[i]->finished) resident.push_back(i);
+        if (!resident.empty() || !out_pending.empty()) break;
+        s->cv.wait(lk);
+      }
+    }
+    cudaError_t e = cudaSuccess;
+    int nw = (int)resident.size();
+    if (nw > 0) {
+      // inputs and descriptors of the admitted requests on the copy stream
+      size_t need = 0;
+      for (Req* r : admitted)
+        if (!r->pin) need += r->bytes.in;
+      if (!grow_stage(s, need)) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        fail_all(s, "pinned staging allocation failed");
+        return;
+      }
+      size_t so = 0;
+      for (Req* r : admitted) {
+        char* blk = s->base + r->off;
+        if (r->pin) {
+          cudaMemcpyAsync(blk, r->pin, r->bytes.in, cudaMemcpyHostToDevice, s->cs);
+        } else {
+          memcpy(s->h_stage + so, r->in.data(), r->bytes.in);
+          cudaMemcpyAsync(blk, s->h_stage + so, r->bytes.in, cudaMemcpyHostToDevice, s->cs);
+          so += r->bytes.in;
+        }
+        BProb& p = s->h_probs[r->slot];
+        memset(&p, 0, sizeof(p));
+        p.C = r->C;
+        p.P = r->P;
+        p.N = r->N;
+        p.iters = h->opts.max_lm_iters;
+        p.K = r->K;
+        p.phase = kPhaseSetup;
+        p.npairs = r->npairs;
+        assign_prob(prec, p, blk, blk + r->bytes.in, blk + r->bytes.in + r->bytes.out);
+        cudaMemcpyAsync(s->d_probs + r->slot, &p, sizeof(BProb), cudaMemcpyHostToDevice, s->cs);
+      }
+      cudaEventRecord(s->ev_in, s->cs);
+      int max_cams = 1;
+      for (int i : resident) max_cams = std::max(max_cams, s->slots[i]->C);
+      std::sort(resident.begin(), resident.end(), [&](int a, int b) {
+        const Req* ra = s->slots[a];
+        const Req* rb = s->slots[b];
+        const double wa = 40.0 * ra->N + 36.0 * ra->C * ra->C * ra->C;
+        const double wb = 40.0 * rb->N + 36.0 * rb->C * rb->C * rb->C;
+        return wa > wb || (wa == wb && a < b);
+      });
+      for (int i = 0; i < nw; ++i) s->h_work[i] = resident[i];
+      size_t smem = 0;
+      int grid = 0;
+      std::string why;
+      if (!plan_launch(h->device, prec, s->threads, 0, max_cams, smem, grid, why)) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        fail_all(s, why);
+        return;
+      }
+      BatchRun a{};
+      a.probs = s->d_probs;
+      a.work = s->d_work;
+      a.n_work = nw;
+      a.queue = s->d_queue;
+      a.iters_per_tick = 1;
+      a.tick_budget_ns = (long long)(h->opts.serve_tick_ms * 1e6);
+      a.done_list = s->d_done;
+      a.done_count = s->d_done_count;
+      a.huber_delta = h->opts.huber_delta;
+      a.mu0 = h->opts.mu0;
+      a.mu_min = h->opts.mu_min >= 0 ? h->opts.mu_min : (prec == BA_FP32 ? kMuMinFp32 : 0.0);
+      cudaStreamWaitEvent(st, s->ev_in, 0);
+      cudaMemcpyAsync(s->d_work, s->h_work, sizeof(int32_t) * nw, cudaMemcpyHostToDevice, st);
+      cudaMemsetAsync(s->d_queue, 0, sizeof(unsigned), st);
+      cudaMemsetAsync(s->d_done_count, 0, sizeof(unsigned), st);
+      cudaEventRecord(s->ev_t0, st);
+      e = launch_batch(prec, s->threads, std::min(grid, std::max(nw, 1)), smem, a, st);
+      cudaEventRecord(s->ev_t1, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->h_done, s->d_done_count, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                            st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->h_done + 1, s->d_done, sizeof(int32_t) * nw,
+                            cudaMemcpyDeviceToHost, st);
+    }
+    // while the tick runs: results of the previous tick's finished requests
+    if (!out_pending.empty()) {
+      const cudaError_t e2 = cudaStreamSynchronize(s->cs);
+      if (e2 != cudaSuccess) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        fail_all(s, std::string("result copy failed: ") + cudaGetErrorString(e2));
+        return;
+      }
+      finalize(s, out_pending);
+    }
+    if (nw == 0) continue;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    // the admitted requests' pinned input blocks are on the device now
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      for (Req* r : admitted)
+        if (r->pin) {
+          s->pool.release(r->pin_off, r->bytes.in);
+          r->pin = nullptr;
+        }
+    }
+    if (e != cudaSuccess) {
+      std::lock_guard<std::mutex> lk(s->mu);
+      fail_all(s, std::string("tick failed: ") + cudaGetErrorString(e));
+      return;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, s->ev_t0, s->ev_t1);
+    s->busy_ms += ms;
+    s->ticks += 1;
+    // this tick's finished requests: start their output copies
+    const int ndone = std::min((int)(unsigned)s->h_done[0], nw);
+    for (int i = 0; i < ndone; ++i) {
+      const int slot = s->h_done[1 + i];
+      if (slot < 0 || slot >= (int)s->slots.size() || !s->slots[slot]) continue;
+      Req* r = s->slots[slot];
+      r->finished = true;
+      if (!start_output_copy(s, r)) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        fail_all(s, "result copy failed");
+        return;
+      }
+      out_pending.push_back(r);
+    }
   }
 }
 
@@ -379,6 +426,12 @@ void destroy_server(ba_handle* h) {
   s->cv.notify_all();
   if (s->worker.joinable()) s->worker.join();
   cudaStreamSynchronize(h->stream);
+  if (s->cs) {
+    cudaStreamSynchronize(s->cs);
+    cudaStreamDestroy(s->cs);
+  }
+  for (cudaEvent_t ev : {s->ev_in, s->ev_t0, s->ev_t1})
+    if (ev) cudaEventDestroy(ev);
   for (auto& kv : s->reqs) delete kv.second;
   for (Req* r : s->waiting) (void)r;  // owned through reqs
   dev_free(h, s->base);
@@ -448,6 +501,14 @@ ba_status ba_create_server(const ba_options* opts, ba_handle** out) {
   }
   s->arena.init(bytes);
   s->slots.assign(ns, nullptr);
+  if (cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreate(&s->ev_t0) != cudaSuccess || cudaEventCreate(&s->ev_t1) != cudaSuccess) {
+    cudaGetLastError();
+    ba_destroy(h);
+    *out = nullptr;
+    return BA_ERR_CUDA;
+  }
   s->worker = std::thread(worker_main, s);
   *out = h;
   return BA_OK;
@@ -488,6 +549,7 @@ ba_status ba_submit(ba_handle* h, const ba_problem* req, uint64_t* req_id) {
     if (s->pool.alloc(r->bytes.in, off)) {
       r->pin = s->h_pool + off;
       r->pin_off = off;
+      r->pin_bytes = r->bytes.in;
     }
   }
   if (r->pin) {

@@ -69,7 +69,7 @@ def test_result_same_alone_and_in_the_mix():
     assert np.array_equal(arrs[3].q_out, q_alone) and np.array_equal(arrs[3].p_out, p_alone)
     assert all(r.status == ba.BA_OK and r.latency_ms > 0 for r in results)
     assert stats["serve_completed"][0] == 11
-    assert stats["serve_tick"][0] >= 5
+    assert stats["serve_tick"][0] >= 1
 
 
 def test_served_matches_batched():
@@ -166,3 +166,18 @@ def test_invalid_request_is_reported():
         rid = ba.ba_submit(h, a)
         with pytest.raises(ba.BAError, match="INVALID"):
             _wait(h, rid)
+
+
+def test_tick_budget_does_not_change_results():
+    reqs = [_req(900 + i, cams=(10, 40), pts=(300, 2000)) for i in range(5)]
+    arrs = [ba._ProblemArrays.from_scene(s) for s in reqs]
+    out = []
+    for budget in (0.0, 50.0):
+        with _server(reqs[0], serve_tick_ms=budget) as h:
+            ids = [ba.ba_submit(h, a) for a in arrs]
+            out.append([_wait(h, rid) for rid in ids])
+            ticks = ba.ba_kernel_stats(h)["serve_tick"][0]
+        if budget == 0.0:
+            assert ticks >= 5  # one iteration per tick
+    for a, b in zip(*out):
+        assert np.array_equal(a.costs(), b.costs())
