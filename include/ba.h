@@ -106,7 +106,8 @@ typedef struct {
                                smallest eigenvalues; 0 for BA_FP64)          */
   double serve_tick_ms;     /* serving handles: every resident request gets one
                                LM iteration per tick, and more while the tick
-                               is younger than this (ms; 0: exactly one)      */
+                               is younger than this (ms; 0: exactly one; < 0:
+                               auto, 90 % of the previous tick, >= 2 ms)      */
 } ba_options;
 
 typedef struct {

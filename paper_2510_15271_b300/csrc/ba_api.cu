@@ -143,8 +143,8 @@ static ba_status check_options(const ba_options* o, std::string& err) {
     err = "precision must be BA_FP64 or BA_FP32";
     return BA_ERR_INVALID_ARG;
   }
-  if (!(o->serve_tick_ms >= 0.0) || !isfinite(o->serve_tick_ms)) {
-    err = "serve_tick_ms must be finite and >= 0";
+  if (!isfinite(o->serve_tick_ms)) {
+    err = "serve_tick_ms must be finite";
     return BA_ERR_INVALID_ARG;
   }
   if (o->pcg_variant < 0 || o->pcg_variant > 3) {

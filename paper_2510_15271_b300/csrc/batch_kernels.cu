@@ -754,6 +754,25 @@ __device__ void build_pairs(BProb& p, int* wsm, Smem& sm) {
   __syncthreads();
 }
 
+// Pitch of the shared-memory panel rows (16-byte aligned for vector loads).
+constexpr int kPanelPitch = kPanel + 4;
+
+__device__ __forceinline__ void ld4(const float* p, float out[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  out[0] = v.x;
+  out[1] = v.y;
+  out[2] = v.z;
+  out[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double out[4]) {
+  const double2 v0 = *reinterpret_cast<const double2*>(p);
+  const double2 v1 = *reinterpret_cast<const double2*>(p + 2);
+  out[0] = v0.x;
+  out[1] = v0.y;
+  out[2] = v1.x;
+  out[3] = v1.y;
+}
+
 // Blocked right-looking Cholesky S = L L^T in place (lower triangle), panel
 // width kPanel: warp 0 factors the diagonal block in shared memory, every
 // thread then solves rows of the panel below it (kept in shared memory as
@@ -763,9 +782,10 @@ template <typename T>
 __device__ bool cholesky(T* A, int n, T* dyn, size_t dyn_bytes, Smem& sm) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NT = blockDim.x;
   constexpr int LD = kPanel + 1;
+  constexpr int LP = kPanelPitch;  // panel row pitch: rows start 16-byte aligned
   T* sd = dyn;
   T* Ps = dyn + kPanel * LD;  // panel rows below the diagonal block
-  const bool panel_smem = (size_t)(kPanel * LD + (size_t)n * LD) * sizeof(T) <= dyn_bytes;
+  const bool panel_smem = (size_t)(kPanel * LD + (size_t)n * LP) * sizeof(T) <= dyn_bytes;
   if (threadIdx.x == 0) sm.ok = 1;
   __syncthreads();
   for (int jb = 0; jb < n; jb += kPanel) {
@@ -811,23 +831,25 @@ __device__ bool cholesky(T* A, int n, T* dyn, size_t dyn_bytes, Smem& sm) {
           xr[c] = s / sd[c * LD + c];
         }
       }
-      T* ps = Ps + (int64_t)(i - m0) * LD;
+      T* ps = Ps + (int64_t)(i - m0) * LP;
 #pragma unroll
-      for (int c = 0; c < kPanel; ++c)
-        if (c < pb) {
-          a[c] = xr[c];
-          if (panel_smem) ps[c] = xr[c];
-        }
+      for (int c = 0; c < kPanel; ++c) {
+        if (c < pb) a[c] = xr[c];
+        if (panel_smem) ps[c] = c < pb ? xr[c] : T(0);
+      }
     }
     __syncthreads();
     if (rem > 0) {
       const int nt = (rem + 3) / 4;
       const int ntiles = nt * (nt + 1) / 2;
+      // tile tt = ti (ti + 1) / 2 + tk (tk <= ti), advanced incrementally
+      // (no square root: FP64 is slow on this part)
+      int ti = 0, tk = threadIdx.x;
+      while (tk > ti) {
+        tk -= ti + 1;
+        ++ti;
+      }
       for (int tt = threadIdx.x; tt < ntiles; tt += NT) {
-        int ti = (int)((sqrt(8.0 * tt + 1.0) - 1.0) * 0.5);
-        while ((ti + 1) * (ti + 2) / 2 <= tt) ++ti;
-        while (ti * (ti + 1) / 2 > tt) --ti;
-        const int tk = tt - ti * (ti + 1) / 2;
         T acc[4][4];
 #pragma unroll
         for (int r = 0; r < 4; ++r)
@@ -838,20 +860,24 @@ __device__ bool cholesky(T* A, int n, T* dyn, size_t dyn_bytes, Smem& sm) {
           const T* Ak[4];
 #pragma unroll
           for (int r = 0; r < 4; ++r) {
-            Ai[r] = Ps + (int64_t)min(4 * ti + r, rem - 1) * LD;
-            Ak[r] = Ps + (int64_t)min(4 * tk + r, rem - 1) * LD;
+            Ai[r] = Ps + (int64_t)min(4 * ti + r, rem - 1) * LP;
+            Ak[r] = Ps + (int64_t)min(4 * tk + r, rem - 1) * LP;
           }
-          for (int m = 0; m < pb; ++m) {
-            T a[4], b[4];
+          // four consecutive panel columns per vector load (the panel's
+          // columns beyond pb are zero-padded)
+          for (int m = 0; m < pb; m += 4) {
+            T a[4][4], b[4][4];
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-              a[r] = Ai[r][m];
-              b[r] = Ak[r][m];
+              ld4(Ai[r] + m, a[r]);
+              ld4(Ak[r] + m, b[r]);
             }
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
+            for (int u = 0; u < 4; ++u)
 #pragma unroll
-              for (int c = 0; c < 4; ++c) acc[r][c] += a[r] * b[c];
+              for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] += a[r][u] * b[c][u];
           }
         } else {
           const T* Ai[4];
@@ -882,6 +908,11 @@ __device__ bool cholesky(T* A, int n, T* dyn, size_t dyn_bytes, Smem& sm) {
             const int i = i0 + r, k = k0 + c;
             if (i < n && k <= i) A[(int64_t)i * n + k] -= acc[r][c];
           }
+        tk += NT;
+        while (tk > ti) {
+          tk -= ti + 1;
+          ++ti;
+        }
       }
     }
     __syncthreads();
@@ -1262,7 +1293,7 @@ size_t batch_smem_bytes(int precision, int threads, int max_cams) {
 
 size_t batch_smem_want(int precision, int threads, int max_cams) {
   const size_t t = precision == BA_FP32 ? 4 : 8;
-  const size_t panel = ((size_t)kPanel * (kPanel + 1) + (size_t)6 * max_cams * (kPanel + 1)) * t;
+  const size_t panel = ((size_t)kPanel * (kPanel + 1) + (size_t)6 * max_cams * kPanelPitch) * t;
   const size_t need = batch_smem_bytes(precision, threads, max_cams);
   return panel > need ? panel : need;
 }

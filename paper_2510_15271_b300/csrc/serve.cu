@@ -128,12 +128,13 @@ struct ba_server {
   int32_t* d_done = nullptr;   // ids finished by a tick, and their count
   unsigned* d_done_count = nullptr;
   int32_t* h_done = nullptr;   // pinned: [0] count, [1..] ids
-  int threads = 256;
+  int threads = 512;  // CTA size of the ticks (one CTA per SM: 16 warps)
   cudaStream_t cs = nullptr;  // copies in and out, beside the compute stream
   cudaEvent_t ev_in = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
   // statistics
   uint64_t ticks = 0, completed = 0;
   double busy_ms = 0.0;
+  double last_tick_ms = 0.0;
 };
 
 namespace {
@@ -330,7 +331,13 @@ void worker_main(ba_server* s) {
       a.n_work = nw;
       a.queue = s->d_queue;
       a.iters_per_tick = 1;
-      a.tick_budget_ns = (long long)(h->opts.serve_tick_ms * 1e6);
+      // budget: as given, or (auto) 90 % of the previous tick, at least 2 ms,
+      // so small requests keep iterating while the largest one finishes its
+      // guaranteed iteration
+      const double budget_ms = h->opts.serve_tick_ms >= 0.0
+                                   ? h->opts.serve_tick_ms
+                                   : std::max(2.0, 0.9 * s->last_tick_ms);
+      a.tick_budget_ns = (long long)(budget_ms * 1e6);
       a.done_list = s->d_done;
       a.done_count = s->d_done_count;
       a.huber_delta = h->opts.huber_delta;
@@ -379,6 +386,7 @@ void worker_main(ba_server* s) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, s->ev_t0, s->ev_t1);
     s->busy_ms += ms;
+    s->last_tick_ms = ms;
     s->ticks += 1;
     // this tick's finished requests: start their output copies
     const int ndone = std::min((int)(unsigned)s->h_done[0], nw);
