@@ -402,13 +402,15 @@ ba_status ba_set_problem(ba_handle* h, int32_t n_cams, int32_t n_pts, int64_t n_
   CK(cudaStreamSynchronize(s));
   d.nnzb = nnzb;
   d.max_row_nnz = *std::max_element(hrow.begin(), hrow.end());
-  ok = keep(h, d.s_col, (size_t)nnzb * sizeof(int32_t)) && keep(h, d.S, (size_t)nnzb * 36 * Tsz);
+  ok = keep(h, d.s_col, (size_t)nnzb * sizeof(int32_t)) && keep(h, d.S, (size_t)nnzb * 36 * Tsz) &&
+       keep(h, d.s_mirror, (size_t)nnzb * sizeof(int32_t));
   if (!ok) {
     h->err = "ba_set_problem: out of device memory (S)";
     free_problem(h);
     return BA_ERR_OOM;
   }
   launch_pattern(d, nullptr, d.s_rowptr, 1, s);
+  launch_mirror(d, s);
   CK(cudaGetLastError());
 
   // ---- Schur pair list (pairs of observations of one point, grouped by
@@ -416,17 +418,17 @@ ba_status ba_set_problem(ba_handle* h, int32_t n_cams, int32_t n_pts, int64_t n_
   {
     std::vector<int32_t> hpt(P + 1);
     CK(cudaMemcpy(hpt.data(), d.pt_ptr, (P + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
-    int64_t np = 0;
+    int64_t bound = 0;  // sum of squared track lengths >= the number of pairs
     for (int j = 0; j < P; ++j) {
       const int64_t L = hpt[j + 1] - hpt[j];
-      np += L * L;
+      bound += L * L;
     }
-    if (np >= (int64_t)INT32_MAX - 1) {
+    if (bound >= (int64_t)INT32_MAX - 1) {
       h->err = "ba_set_problem: more than 2^31 observation pairs (sum of squared track lengths)";
       free_problem(h);
       return BA_ERR_INVALID_ARG;
     }
-    d.npairs = np;
+    int64_t np = bound;
     int32_t* cnt = (int32_t*)tmp.get((N + 1) * sizeof(int32_t));
     int32_t* pair_ptr = (int32_t*)tmp.get((N + 1) * sizeof(int32_t));
     int32_t* nch = (int32_t*)tmp.get((C + 1) * sizeof(int32_t));
@@ -441,10 +443,13 @@ ba_status ba_set_problem(ba_handle* h, int32_t n_cams, int32_t n_pts, int64_t n_
     launch_pair_counts(d, cnt, nch, s);
     launch_scan_i32(cnt, pair_ptr, N, stmp2, pair_ptr + N, s);
     launch_scan_i32(nch, d.chunk_ptr, C, stmp2, d.chunk_ptr + C, s);
-    int32_t nchunks = 0;
+    int32_t nchunks = 0, np32 = 0;
     CK(cudaMemcpyAsync(&nchunks, d.chunk_ptr + C, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&np32, pair_ptr + N, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     d.nchunks = nchunks;
+    np = np32;  // upper-triangle pairs only
+    d.npairs = np;
     uint64_t* pk0 = (uint64_t*)tmp.get(np * sizeof(uint64_t));
     uint64_t* pk1 = (uint64_t*)tmp.get(np * sizeof(uint64_t));
     int32_t* pv0 = (int32_t*)tmp.get(np * sizeof(int32_t));

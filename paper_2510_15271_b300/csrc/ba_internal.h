@@ -91,13 +91,16 @@ struct DevProblem {
   int32_t* s_rowptr = nullptr;  // [C+1]
   int32_t* s_col = nullptr;     // [nnzb]
   int32_t* s_diag = nullptr;    // [C]
+  int32_t* s_mirror = nullptr;  // [nnzb] index of block (c, i) for each block (i, c > i), else -1
   int64_t nnzb = 0;
   int max_row_nnz = 0;
   int max_cam_obs = 0;
-  // Schur pair list: every ordered pair (k1, k2) of observations of one
-  // point, grouped by (camera row i1 = cam(k1), chunk of kSchurChunk
-  // observations of that row, output block slot of cam(k2)), stable so the
-  // pairs of a segment are in (k1, k2) order.
+  // Schur pair list: every pair (k1, k2) of observations of one point with
+  // cam(k2) >= cam(k1) (S is symmetric: row i1 assembles its blocks on and
+  // right of the diagonal and writes each off-diagonal one transposed below),
+  // grouped by (camera row i1 = cam(k1), chunk of kSchurChunk observations
+  // of that row, output block slot of cam(k2)), stable so the pairs of a
+  // segment are in (k1, k2) order.
   uint16_t* pair_t = nullptr;   // [npairs] k1 - first obs of its chunk
   int32_t* pair_k2 = nullptr;   // [npairs]
   int32_t* seg_slot = nullptr;  // [nseg] block slot within the row

@@ -461,12 +461,48 @@ void launch_cams_to_qt(int C, const double* R, const double* t, double* qt, cuda
 
 namespace ba {
 
-__global__ void k_pair_counts(int64_t N, const int32_t* __restrict__ oc_pt,
-                              const int32_t* __restrict__ pt_ptr, int32_t* __restrict__ cnt) {
+// First position, in the point-order list of point j (sorted by camera), of
+// an observation in a camera >= c.
+__device__ __forceinline__ int first_partner(const int32_t* __restrict__ pt_ptr,
+                                             const int32_t* __restrict__ po_cam, int j, int c) {
+  int q = pt_ptr[j];
+  const int qe = pt_ptr[j + 1];
+  while (q < qe && po_cam[q] < c) ++q;
+  return q;
+}
+
+// S is symmetric: row i1 assembles only its blocks (i1, i2 >= i1), so an
+// observation k1 pairs with the observations of its point in cameras >=
+// cam(k1) (its own included).
+__global__ void k_pair_counts(int64_t N, const int32_t* __restrict__ oc_cam,
+                              const int32_t* __restrict__ oc_pt, const int32_t* __restrict__ pt_ptr,
+                              const int32_t* __restrict__ po_cam, int32_t* __restrict__ cnt) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int j = oc_pt[k];
-    cnt[k] = pt_ptr[j + 1] - pt_ptr[j];
+    cnt[k] = pt_ptr[j + 1] - first_partner(pt_ptr, po_cam, j, oc_cam[k]);
+  }
+}
+
+// Index of the transposed block (c, i) of every block (i, c > i) of S; -1
+// for blocks on or below the diagonal.  Thread per block row.
+__global__ void k_mirror(int C, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                         int32_t* __restrict__ mirror) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < C; i += gridDim.x * blockDim.x) {
+    for (int b = rowptr[i]; b < rowptr[i + 1]; ++b) {
+      const int c = col[b];
+      if (c <= i) {
+        mirror[b] = -1;
+        continue;
+      }
+      int lo = rowptr[c], hi = rowptr[c + 1] - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (col[mid] < i) lo = mid + 1;
+        else hi = mid;
+      }
+      mirror[b] = lo;
+    }
   }
 }
 
@@ -503,7 +539,7 @@ __global__ void k_gen_pairs(DevProblem d, const int32_t* __restrict__ chunk_ptr,
     const int32_t* cols = d.s_col + d.s_rowptr[i1];
     const int ncol = d.s_rowptr[i1 + 1] - d.s_rowptr[i1];
     const int base = pair_ptr[k];
-    const int q0 = d.pt_ptr[j], L = d.pt_ptr[j + 1] - q0;
+    const int q0 = first_partner(d.pt_ptr, d.po_cam, j, i1), L = d.pt_ptr[j + 1] - q0;
     for (int r = 0; r < L; ++r) {
       const int q = q0 + r;
       const int s = find_slot(cols, ncol, d.po_cam[q]);
@@ -549,8 +585,12 @@ __global__ void k_segments(int64_t np, const uint64_t* __restrict__ keys,
 }
 
 void launch_pair_counts(const DevProblem& d, int32_t* cnt, int32_t* nch, cudaStream_t s) {
-  k_pair_counts<<<grid_for(d.N, 256), 256, 0, s>>>(d.N, d.oc_pt, d.pt_ptr, cnt);
+  k_pair_counts<<<grid_for(d.N, 256), 256, 0, s>>>(d.N, d.oc_cam, d.oc_pt, d.pt_ptr, d.po_cam, cnt);
   k_chunk_counts<<<grid_for(d.C, 256), 256, 0, s>>>(d.C, d.cam_ptr, nch);
+}
+
+void launch_mirror(const DevProblem& d, cudaStream_t s) {
+  k_mirror<<<grid_for(d.C, 128), 128, 0, s>>>(d.C, d.s_rowptr, d.s_col, d.s_mirror);
 }
 
 void launch_gen_pairs(const DevProblem& d, const int32_t* chunk_ptr, const int32_t* pair_ptr,

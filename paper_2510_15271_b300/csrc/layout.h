@@ -35,6 +35,8 @@ void launch_cams_to_qt(int C, const double* R, const double* t, double* qt, cuda
 
 namespace ba {
 void launch_pair_counts(const DevProblem& d, int32_t* cnt, int32_t* nch, cudaStream_t s);
+// d.s_mirror from the pattern (d.s_rowptr, d.s_col)
+void launch_mirror(const DevProblem& d, cudaStream_t s);
 void launch_gen_pairs(const DevProblem& d, const int32_t* chunk_ptr, const int32_t* pair_ptr,
                       uint64_t* keys, int32_t* vals, uint16_t* gen_t, int32_t* gen_k2,
                       cudaStream_t s);

@@ -450,6 +450,7 @@ __global__ void __launch_bounds__(NT, 2) k_schur(DevProblem d, int colcap) {
       const int s = e / 36, el = e % 36;
       const int a = el / 6, bb = el % 6;
       const int col = d.s_col[rb + cb + s];
+      if (col < i) continue;  // written, transposed, by row col
       T val;
       if (fixed_i) {
         val = (col == i && a == bb) ? T(1) : T(0);
@@ -462,6 +463,7 @@ __global__ void __launch_bounds__(NT, 2) k_schur(DevProblem d, int colcap) {
         }
       }
       Sg[36 * (int64_t)(rb + cb + s) + el] = val;
+      if (col > i) Sg[36 * (int64_t)d.s_mirror[rb + cb + s] + 6 * bb + a] = val;
     }
     __syncthreads();
   }
