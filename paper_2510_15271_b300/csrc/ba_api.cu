@@ -489,9 +489,8 @@ ba_status ba_set_problem(ba_handle* h, int32_t n_cams, int32_t n_pts, int64_t n_
     CK(cudaStreamSynchronize(s));
 
     // sub-segments of at most sub_len pairs (host side, from the segment table)
-    std::vector<int32_t> hsb(nseg + 1), hslot(nseg), hcs(nchunks + 1);
+    std::vector<int32_t> hsb(nseg + 1), hcs(nchunks + 1);
     CK(cudaMemcpy(hsb.data(), d.seg_begin, (nseg + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(hslot.data(), d.seg_slot, nseg * sizeof(int32_t), cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(hcs.data(), d.chunk_seg, (nchunks + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
     const size_t smax_sub = max_dyn_smem(h->device) - 4096;
     const int colcap_guess = std::min<int>(*std::max_element(hrow.begin(), hrow.end()), 64);
@@ -506,19 +505,12 @@ ba_status ba_set_problem(ba_handle* h, int32_t n_cams, int32_t n_pts, int64_t n_
       }
       if (schur_smem(prec, colcap_guess, max_subs) <= smax_sub || sub_len >= 4096) break;
     }
-    std::vector<int32_t> hss(nseg + 1), hsub, hsubslot;
-    hsub.reserve((size_t)nseg * 2);
-    for (int sg = 0; sg < nseg; ++sg) {
-      hss[sg] = (int32_t)hsub.size();
-      for (int p = hsb[sg]; p < hsb[sg + 1]; p += sub_len) {
-        hsub.push_back(p);
-        hsubslot.push_back(hslot[sg]);
-      }
-    }
-    hss[nseg] = (int32_t)hsub.size();
-    const int nsub = (int)hsub.size();
-    hsub.push_back((int32_t)np);
-    ok = keep(h, d.sub_begin, (nsub + 1) * sizeof(int32_t)) &&
+    // the table itself is built on the device: counts, scan, fill
+    int64_t nsub64 = 0;
+    for (int sg = 0; sg < nseg; ++sg) nsub64 += (hsb[sg + 1] - hsb[sg] + sub_len - 1) / sub_len;
+    const int nsub = (int)nsub64;
+    int32_t* scnt = (int32_t*)tmp.get((size_t)(nseg + 1) * sizeof(int32_t));
+    ok = scnt && keep(h, d.sub_begin, (nsub + 1) * sizeof(int32_t)) &&
          keep(h, d.sub_slot, std::max(nsub, 1) * sizeof(int32_t)) &&
          keep(h, d.seg_sub, (nseg + 1) * sizeof(int32_t));
     if (!ok) {
@@ -526,9 +518,12 @@ ba_status ba_set_problem(ba_handle* h, int32_t n_cams, int32_t n_pts, int64_t n_
       free_problem(h);
       return BA_ERR_OOM;
     }
-    CK(cudaMemcpy(d.sub_begin, hsub.data(), (nsub + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
-    if (nsub) CK(cudaMemcpy(d.sub_slot, hsubslot.data(), nsub * sizeof(int32_t), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d.seg_sub, hss.data(), (nseg + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+    launch_sub_counts(nseg, d.seg_begin, sub_len, scnt, s);
+    launch_scan_i32(scnt, d.seg_sub, nseg, stmp2, d.seg_sub + nseg, s);
+    launch_sub_fill(nseg, d.seg_begin, d.seg_slot, d.seg_sub, sub_len, d.sub_begin, d.sub_slot, s);
+    const int32_t npi = (int32_t)np;
+    CK(cudaMemcpyAsync(d.sub_begin + nsub, &npi, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    CK(cudaGetLastError());
     d.nsub = nsub;
     d.sub_len = sub_len;
     d.max_chunk_subs = max_subs;

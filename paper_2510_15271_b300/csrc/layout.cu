@@ -584,6 +584,39 @@ __global__ void k_segments(int64_t np, const uint64_t* __restrict__ keys,
   }
 }
 
+// Sub-segments of at most sub_len consecutive pairs: count per segment, then
+// (after an exclusive scan into seg_sub) the first pair and the slot of each.
+__global__ void k_sub_counts(int nseg, const int32_t* __restrict__ seg_begin, int sub_len,
+                             int32_t* __restrict__ cnt) {
+  for (int sg = blockIdx.x * blockDim.x + threadIdx.x; sg < nseg; sg += gridDim.x * blockDim.x)
+    cnt[sg] = (seg_begin[sg + 1] - seg_begin[sg] + sub_len - 1) / sub_len;
+}
+
+__global__ void k_sub_fill(int nseg, const int32_t* __restrict__ seg_begin,
+                           const int32_t* __restrict__ seg_slot, const int32_t* __restrict__ seg_sub,
+                           int sub_len, int32_t* __restrict__ sub_begin,
+                           int32_t* __restrict__ sub_slot) {
+  for (int sg = blockIdx.x * blockDim.x + threadIdx.x; sg < nseg; sg += gridDim.x * blockDim.x) {
+    int u = seg_sub[sg];
+    for (int q = seg_begin[sg]; q < seg_begin[sg + 1]; q += sub_len, ++u) {
+      sub_begin[u] = q;
+      sub_slot[u] = seg_slot[sg];
+    }
+  }
+}
+
+void launch_sub_counts(int nseg, const int32_t* seg_begin, int sub_len, int32_t* cnt,
+                       cudaStream_t s) {
+  k_sub_counts<<<grid_for(nseg, 256), 256, 0, s>>>(nseg, seg_begin, sub_len, cnt);
+}
+
+void launch_sub_fill(int nseg, const int32_t* seg_begin, const int32_t* seg_slot,
+                     const int32_t* seg_sub, int sub_len, int32_t* sub_begin, int32_t* sub_slot,
+                     cudaStream_t s) {
+  k_sub_fill<<<grid_for(nseg, 256), 256, 0, s>>>(nseg, seg_begin, seg_slot, seg_sub, sub_len,
+                                                  sub_begin, sub_slot);
+}
+
 void launch_pair_counts(const DevProblem& d, int32_t* cnt, int32_t* nch, cudaStream_t s) {
   k_pair_counts<<<grid_for(d.N, 256), 256, 0, s>>>(d.N, d.oc_cam, d.oc_pt, d.pt_ptr, d.po_cam, cnt);
   k_chunk_counts<<<grid_for(d.C, 256), 256, 0, s>>>(d.C, d.cam_ptr, nch);

@@ -35,6 +35,12 @@ void launch_cams_to_qt(int C, const double* R, const double* t, double* qt, cuda
 
 namespace ba {
 void launch_pair_counts(const DevProblem& d, int32_t* cnt, int32_t* nch, cudaStream_t s);
+// Sub-segments of the Schur pair list (at most sub_len pairs each)
+void launch_sub_counts(int nseg, const int32_t* seg_begin, int sub_len, int32_t* cnt,
+                       cudaStream_t s);
+void launch_sub_fill(int nseg, const int32_t* seg_begin, const int32_t* seg_slot,
+                     const int32_t* seg_sub, int sub_len, int32_t* sub_begin, int32_t* sub_slot,
+                     cudaStream_t s);
 // d.s_mirror from the pattern (d.s_rowptr, d.s_col)
 void launch_mirror(const DevProblem& d, cudaStream_t s);
 void launch_gen_pairs(const DevProblem& d, const int32_t* chunk_ptr, const int32_t* pair_ptr,
