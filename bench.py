@@ -258,14 +258,20 @@ def run_ours(args, rank, world, local_rank):
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
-        qh = np.ascontiguousarray(s.cam_qt)
-        ph = np.ascontiguousarray(s.pts)
-        ch = np.ascontiguousarray(s.obs_cam)
-        jh = np.ascontiguousarray(s.obs_pt)
-        uvh = np.ascontiguousarray(s.obs_uv)
-        fh = np.ascontiguousarray(s.cam_fixed)
-        qo = np.empty_like(qh)
-        po = np.empty_like(ph)
+        # inputs and outputs in pinned host memory (the library copies them in
+        # and out inside the timed region)
+        def pinned(a):
+            t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)), pin_memory=True)
+            out = t.numpy()
+            out[...] = a
+            return out, t
+        keep = []
+        qh, ph, ch, jh, uvh, fh = [pinned(np.ascontiguousarray(a)) for a in
+                                   (s.cam_qt, s.pts, s.obs_cam, s.obs_pt, s.obs_uv, s.cam_fixed)]
+        keep += [x[1] for x in (qh, ph, ch, jh, uvh, fh)]
+        qh, ph, ch, jh, uvh, fh = [x[0] for x in (qh, ph, ch, jh, uvh, fh)]
+        (qo, tq), (po, tp) = pinned(np.empty_like(qh)), pinned(np.empty_like(ph))
+        keep += [tq, tp]
         o = ba.options_for_scene(s, "fp32", device=local_rank)
         with ba.ba_create(o, use_torch=True) as h:
             def one():

@@ -91,11 +91,11 @@ typedef struct {
   int serve_queue;          /* maximum requests waiting for admission        */
   int profile;              /* record per-kernel device times (CUDA events
                                between the kernels of the captured loop)      */
-  int pcg_variant;          /* PCG kernel.  0: auto (1); 1: standard PCG on
+  int pcg_variant;          /* PCG kernel.  0: auto (2); 1: standard PCG on
                                a cooperative grid
                                (two grid barriers per iteration); 2:
-                               pipelined PCG (one grid barrier per iteration;
-                               in FP32 it converges less well); 3: standard
+                               pipelined PCG (one grid barrier per iteration,
+                               recurrence vectors in FP64); 3: standard
                                PCG in one thread-block cluster (hardware
                                cluster barriers, exchanges through
                                distributed shared memory; falls back to 1

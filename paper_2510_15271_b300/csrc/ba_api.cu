@@ -598,7 +598,9 @@ ba_status ba_set_problem(ba_handle* h, int32_t n_cams, int32_t n_pts, int64_t n_
   cfg.refine = (h->opts.refine && prec == BA_FP32) ? 1 : 0;
   cfg.refine_max = h->opts.refine_max;
   cfg.refine_tol = h->opts.refine_tol;
-  cfg.pcg_pipelined = h->opts.pcg_variant == 2;
+  // auto (0) takes the pipelined recurrence: one grid barrier per iteration,
+  // FP64 recurrence vectors, about as many iterations as the standard form
+  cfg.pcg_pipelined = (h->opts.pcg_variant == 2 || h->opts.pcg_variant == 0) ? 1 : 0;
   int solver = h->opts.solver;
   if (solver == BA_SOLVER_AUTO) solver = (6 * C <= h->opts.dense_max_dim) ? BA_SOLVER_DENSE : BA_SOLVER_PCG;
   cfg.solver = solver;

@@ -422,21 +422,23 @@ __device__ int pcg_solve_pipelined(const DevProblem& d, const RowSet<T>& rs,
   double* partA = d.part + kPartPcg;  // [nb][3]
   const int el = lane < 6 ? lane : 0;
 
-  T xr[RW], rr_[RW], ur[RW], wr[RW], zr[RW], qr[RW], sr[RW], pr[RW], mr[RW];
+  // The recurrence vectors are FP64 on both paths (S, M and the exchanged
+  // vectors stay in T): the pipelined recurrences drift in FP32.
+  double xr[RW], rr_[RW], ur[RW], wr[RW], zr[RW], qr[RW], sr[RW], pr[RW], mr[RW];
   // r = rhs, u = M r (published for w = S u)
 #pragma unroll
   for (int m = 0; m < RW; ++m) {
     const int i = rs.r0 + warp + m * NW;
-    xr[m] = rr_[m] = ur[m] = wr[m] = zr[m] = qr[m] = sr[m] = pr[m] = mr[m] = T(0);
+    xr[m] = rr_[m] = ur[m] = wr[m] = zr[m] = qr[m] = sr[m] = pr[m] = mr[m] = 0.0;
     if (i >= rs.r1) continue;
-    const T ri = lane < 6 ? rhs[6 * i + el] : T(0);
+    const double ri = lane < 6 ? (double)rhs[6 * i + el] : 0.0;
     rr_[m] = ri;
     const T* M = rs.minv(i);
-    T ui = T(0);
+    double ui = 0.0;
 #pragma unroll
-    for (int f = 0; f < 6; ++f) ui += M[6 * el + f] * __shfl_sync(0xffffffffu, ri, f);
+    for (int f = 0; f < 6; ++f) ui += (double)M[6 * el + f] * __shfl_sync(0xffffffffu, ri, f);
     ur[m] = ui;
-    if (lane < 6) ub[6 * i + el] = ui;
+    if (lane < 6) ub[6 * i + el] = (T)ui;
   }
   grid_barrier(d.barrier, nb, err);
   // w = S u
@@ -448,8 +450,11 @@ __device__ int pcg_solve_pipelined(const DevProblem& d, const RowSet<T>& rs,
     T wi[6];
     if (STAGED) row_spmv<T>(rs, i, [&](int idx) { return rs.sv[idx]; }, wi);
     else row_spmv<T>(rs, i, [&](int idx) { return ldcg(ub + idx); }, wi);
-    wr[m] = pick6(wi, el);
+    wr[m] = (double)pick6(wi, el);
   }
+  // scalars: thread 0 (FP64 is slow on this part), broadcast
+  __shared__ double s_al, s_bt;
+  __shared__ int s_go;
   double bnorm = -1.0, gamma_prev = 0.0, alpha_prev = 0.0, rr = 0.0;
   int k = 0;
   for (;;) {
@@ -461,37 +466,46 @@ __device__ int pcg_solve_pipelined(const DevProblem& d, const RowSet<T>& rs,
       const int i = rs.r0 + warp + m * NW;
       if (i >= rs.r1) continue;
       const T* M = rs.minv(i);
-      const T wi = lane < 6 ? wr[m] : T(0);
-      T mi = T(0);
+      const double wi = lane < 6 ? wr[m] : 0.0;
+      double mi = 0.0;
 #pragma unroll
-      for (int f = 0; f < 6; ++f) mi += M[6 * el + f] * __shfl_sync(0xffffffffu, wi, f);
+      for (int f = 0; f < 6; ++f) mi += (double)M[6 * el + f] * __shfl_sync(0xffffffffu, wi, f);
       mr[m] = mi;
       if (lane < 6) {
-        mo[6 * i + el] = mi;
-        loc[0] += (double)rr_[m] * (double)ur[m];
-        loc[1] += (double)wr[m] * (double)ur[m];
-        loc[2] += (double)rr_[m] * (double)rr_[m];
+        mo[6 * i + el] = (T)mi;
+        loc[0] += rr_[m] * ur[m];
+        loc[1] += wr[m] * ur[m];
+        loc[2] += rr_[m] * rr_[m];
       }
     }
     cta_partials<NT, 3>(loc, red, partA, 3);
     grid_barrier(d.barrier, nb, err);
     double tot[3];
     all_partials<3>(partA, 3, nb, tot);
-    const double gamma = tot[0], delta = tot[1];
-    rr = tot[2];
-    if (bnorm < 0.0) bnorm = sqrt(rr);
-    if (!(k < max_iters && sqrt(rr) > tol * bnorm) || ld_err(err)) break;
-    double beta, alpha;
-    if (k == 0) {
-      beta = 0.0;
-      alpha = gamma / delta;
-    } else {
-      beta = gamma / gamma_prev;
-      const double den = delta - beta * gamma / alpha_prev;
-      alpha = gamma / den;
+    if (threadIdx.x == 0) {
+      const double gamma = tot[0], delta = tot[1];
+      rr = tot[2];
+      if (bnorm < 0.0) bnorm = sqrt(rr);
+      int go = (k < max_iters && sqrt(rr) > tol * bnorm && !ld_err(err)) ? 1 : 0;
+      double beta = 0.0, alpha = 0.0;
+      if (go) {
+        if (k == 0) {
+          alpha = gamma / delta;
+        } else {
+          beta = gamma / gamma_prev;
+          alpha = gamma / (delta - beta * gamma / alpha_prev);
+        }
+        if (!(alpha > 0.0) || !isfinite(alpha)) go = 0;  // curvature not positive
+      }
+      s_go = go;
+      s_al = alpha;
+      s_bt = beta;
+      gamma_prev = gamma;
+      alpha_prev = alpha;
     }
-    if (!(alpha > 0.0) || !isfinite(alpha)) break;  // curvature not positive
-    const T bt = (T)beta, al = (T)alpha;
+    __syncthreads();
+    if (!s_go) break;
+    const double bt = s_bt, al = s_al;
     // n = S m; recurrences
     if (STAGED) stage<T, NT>(rs, mo, (const T*)nullptr, T(0));
 #pragma unroll
@@ -501,7 +515,7 @@ __device__ int pcg_solve_pipelined(const DevProblem& d, const RowSet<T>& rs,
       T ni6[6];
       if (STAGED) row_spmv<T>(rs, i, [&](int idx) { return rs.sv[idx]; }, ni6);
       else row_spmv<T>(rs, i, [&](int idx) { return ldcg(mo + idx); }, ni6);
-      const T ni = pick6(ni6, el);
+      const double ni = (double)pick6(ni6, el);
       zr[m] = ni + bt * zr[m];
       qr[m] = mr[m] + bt * qr[m];
       sr[m] = wr[m] + bt * sr[m];
@@ -511,15 +525,14 @@ __device__ int pcg_solve_pipelined(const DevProblem& d, const RowSet<T>& rs,
       ur[m] = ur[m] - al * qr[m];
       wr[m] = wr[m] - al * zr[m];
     }
-    gamma_prev = gamma;
-    alpha_prev = alpha;
     ++k;
   }
 #pragma unroll
   for (int m = 0; m < RW; ++m) {
     const int i = rs.r0 + warp + m * NW;
-    if (i < rs.r1 && lane < 6) x[6 * i + el] = xr[m];
+    if (i < rs.r1 && lane < 6) x[6 * i + el] = (T)xr[m];
   }
+  // rr (and so *rel) is current in thread 0 only
   *rel = bnorm > 0.0 ? sqrt(rr) / bnorm : 0.0;
   return k;
 }
@@ -826,11 +839,20 @@ bool plan_pcg(int precision, int device, const std::vector<int32_t>& rowptr,
   const int per_sm_plain = pcg_occupancy(pcg_fn_prec(precision, false, 1, pipe), 0);
   const int gmax = std::max(1, std::min(per_sm_plain * sms, 1024));
   int G = std::max(1, std::min(gmax, (C + kPcgWarps - 1) / kPcgWarps));
-  int R = (C + G - 1) / G;
-  G = (C + R - 1) / R;
-  int rw = 1;
-  while (rw * kPcgWarps < R) rw *= 2;
-  if (rw > 16) return false;
+  int R = 1, rw = 1;
+  // the cooperative grid must be co-resident with the variant it launches
+  // (more rows per warp: more registers, fewer CTAs per SM)
+  for (int attempt = 0;; ++attempt) {
+    R = (C + G - 1) / G;
+    G = (C + R - 1) / R;
+    rw = 1;
+    while (rw * kPcgWarps < R) rw *= 2;
+    if (rw > 16) return false;
+    const int occ = pcg_occupancy(pcg_fn_prec(precision, false, rw, pipe), 0);
+    if (occ * sms >= G) break;
+    if (occ < 1 || attempt >= 8) return false;
+    G = occ * sms;
+  }
   // per-CTA column lists
   plan.ucol.clear();
   plan.uptr.assign(G + 1, 0);
