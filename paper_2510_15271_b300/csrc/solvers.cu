@@ -144,13 +144,19 @@ struct RowSet {
 };
 
 // sv = a + beta b over the listed columns (b may be null); coalesced: the 6
-// values of a column are consecutive in both.
+// values of a column are consecutive in both.  stage_nosync leaves the
+// barrier to the caller (so other loads can be in flight meanwhile).
 template <typename T, int NT>
-__device__ __forceinline__ void stage(const RowSet<T>& rs, const T* a, const T* b, T beta) {
+__device__ __forceinline__ void stage_nosync(const RowSet<T>& rs, const T* a, const T* b, T beta) {
   for (int idx = threadIdx.x; idx < rs.nu * 6; idx += NT) {
     const int g = 6 * rs.ucol[idx / 6] + idx % 6;
     rs.sv[idx] = b ? ldcg(a + g) + beta * ldcg(b + g) : ldcg(a + g);
   }
+}
+
+template <typename T, int NT>
+__device__ __forceinline__ void stage(const RowSet<T>& rs, const T* a, const T* b, T beta) {
+  stage_nosync<T, NT>(rs, a, b, beta);
   __syncthreads();
 }
 
@@ -480,6 +486,9 @@ __device__ int pcg_solve_pipelined(const DevProblem& d, const RowSet<T>& rs,
     }
     cta_partials<NT, 3>(loc, red, partA, 3);
     grid_barrier(d.barrier, nb, err);
+    // the next product's input (m of the listed columns) and the partial sums
+    // are read together (all_partials ends with a CTA barrier)
+    if (STAGED) stage_nosync<T, NT>(rs, mo, (const T*)nullptr, T(0));
     double tot[3];
     all_partials<3>(partA, 3, nb, tot);
     if (threadIdx.x == 0) {
@@ -506,8 +515,7 @@ __device__ int pcg_solve_pipelined(const DevProblem& d, const RowSet<T>& rs,
     __syncthreads();
     if (!s_go) break;
     const double bt = s_bt, al = s_al;
-    // n = S m; recurrences
-    if (STAGED) stage<T, NT>(rs, mo, (const T*)nullptr, T(0));
+    // n = S m (m staged above); recurrences
 #pragma unroll
     for (int m = 0; m < RW; ++m) {
       const int i = rs.r0 + warp + m * NW;
