@@ -179,3 +179,31 @@ def test_eager_and_graph_launches_agree():
     e, _ = _batch(ws, "fp32", iters=3, use_graph=0)
     for a, b in zip(g, e):
         assert np.array_equal(a.costs(), b.costs())
+
+
+def test_large_window_uses_the_global_memory_cholesky():
+    """300 cameras: the Cholesky panel (1800 rows) no longer fits in shared
+    memory and the factorisation runs on the global-memory path."""
+    s = scenes.make_scene("window", seed=22, n_cams=300, n_pts=2500)
+    res, _ = _batch([s], "fp64", iters=3)
+    _, ref = _oracle(s, 3)
+    rel = np.abs(res[0].costs() - ref.costs) / ref.costs
+    assert rel.max() <= COST_RTOL, (rel, res[0].costs(), ref.costs)
+
+
+def test_minimal_window():
+    s = scenes.make_scene("window", seed=23, n_cams=2, n_pts=12)
+    res, _ = _batch([s], "fp64", iters=4)
+    _, ref = _oracle(s, 4)
+    rel = np.abs(res[0].costs() - ref.costs) / np.maximum(ref.costs, 1e-300)
+    assert rel.max() <= COST_RTOL, (res[0].costs(), ref.costs)
+
+
+def test_all_cameras_fixed_window_moves_only_points():
+    s = scenes.make_scene("window", seed=24, n_cams=8, n_pts=200)
+    s.cam_fixed = np.ones(s.n_cams, dtype=np.uint8)
+    res, arrs = _batch([s], "fp64", iters=4)
+    _, ref = _oracle(s, 4)
+    rel = np.abs(res[0].costs() - ref.costs) / ref.costs
+    assert rel.max() <= COST_RTOL
+    np.testing.assert_allclose(arrs[0].q_out[:, 4:], s.cam_qt[:, 4:], atol=1e-12)
