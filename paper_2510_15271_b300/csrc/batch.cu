@@ -114,7 +114,7 @@ void carve_work(Carve& c, BProb& p, int precision, int C, int P, int64_t N, int6
   p.gp = c.take_bytes((size_t)P * 3 * t);
   p.e = c.take_bytes((size_t)P * 3 * t);
   p.Vinv = c.take<double>((size_t)P * 6);
-  p.S = c.take_bytes(n * n * t);
+  p.S = c.take_bytes(n * (size_t)dense_ld((int)n) * t);
   p.b = c.take_bytes(n * t);
   p.x = c.take_bytes(n * t);
   p.cpart = c.take<double>((size_t)C * 2);

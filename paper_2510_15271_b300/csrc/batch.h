@@ -124,6 +124,10 @@ enum : int {
   kPhaseCount
 };
 
+// Row stride of a problem's dense S (n = 6C rounded up to a multiple of 4, so
+// rows start 16-byte aligned).
+__host__ __device__ inline int dense_ld(int n) { return (n + 3) & ~3; }
+
 // Bytes of arena one problem needs (inputs, outputs, work), 256-aligned parts.
 struct ProbBytes {
   size_t in, out, work;

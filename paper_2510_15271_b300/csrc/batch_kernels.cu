@@ -644,7 +644,7 @@ __device__ void schur_items(const BProb& p) {
 // are added in order.  Diagonal blocks get U*; fixed cameras identity rows.
 template <typename T>
 __device__ void schur_blocks(const BProb& p, double mu) {
-  const int C = p.C, n = 6 * C;
+  const int C = p.C, ld = dense_ld(6 * C);
   const T* part = (const T*)p.part;
   T* S = (T*)p.S;
   for (int t = threadIdx.x; t < 6 * C * C; t += blockDim.x) {
@@ -674,8 +674,8 @@ __device__ void schur_blocks(const BProb& p, double mu) {
         }
       }
       const int gr = 6 * i1 + r, gc = 6 * i2 + c;
-      S[(int64_t)gr * n + gc] = val;
-      if (i2 > i1) S[(int64_t)gc * n + gr] = val;
+      S[(int64_t)gr * ld + gc] = val;
+      if (i2 > i1) S[(int64_t)gc * ld + gr] = val;
     }
   }
 }
@@ -757,6 +757,27 @@ __device__ void build_pairs(BProb& p, int* wsm, Smem& sm) {
 // Pitch of the shared-memory panel rows (16-byte aligned for vector loads).
 constexpr int kPanelPitch = kPanel + 4;
 
+// A[r][0..3] -= v[0..3] (16-byte aligned rows).
+__device__ __forceinline__ void sub4(float* a, const float v[4]) {
+  float4* q = reinterpret_cast<float4*>(a);
+  float4 x = *q;
+  x.x -= v[0];
+  x.y -= v[1];
+  x.z -= v[2];
+  x.w -= v[3];
+  *q = x;
+}
+__device__ __forceinline__ void sub4(double* a, const double v[4]) {
+  double2* q = reinterpret_cast<double2*>(a);
+  double2 x0 = q[0], x1 = q[1];
+  x0.x -= v[0];
+  x0.y -= v[1];
+  x1.x -= v[2];
+  x1.y -= v[3];
+  q[0] = x0;
+  q[1] = x1;
+}
+
 __device__ __forceinline__ void ld4(const float* p, float out[4]) {
   const float4 v = *reinterpret_cast<const float4*>(p);
   out[0] = v.x;
@@ -780,6 +801,7 @@ __device__ __forceinline__ void ld4(const double* p, double out[4]) {
 // triangle.  Returns false on a non-positive pivot.
 template <typename T>
 __device__ bool cholesky(T* A, int n, T* dyn, size_t dyn_bytes, Smem& sm) {
+  const int ld = dense_ld(n);  // row stride (a multiple of 4: vector row access)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NT = blockDim.x;
   constexpr int LD = kPanel + 1;
   constexpr int LP = kPanelPitch;  // panel row pitch: rows start 16-byte aligned
@@ -792,7 +814,7 @@ __device__ bool cholesky(T* A, int n, T* dyn, size_t dyn_bytes, Smem& sm) {
     const int pb = min(kPanel, n - jb);
     if (warp == 0) {
       if (lane < pb)
-        for (int c = 0; c <= lane; ++c) sd[lane * LD + c] = A[(int64_t)(jb + lane) * n + jb + c];
+        for (int c = 0; c <= lane; ++c) sd[lane * LD + c] = A[(int64_t)(jb + lane) * ld + jb + c];
       __syncwarp();
       for (int j = 0; j < pb; ++j) {
         if (lane == j) {
@@ -814,14 +836,14 @@ __device__ bool cholesky(T* A, int n, T* dyn, size_t dyn_bytes, Smem& sm) {
         __syncwarp();
       }
       if (lane < pb)
-        for (int c = 0; c <= lane; ++c) A[(int64_t)(jb + lane) * n + jb + c] = sd[lane * LD + c];
+        for (int c = 0; c <= lane; ++c) A[(int64_t)(jb + lane) * ld + jb + c] = sd[lane * LD + c];
     }
     __syncthreads();
     if (!sm.ok) return false;
     const int m0 = jb + pb, rem = n - m0;
     // panel rows below the diagonal block: x L_d^T = a
     for (int i = m0 + threadIdx.x; i < n; i += NT) {
-      T* a = A + (int64_t)i * n + jb;
+      T* a = A + (int64_t)i * ld + jb;
       T xr[kPanel];
 #pragma unroll
       for (int c = 0; c < kPanel; ++c) {
@@ -884,8 +906,8 @@ __device__ bool cholesky(T* A, int n, T* dyn, size_t dyn_bytes, Smem& sm) {
           const T* Ak[4];
 #pragma unroll
           for (int r = 0; r < 4; ++r) {
-            Ai[r] = A + (int64_t)min(m0 + 4 * ti + r, n - 1) * n + jb;
-            Ak[r] = A + (int64_t)min(m0 + 4 * tk + r, n - 1) * n + jb;
+            Ai[r] = A + (int64_t)min(m0 + 4 * ti + r, n - 1) * ld + jb;
+            Ak[r] = A + (int64_t)min(m0 + 4 * tk + r, n - 1) * ld + jb;
           }
           for (int m = 0; m < pb; ++m) {
             T a[4], b[4];
@@ -900,14 +922,12 @@ __device__ bool cholesky(T* A, int n, T* dyn, size_t dyn_bytes, Smem& sm) {
               for (int c = 0; c < 4; ++c) acc[r][c] += a[r] * b[c];
           }
         }
+        // four-wide row updates: the columns past the diagonal (or past n,
+        // in the padding) are never read by the factorisation or the solves
         const int i0 = m0 + 4 * ti, k0 = m0 + 4 * tk;
 #pragma unroll
         for (int r = 0; r < 4; ++r)
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const int i = i0 + r, k = k0 + c;
-            if (i < n && k <= i) A[(int64_t)i * n + k] -= acc[r][c];
-          }
+          if (i0 + r < n) sub4(A + (int64_t)(i0 + r) * ld + k0, acc[r]);
         tk += NT;
         while (tk > ti) {
           tk -= ti + 1;
@@ -925,12 +945,13 @@ __device__ bool cholesky(T* A, int n, T* dyn, size_t dyn_bytes, Smem& sm) {
 // one) and solves it with shuffles; all threads apply it to the other rows.
 template <typename T>
 __device__ void chol_solve(const T* A, int n, T* x) {
+  const int ld = dense_ld(n);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NT = blockDim.x;
   for (int jb = 0; jb < n; jb += 32) {
     const int pb = min(32, n - jb);
     if (warp == 0) {
       T L[32];
-      const T* row = A + (int64_t)(jb + min(lane, pb - 1)) * n + jb;
+      const T* row = A + (int64_t)(jb + min(lane, pb - 1)) * ld + jb;
 #pragma unroll
       for (int j = 0; j < 32; ++j) L[j] = j < pb ? row[j] : T(1);
       T yr = lane < pb ? x[jb + lane] : T(0);
@@ -946,7 +967,7 @@ __device__ void chol_solve(const T* A, int n, T* x) {
     }
     __syncthreads();
     for (int i = jb + pb + threadIdx.x; i < n; i += NT) {
-      const T* a = A + (int64_t)i * n + jb;
+      const T* a = A + (int64_t)i * ld + jb;
       T s = x[i];
       for (int m = 0; m < pb; ++m) s -= a[m] * x[jb + m];
       x[i] = s;
@@ -959,7 +980,7 @@ __device__ void chol_solve(const T* A, int n, T* x) {
       T L[32];  // L[j] = A[jb + j][jb + lane]
       const int cl = min(lane, pb - 1);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) L[j] = j < pb ? A[(int64_t)(jb + j) * n + jb + cl] : T(1);
+      for (int j = 0; j < 32; ++j) L[j] = j < pb ? A[(int64_t)(jb + j) * ld + jb + cl] : T(1);
       T xr = lane < pb ? x[jb + lane] : T(0);
 #pragma unroll
       for (int j = 31; j >= 0; --j) {
@@ -974,7 +995,7 @@ __device__ void chol_solve(const T* A, int n, T* x) {
     __syncthreads();
     for (int i = threadIdx.x; i < jb; i += NT) {
       T s = x[i];
-      for (int m = 0; m < pb; ++m) s -= A[(int64_t)(jb + m) * n + i] * x[jb + m];
+      for (int m = 0; m < pb; ++m) s -= A[(int64_t)(jb + m) * ld + i] * x[jb + m];
       x[i] = s;
     }
     __syncthreads();

@@ -129,16 +129,24 @@ def test_request_larger_than_arena_is_refused():
 
 
 def test_queue_full_is_busy():
+    """One slot and a waiting queue of one: while the big request runs, a
+    second request waits and the next submission is refused with BUSY."""
     big = _req(600, cams=(150, 160), pts=(20000, 25000))
     small = _req(601, cams=(10, 12), pts=(300, 400))
+    sa = ba._ProblemArrays.from_scene(small)
     with _server(big, slots=1, queue=1) as h:
-        first = ba.ba_submit(h, ba._ProblemArrays.from_scene(big))
-        time.sleep(0.05)  # the worker has admitted it and is running its ticks
-        second = ba.ba_submit(h, ba._ProblemArrays.from_scene(small))
-        with pytest.raises(ba.BAError, match="BUSY"):
-            ba.ba_submit(h, ba._ProblemArrays.from_scene(small))
-        assert _wait(h, first).status == ba.BA_OK
-        assert _wait(h, second).status == ba.BA_OK
+        ids = [ba.ba_submit(h, ba._ProblemArrays.from_scene(big))]
+        busy = False
+        for _ in range(8):  # submissions are microseconds apart; the big solve takes ms
+            try:
+                ids.append(ba.ba_submit(h, sa))
+            except ba.BAError as e:
+                assert e.status == ba.BA_ERR_BUSY
+                busy = True
+                break
+        assert busy
+        assert len(ids) <= 3
+        assert all(_wait(h, rid).status == ba.BA_OK for rid in ids)
 
 
 def test_poll_semantics_and_state_errors():
