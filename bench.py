@@ -28,6 +28,11 @@ import sys
 import tempfile
 import time
 
+# The served leg runs long requests in launches of their own, each on its own
+# stream; more hardware queues than the default 8 keep them from delaying the
+# ticks.  Read when the CUDA context is created, so it is set before torch.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -481,7 +486,8 @@ def run_served(args, local_rank):
     o.serve_slots = args.serve_slots
     o.serve_queue = 1 << 20
     o.serve_arena_bytes = args.serve_arena_gb << 30
-    lat, obs_done = [], 0
+    o.serve_split_ms = args.serve_split_ms
+    lat, cams, obs_done = [], [], 0
     with ba.ba_create_server(o) as h:
         for a in arrs[:8]:  # warm-up
             rid = ba.ba_submit(h, a)
@@ -499,21 +505,26 @@ def run_served(args, local_rank):
                         r = ba.ba_poll(h, rid)
                         if r is not None:
                             lat.append(r.latency_ms)
-                            obs_done += pending.pop(rid)
+                            j = pending.pop(rid)
+                            cams.append(pool[j].n_cams)
+                            obs_done += len(pool[j].obs_cam)
                 else:
                     time.sleep(min(ta - now, 2e-4))
             j = i % len(arrs)
-            pending[ba.ba_submit(h, arrs[j])] = len(pool[j].obs_cam)
+            pending[ba.ba_submit(h, arrs[j])] = j
         while pending:
             for rid in list(pending):
                 r = ba.ba_poll(h, rid)
                 if r is not None:
                     lat.append(r.latency_ms)
-                    obs_done += pending.pop(rid)
+                    j = pending.pop(rid)
+                    cams.append(pool[j].n_cams)
+                    obs_done += len(pool[j].obs_cam)
             time.sleep(2e-4)
         span = time.perf_counter() - t0
         st = ba.ba_kernel_stats(h)
-    lat = np.array(lat)
+    lat, cams = np.array(lat), np.array(cams)
+    big = cams > 96  # latency by window size
     return {
         "workload": f"Poisson arrivals at {args.serve_rate:g} req/s for {args.serve_seconds:g} s "
                     f"({len(arrivals)} requests replaying {len(pool)} seeded requests: cameras "
@@ -523,7 +534,15 @@ def run_served(args, local_rank):
         "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()),
         "throughput_req_s": lat.size / span, "value": obs_done * pool[0].lm_iters / span,
         "unit": UNIT, "ticks": int(st["serve_tick"][0]),
-        "gpu_busy_frac": st["serve_tick"][1] / 1e3 / span,
+        "tick_busy_frac": st["serve_tick"][1] / 1e3 / span,
+        "large_launches": int(st["serve_large"][0]),
+        "tick_mean_ctas": int(st["serve_tick_ctas"][0]),
+        "tick_mean_requests": round(float(st["serve_tick_ctas"][1]), 1),
+        "tick_mean_ms": round(st["serve_tick"][1] / max(st["serve_tick"][0], 1), 2),
+        "p50_ms_small": float(np.percentile(lat[~big], 50)) if (~big).any() else None,
+        "p99_ms_small": float(np.percentile(lat[~big], 99)) if (~big).any() else None,
+        "p50_ms_large": float(np.percentile(lat[big], 50)) if big.any() else None,
+        "p99_ms_large": float(np.percentile(lat[big], 99)) if big.any() else None,
         "mean_obs_per_request": float(np.mean([len(r.obs_cam) for r in pool])),
     }
 
@@ -601,6 +620,9 @@ def main():
     ap.add_argument("--serve-pool", type=int, default=96)
     ap.add_argument("--serve-slots", type=int, default=1024)
     ap.add_argument("--serve-arena-gb", type=int, default=32)
+    ap.add_argument("--serve-split-ms", type=float, default=10.0,
+                    help="served leg: requests estimated to take longer run in launches of "
+                         "their own beside the ticks (< 0: all in the ticks)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

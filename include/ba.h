@@ -108,6 +108,17 @@ typedef struct {
                                LM iteration per tick, and more while the tick
                                is younger than this (ms; 0: exactly one; < 0:
                                auto, 90 % of the previous tick, >= 2 ms)      */
+  double serve_split_ms;    /* serving handles: a request whose whole solve is
+                               estimated to take longer than this (ms, on one
+                               SM) runs to completion in a launch of its own
+                               beside the ticks instead of in them; < 0: every
+                               request in the ticks; 0: none.  Up to 16 such
+                               launches run at once, each on its own stream:
+                               give the process CUDA_DEVICE_MAX_CONNECTIONS
+                               >= 20 (read when the CUDA context is created)
+                               so that they do not share hardware queues with
+                               the ticks, which would hold a tick behind a
+                               long launch                                   */
 } ba_options;
 
 typedef struct {
@@ -148,7 +159,8 @@ typedef struct {
 /* Fill *opts with the defaults: FP64, AUTO solver, 10 iterations, no Huber,
  * PCG tol 1e-6 / 100, no refinement (5 steps, tol 1e-6 when enabled),
  * mu0 1e-4, dense_max_dim 1200, device 0, library stream, graphs on,
- * cudaMalloc, serving arena 0 (= 1/4 of free memory), 256 slots, 4096 queue. */
+ * cudaMalloc, serving arena 0 (= 1/4 of free memory), 256 slots, 4096 queue,
+ * tick 4 ms, split 10 ms. */
 void ba_options_default(ba_options* opts);
 
 /* Create a solver handle on opts->device.  *out receives the handle; the
@@ -192,8 +204,12 @@ ba_status ba_get_state(const ba_handle* h, double* cam_qt_out, double* pts_out, 
 ba_status ba_set_state(ba_handle* h, const double* cam_qt, const double* pts, int mem_kind);
 
 /* Kernel timings of the last solve, one entry per kernel kind: out[max]
- * receives up to max entries, *n the number written.  Errors: STATE (no
- * solve yet or profiling off), INVALID_ARG. */
+ * receives up to max entries, *n the number written.  A serving handle adds
+ * serve_tick (ticks, their summed milliseconds), serve_completed (requests),
+ * serve_large (launches of long requests, their summed milliseconds) and
+ * serve_tick_ctas (mean CTAs of a tick in launches, mean resident requests
+ * of a tick in total_ms).  Errors: STATE (no solve yet or profiling off),
+ * INVALID_ARG. */
 ba_status ba_kernel_stats(const ba_handle* h, ba_kernel_stat* out, int32_t max, int32_t* n);
 
 /* Reprojection cost F = 1/2 sum_k rho(||r_k||^2) of a given state, with no

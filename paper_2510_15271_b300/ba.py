@@ -46,7 +46,8 @@ class Options(Structure):
                 ("free_fn", FREE_FN), ("alloc_ctx", c_void_p), ("serve_arena_bytes", c_size_t),
                 ("serve_slots", c_int), ("serve_queue", c_int), ("profile", c_int),
                 ("pcg_variant", c_int), ("mu_min", c_double),
-                ("serve_tick_ms", c_double)]
+                ("serve_tick_ms", c_double),
+                ("serve_split_ms", c_double)]
 
 
 class Intrinsics(Structure):

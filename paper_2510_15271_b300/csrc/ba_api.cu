@@ -136,6 +136,7 @@ void ba_options_default(ba_options* o) {
   o->serve_queue = 4096;
   o->mu_min = -1.0;
   o->serve_tick_ms = 4.0;
+  o->serve_split_ms = 10.0;
 }
 
 static ba_status check_options(const ba_options* o, std::string& err) {
@@ -143,8 +144,8 @@ static ba_status check_options(const ba_options* o, std::string& err) {
     err = "precision must be BA_FP64 or BA_FP32";
     return BA_ERR_INVALID_ARG;
   }
-  if (!isfinite(o->serve_tick_ms)) {
-    err = "serve_tick_ms must be finite";
+  if (!isfinite(o->serve_tick_ms) || !isfinite(o->serve_split_ms)) {
+    err = "serve_tick_ms and serve_split_ms must be finite";
     return BA_ERR_INVALID_ARG;
   }
   if (o->pcg_variant < 0 || o->pcg_variant > 3) {

@@ -31,6 +31,7 @@ struct BProb {
   int C, P, N, iters;
   Intrinsics K;
   int phase, status, error, done_iters;
+  unsigned ticket;  // written to the launch's done flag when finished (served)
   // LM control (FP64)
   double mu, nu, F, F_new, dL, gain;
   int need_lin, step_ok, iter, n_accepted;
@@ -102,8 +103,9 @@ struct BatchRun {
                         // launch is younger than tick_budget_ns
   long long tick_budget_ns;
   double huber_delta, mu0, mu_min;
-  int32_t* done_list;       // optional: ids of problems finished by this launch
-  unsigned* done_count;     //   and their count (zeroed before the launch)
+  // optional, host-mapped: done_flags[id] = probs[id].ticket once problem id
+  // is finished and its outputs are written (system-scope release)
+  unsigned* done_flags;
   unsigned long long* phase_ns;  // optional: [kPhaseCount] CTA-ns per phase
 };
 

@@ -25,10 +25,14 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "batch.h"
 
 namespace ba {
 namespace {
+
+constexpr int kMaxDevices = 64;
 
 template <typename T>
 struct WS;
@@ -1220,9 +1224,17 @@ __device__ void lm_end(BProb& p, const BatchRun& a, Smem& sm) {
   __syncthreads();
 }
 
-// Record a finished problem in the launch's done list (when there is one).
+// Tell the host that problem id is finished (when the launch has done
+// flags).  Called after a CTA barrier that follows the problem's last writes;
+// the system-scope fence orders them before the flag for the host and for
+// copies the host then starts.
 __device__ void note_done(const BatchRun& a, int id) {
-  if (a.done_list && threadIdx.x == 0) a.done_list[atomicAdd(a.done_count, 1u)] = id;
+  if (a.done_flags && threadIdx.x == 0) {
+    const unsigned t = a.probs[id].ticket;
+    __threadfence_system();
+    asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(a.done_flags + id), "r"(t)
+                 : "memory");
+  }
 }
 
 template <typename T, int NT>
@@ -1285,10 +1297,33 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 1 : (NT >= 256 ? 2 : 3))) k_b
   }
 }
 
+// The kernel's dynamic shared memory limit is raised to the device's opt-in
+// maximum once per device, not before every launch: the server launches this
+// kernel while other launches of it run, and a launch's own size only has to
+// stay within the limit.
+template <typename T, int NT>
+cudaError_t allow_smem() {
+  static std::atomic<int> done[kMaxDevices];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  if (done[dev].load(std::memory_order_acquire)) return cudaSuccess;
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa{};
+  e = cudaFuncGetAttributes(&fa, k_batch<T, NT>);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_batch<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           optin - (int)fa.sharedSizeBytes);
+  if (e == cudaSuccess) done[dev].store(1, std::memory_order_release);
+  return e;
+}
+
 template <typename T, int NT>
 cudaError_t launch_t(int grid, size_t smem, const BatchRun& a, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(k_batch<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = allow_smem<T, NT>();
   if (e != cudaSuccess) return e;
   k_batch<T, NT><<<grid, NT, smem, s>>>(a, (int)smem);
   return cudaGetLastError();
@@ -1296,9 +1331,7 @@ cudaError_t launch_t(int grid, size_t smem, const BatchRun& a, cudaStream_t s) {
 
 template <typename T, int NT>
 int occupancy_t(size_t smem) {
-  if (cudaFuncSetAttribute(k_batch<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem) != cudaSuccess)
-    return 0;
+  if (allow_smem<T, NT>() != cudaSuccess) return 0;
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<T, NT>, NT, smem) != cudaSuccess)
     return 0;

@@ -3,6 +3,11 @@ import sys
 
 import pytest
 
+# the server's long-request launches each use a stream of their own; more
+# hardware queues than the default 8 keep them from delaying its ticks (read
+# when the CUDA context is created)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)

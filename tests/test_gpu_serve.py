@@ -189,3 +189,27 @@ def test_tick_budget_does_not_change_results():
             assert ticks >= 5  # one iteration per tick
     for a, b in zip(*out):
         assert np.array_equal(a.costs(), b.costs())
+
+
+def test_large_requests_run_beside_the_ticks():
+    """Requests above 96 cameras run in launches of their own beside the
+    small requests' ticks; every result still equals the batched solver's."""
+    small = [_req(1000 + i, cams=(10, 40), pts=(300, 2000)) for i in range(6)]
+    large = [_req(1100 + i, cams=(100, 130), pts=(3000, 6000)) for i in range(3)]
+    reqs = [x for pair in zip(small, large + [None] * 3) for x in pair if x is not None]
+    arrs = [ba._ProblemArrays.from_scene(s, want_state=True) for s in reqs]
+    with _server(reqs[0]) as h:
+        ids = []
+        for i, a in enumerate(arrs):
+            ids.append(ba.ba_submit(h, a))
+            if i % 4 == 3:
+                time.sleep(0.003)
+        served = [_wait(h, rid) for rid in ids]
+        stats = ba.ba_kernel_stats(h)
+    assert stats["serve_large"][0] >= 1
+    o = ba.options_for_scene(reqs[0], "fp32", max_lm_iters=5)
+    with ba.ba_create(o) as h:
+        batched = ba.ba_solve_batch(h, [ba._ProblemArrays.from_scene(s) for s in reqs])
+    for b, r in zip(batched, served):
+        assert r.status == ba.BA_OK
+        assert np.array_equal(b.costs(), r.costs())
