@@ -758,8 +758,16 @@ __device__ void build_pairs(BProb& p, int* wsm, Smem& sm) {
   __syncthreads();
 }
 
-// Pitch of the shared-memory panel rows (16-byte aligned for vector loads).
-constexpr int kPanelPitch = kPanel + 4;
+// Pitch of the shared-memory panel rows.  Within a row the 4-column groups
+// are XOR-swizzled by the row's 4-row tile index, so that the lanes of a warp
+// reading four consecutive columns of the same row of 8 consecutive tiles hit
+// 8 different 16-byte bank groups (with a plain pitch they would share 2).
+constexpr int kPanelPitch = kPanel;
+
+// Offset of column c (< kPanel) of panel row r within that row.
+__device__ __forceinline__ int pswz(int r, int c) {
+  return ((((c >> 2) ^ (r >> 2)) & 7) << 2) | (c & 3);
+}
 
 // A[r][0..3] -= v[0..3] (16-byte aligned rows).
 __device__ __forceinline__ void sub4(float* a, const float v[4]) {
@@ -861,7 +869,7 @@ __device__ bool cholesky(T* A, int n, T* dyn, size_t dyn_bytes, Smem& sm) {
 #pragma unroll
       for (int c = 0; c < kPanel; ++c) {
         if (c < pb) a[c] = xr[c];
-        if (panel_smem) ps[c] = c < pb ? xr[c] : T(0);
+        if (panel_smem) ps[pswz(i - m0, c)] = c < pb ? xr[c] : T(0);
       }
     }
     __syncthreads();
@@ -884,19 +892,24 @@ __device__ bool cholesky(T* A, int n, T* dyn, size_t dyn_bytes, Smem& sm) {
         if (panel_smem) {
           const T* Ai[4];
           const T* Ak[4];
+          int si[4], sk[4];  // the rows' swizzles
 #pragma unroll
           for (int r = 0; r < 4; ++r) {
-            Ai[r] = Ps + (int64_t)min(4 * ti + r, rem - 1) * LP;
-            Ak[r] = Ps + (int64_t)min(4 * tk + r, rem - 1) * LP;
+            const int ri = min(4 * ti + r, rem - 1), rk = min(4 * tk + r, rem - 1);
+            Ai[r] = Ps + (int64_t)ri * LP;
+            Ak[r] = Ps + (int64_t)rk * LP;
+            si[r] = (ri >> 2) & 7;
+            sk[r] = (rk >> 2) & 7;
           }
           // four consecutive panel columns per vector load (the panel's
           // columns beyond pb are zero-padded)
           for (int m = 0; m < pb; m += 4) {
             T a[4][4], b[4][4];
+            const int g = m >> 2;
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-              ld4(Ai[r] + m, a[r]);
-              ld4(Ak[r] + m, b[r]);
+              ld4(Ai[r] + ((g ^ si[r]) << 2), a[r]);
+              ld4(Ak[r] + ((g ^ sk[r]) << 2), b[r]);
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u)
