@@ -335,8 +335,9 @@ int batch_stats(ba_handle* h, ba_kernel_stat* out, int max) {
     // CTA-milliseconds per phase of the multi-problem kernel
     static const char* ph[kPhaseCount] = {"ph_idle",         "ph_setup",   "ph_lin",
                                           "ph_damp",         "ph_schur_y", "ph_schur_items",
-                                          "ph_schur_blocks", "ph_cholesky", "ph_solve",
-                                          "ph_trial",        "ph_cost",    "ph_gain"};
+                                          "ph_schur_blocks", "ph_cholesky", "ph_chol_diag",
+                                          "ph_chol_panel",   "ph_solve",   "ph_trial",
+                                          "ph_cost",         "ph_gain"};
     for (int i = 0; i < kPhaseCount && w < max; ++i, ++w) {
       memset(&out[w], 0, sizeof(out[w]));
       strncpy(out[w].name, ph[i], sizeof(out[w].name) - 1);

@@ -118,7 +118,9 @@ enum : int {
   kPhSchurY,     // Y = W V*^-1, b
   kPhSchurItems, // pair sums of the items
   kPhSchurBlocks,// S from the item sums
-  kPhCholesky,   // S = L L^T
+  kPhCholesky,   // S = L L^T: trailing updates
+  kPhCholDiag,   //   diagonal blocks
+  kPhCholPanel,  //   panel solves
   kPhSolve,      // triangular solves
   kPhTrial,      // back-substitution, retraction, model decrease
   kPhCost,       // cost passes (initial, trial, final) and outputs

@@ -764,11 +764,6 @@ __device__ void build_pairs(BProb& p, int* wsm, Smem& sm) {
 // 8 different 16-byte bank groups (with a plain pitch they would share 2).
 constexpr int kPanelPitch = kPanel;
 
-// Offset of column c (< kPanel) of panel row r within that row.
-__device__ __forceinline__ int pswz(int r, int c) {
-  return ((((c >> 2) ^ (r >> 2)) & 7) << 2) | (c & 3);
-}
-
 // A[r][0..3] -= v[0..3] (16-byte aligned rows).
 __device__ __forceinline__ void sub4(float* a, const float v[4]) {
   float4* q = reinterpret_cast<float4*>(a);
@@ -788,6 +783,14 @@ __device__ __forceinline__ void sub4(double* a, const double v[4]) {
   x1.y -= v[3];
   q[0] = x0;
   q[1] = x1;
+}
+
+__device__ __forceinline__ void st4(float* p, const float v[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double v[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
 }
 
 __device__ __forceinline__ void ld4(const float* p, float out[4]) {
@@ -812,7 +815,7 @@ __device__ __forceinline__ void ld4(const double* p, double out[4]) {
 // well when it fits) and updates 4 x 4 tiles of the trailing lower
 // triangle.  Returns false on a non-positive pivot.
 template <typename T>
-__device__ bool cholesky(T* A, int n, T* dyn, size_t dyn_bytes, Smem& sm) {
+__device__ bool cholesky(T* A, int n, T* dyn, size_t dyn_bytes, Smem& sm, PhaseClock& pc) {
   const int ld = dense_ld(n);  // row stride (a multiple of 4: vector row access)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NT = blockDim.x;
   constexpr int LD = kPanel + 1;
@@ -824,55 +827,85 @@ __device__ bool cholesky(T* A, int n, T* dyn, size_t dyn_bytes, Smem& sm) {
   __syncthreads();
   for (int jb = 0; jb < n; jb += kPanel) {
     const int pb = min(kPanel, n - jb);
-    if (warp == 0) {
-      if (lane < pb)
-        for (int c = 0; c <= lane; ++c) sd[lane * LD + c] = A[(int64_t)(jb + lane) * ld + jb + c];
-      __syncwarp();
-      for (int j = 0; j < pb; ++j) {
-        if (lane == j) {
-          T d = sd[j * LD + j];
-          if (!(d > T(0)) || !isfinite((double)d)) {
-            sm.ok = 0;
-            d = T(1);
-          }
-          sd[j * LD + j] = sqrt(d);
-        }
-        __syncwarp();
-        const T ljj = sd[j * LD + j];
-        if (lane > j && lane < pb) sd[lane * LD + j] /= ljj;
-        __syncwarp();
-        if (lane > j && lane < pb) {
-          const T lrj = sd[lane * LD + j];
-          for (int c = j + 1; c <= lane; ++c) sd[lane * LD + c] -= lrj * sd[c * LD + j];
-        }
-        __syncwarp();
-      }
-      if (lane < pb)
-        for (int c = 0; c <= lane; ++c) A[(int64_t)(jb + lane) * ld + jb + c] = sd[lane * LD + c];
+    // the diagonal block's lower triangle into shared memory (identity
+    // beyond pb), loaded by every thread
+    for (int e = threadIdx.x; e < kPanel * kPanel; e += NT) {
+      const int r = e / kPanel, c = e % kPanel;
+      sd[r * LD + c] = (r < pb && c <= r) ? A[(int64_t)(jb + r) * ld + jb + c] : T(c == r ? 1 : 0);
     }
     __syncthreads();
+    if (warp == 0) {
+      // lane r holds row r in registers; factored with shuffles
+      T L[kPanel];
+#pragma unroll
+      for (int c = 0; c < kPanel; ++c) L[c] = sd[lane * LD + c];
+      bool bad = false;
+#pragma unroll
+      for (int j = 0; j < kPanel; ++j) {
+        T piv = __shfl_sync(0xffffffffu, L[j], j);
+        if (!(piv > T(0)) || !isfinite((double)piv)) {
+          bad = true;
+          piv = T(1);
+        }
+        const T d = sqrt(piv), inv = T(1) / d;
+        if (lane == j) L[j] = d;
+        if (lane > j) L[j] *= inv;
+        const T lj = L[j];
+        // constant trip count (c > j folds once both loops are unrolled), so
+        // L stays in registers
+#pragma unroll
+        for (int c = 1; c < kPanel; ++c) {
+          if (c > j) {
+            const T lcj = __shfl_sync(0xffffffffu, lj, c);
+            if (lane >= c) L[c] -= lj * lcj;
+          }
+        }
+      }
+      if (__any_sync(0xffffffffu, bad) && lane == 0) sm.ok = 0;
+      // the factor, and the reciprocal of its diagonal in the padding column
+      T dg = T(1);
+#pragma unroll
+      for (int c = 0; c < kPanel; ++c) {
+        sd[lane * LD + c] = L[c];
+        if (c == lane) dg = L[c];
+      }
+      sd[lane * LD + kPanel] = T(1) / dg;
+      if (lane < pb)
+#pragma unroll
+        for (int c = 0; c < kPanel; ++c)
+          if (c <= lane) A[(int64_t)(jb + lane) * ld + jb + c] = L[c];
+    }
+    __syncthreads();
+    pc.mark(kPhCholDiag);
     if (!sm.ok) return false;
     const int m0 = jb + pb, rem = n - m0;
     // panel rows below the diagonal block: x L_d^T = a
     for (int i = m0 + threadIdx.x; i < n; i += NT) {
       T* a = A + (int64_t)i * ld + jb;
+      // (rows below the block exist only when it is a full panel: pb = 32;
+      // a row's panel part is 16-byte aligned)
       T xr[kPanel];
 #pragma unroll
-      for (int c = 0; c < kPanel; ++c) {
-        if (c < pb) {
-          T s = a[c];
-          for (int m = 0; m < c; ++m) s -= xr[m] * sd[c * LD + m];
-          xr[c] = s / sd[c * LD + c];
-        }
-      }
-      T* ps = Ps + (int64_t)(i - m0) * LP;
+      for (int g = 0; g < kPanel / 4; ++g) ld4(a + 4 * g, xr + 4 * g);
 #pragma unroll
       for (int c = 0; c < kPanel; ++c) {
-        if (c < pb) a[c] = xr[c];
-        if (panel_smem) ps[pswz(i - m0, c)] = c < pb ? xr[c] : T(0);
+        T s = xr[c];
+#pragma unroll
+        for (int m = 0; m < kPanel - 1; ++m)
+          if (m < c) s -= xr[m] * sd[c * LD + m];
+        xr[c] = s * sd[c * LD + kPanel];
+      }
+#pragma unroll
+      for (int g = 0; g < kPanel / 4; ++g) st4(a + 4 * g, xr + 4 * g);
+      if (panel_smem) {
+        T* ps = Ps + (int64_t)(i - m0) * LP;
+        const int sw = ((i - m0) >> 2) & 7;
+#pragma unroll
+        for (int g = 0; g < kPanel / 4; ++g) st4(ps + ((g ^ sw) << 2), xr + 4 * g);
       }
     }
     __syncthreads();
+    pc.mark(kPhCholPanel);
     if (rem > 0) {
       const int nt = (rem + 3) / 4;
       const int ntiles = nt * (nt + 1) / 2;
@@ -953,6 +986,7 @@ __device__ bool cholesky(T* A, int n, T* dyn, size_t dyn_bytes, Smem& sm) {
       }
     }
     __syncthreads();
+    pc.mark(kPhCholesky);
   }
   return true;
 }
@@ -1163,7 +1197,7 @@ __device__ void lm_iteration(BProb& p, const BatchRun& a, Smem& sm, T* dyn, size
   __syncthreads();
   pc.mark(kPhSchurBlocks);
   const int n = 6 * p.C;
-  const bool ok = cholesky<T>((T*)p.S, n, dyn, dyn_bytes, sm);
+  const bool ok = cholesky<T>((T*)p.S, n, dyn, dyn_bytes, sm, pc);
   pc.mark(kPhCholesky);
   double Fn = 0.0, hp = 0.0, hc = 0.0;
   if (ok) {
