@@ -764,27 +764,7 @@ __device__ void build_pairs(BProb& p, int* wsm, Smem& sm) {
 // 8 different 16-byte bank groups (with a plain pitch they would share 2).
 constexpr int kPanelPitch = kPanel;
 
-// A[r][0..3] -= v[0..3] (16-byte aligned rows).
-__device__ __forceinline__ void sub4(float* a, const float v[4]) {
-  float4* q = reinterpret_cast<float4*>(a);
-  float4 x = *q;
-  x.x -= v[0];
-  x.y -= v[1];
-  x.z -= v[2];
-  x.w -= v[3];
-  *q = x;
-}
-__device__ __forceinline__ void sub4(double* a, const double v[4]) {
-  double2* q = reinterpret_cast<double2*>(a);
-  double2 x0 = q[0], x1 = q[1];
-  x0.x -= v[0];
-  x0.y -= v[1];
-  x1.x -= v[2];
-  x1.y -= v[3];
-  q[0] = x0;
-  q[1] = x1;
-}
-
+// Four-wide row access (16-byte aligned rows).
 __device__ __forceinline__ void st4(float* p, const float v[4]) {
   *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
@@ -917,6 +897,13 @@ __device__ bool cholesky(T* A, int n, T* dyn, size_t dyn_bytes, Smem& sm, PhaseC
         ++ti;
       }
       for (int tt = threadIdx.x; tt < ntiles; tt += NT) {
+        const int i0 = m0 + 4 * ti, k0 = m0 + 4 * tk;
+        // the tile's current values, loaded before the products so that
+        // their latency overlaps them
+        T cur[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          if (i0 + r < n) ld4(A + (int64_t)(i0 + r) * ld + k0, cur[r]);
         T acc[4][4];
 #pragma unroll
         for (int r = 0; r < 4; ++r)
@@ -974,10 +961,13 @@ __device__ bool cholesky(T* A, int n, T* dyn, size_t dyn_bytes, Smem& sm, PhaseC
         }
         // four-wide row updates: the columns past the diagonal (or past n,
         // in the padding) are never read by the factorisation or the solves
-        const int i0 = m0 + 4 * ti, k0 = m0 + 4 * tk;
 #pragma unroll
         for (int r = 0; r < 4; ++r)
-          if (i0 + r < n) sub4(A + (int64_t)(i0 + r) * ld + k0, acc[r]);
+          if (i0 + r < n) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) cur[r][c] -= acc[r][c];
+            st4(A + (int64_t)(i0 + r) * ld + k0, cur[r]);
+          }
         tk += NT;
         while (tk > ti) {
           tk -= ti + 1;
