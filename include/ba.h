@@ -91,7 +91,9 @@ typedef struct {
   int serve_queue;          /* maximum requests waiting for admission        */
   int profile;              /* record per-kernel device times (CUDA events
                                between the kernels of the captured loop)      */
-  int pcg_variant;          /* PCG kernel.  0: auto (2); 1: standard PCG on
+  int pcg_variant;          /* PCG kernel.  0: auto (2 when the reduced
+                               system stays in shared memory and there is no
+                               refinement, else 1); 1: standard PCG on
                                a cooperative grid
                                (two grid barriers per iteration); 2:
                                pipelined PCG (one grid barrier per iteration,
@@ -239,6 +241,19 @@ ba_status ba_cost_noalloc(int device, void* cuda_stream, int32_t n_cams, int32_t
                           int64_t n_obs, const double* cam_qt, const double* pts,
                           const int32_t* obs_cam, const int32_t* obs_pt, const double* obs_uv,
                           const ba_intrinsics* K, double huber_delta, double* cost_out);
+
+/* Self-test of the bounded grid barrier the PCG kernels wait at: launches
+ * `blocks` co-resident CTAs (1..64) that meet at one grid barrier expecting
+ * `expected` arrivals, each wait giving up after limit_ms (0 < limit_ms <=
+ * 1000).  With expected > blocks the wait runs out: every CTA records the
+ * time-out in the error word and returns, as the PCG kernels do, and the
+ * device stays usable.  *timed_out receives 1 if the barrier timed out, 0 if
+ * it completed; *waited_ms (may be NULL) the kernel's duration.  Blocks
+ * until done; uses the legacy default stream of `device`, and restores the
+ * caller's current device.  Errors (message in ba_last_error(NULL)):
+ * INVALID_ARG, CUDA. */
+ba_status ba_selftest_barrier(int32_t device, int32_t blocks, int32_t expected, double limit_ms,
+                              int32_t* timed_out, double* waited_ms);
 
 /* Release the handle and everything it owns.  NULL is ignored. */
 void ba_destroy(ba_handle* h);

@@ -128,6 +128,8 @@ _SIGNATURES = {
     "ba_cost_noalloc": (c_int, [c_int, c_void_p, c_int32, c_int32, c_int64, c_void_p, c_void_p,
                                 c_void_p, c_void_p, c_void_p, POINTER(Intrinsics), c_double,
                                 c_void_p]),
+    "ba_selftest_barrier": (c_int, [c_int32, c_int32, c_int32, c_double, POINTER(c_int32),
+                                    POINTER(c_double)]),
 }
 
 EXPORTS = tuple(_SIGNATURES)
@@ -391,6 +393,17 @@ def ba_poll(h: Handle, req_id: int):
 
 
 # --------------------------------------------------------------------------- convenience
+
+def ba_selftest_barrier(device: int = 0, blocks: int = 8, expected: int = 8,
+                        limit_ms: float = 50.0):
+    """(timed_out, waited_ms) of one grid barrier of `blocks` CTAs expecting
+    `expected` arrivals (ba_selftest_barrier)."""
+    t = c_int32()
+    w = c_double()
+    _check(lib().ba_selftest_barrier(device, blocks, expected, limit_ms, ctypes.byref(t),
+                                     ctypes.byref(w)))
+    return bool(t.value), w.value
+
 
 def options_for_scene(scene, precision: Optional[str] = None, **kw) -> Options:
     """Solver options from a scene's solve settings."""

@@ -27,6 +27,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <string>
 #include <vector>
 
 #include "lm.h"
@@ -40,24 +41,6 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
-}
-
-__device__ __forceinline__ unsigned atom_add_relaxed_u32(unsigned* p, unsigned v) {
-  unsigned old;
-  asm volatile("atom.relaxed.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v)
-               : "memory");
-  return old;
-}
-
-__device__ __forceinline__ unsigned atom_add_release_u32(unsigned* p, unsigned v) {
-  unsigned old;
-  asm volatile("atom.release.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v)
-               : "memory");
-  return old;
-}
-
-__device__ __forceinline__ void st_relaxed_u32(unsigned* p, unsigned v) {
-  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 __device__ __forceinline__ void fence_acq_rel_gpu() {
@@ -74,33 +57,40 @@ __device__ __forceinline__ int ld_err(const int* err) {
   return *(volatile const int*)err;
 }
 
+__device__ __forceinline__ void red_add_release_u32(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid barriers this CTA has entered in the current launch (thread 0 only;
+// each kernel that uses grid_barrier zeroes it first).
+__shared__ unsigned s_bar_epoch;
+
 // Grid-wide barrier over co-resident CTAs (cooperative launch).  bar[0]
-// counts arrivals, bar[1] is the generation.  The CTA's writes are released
-// by __syncthreads + the release arrival and acquired by the acquire-load
-// that sees the new generation (the last arriver acquires through its fence).
-// A wait that exceeds kBarrierLimitNs (or sees another CTA's error) sets
+// counts the arrivals of the whole launch (zeroed before it), so barrier e
+// is complete once the count reaches e * nblocks: one fire-and-forget
+// release add per CTA and acquire polls, no reset and no generation word.
+// The CTA's writes are released by __syncthreads + its release arrival; the
+// acquire load that sees the full count synchronises with every arrival
+// (each heads a release sequence that the later additions continue).  A wait
+// that exceeds kBarrierLimitNs (or sees another CTA's error) sets
 // kErrBarrierTimeout in *err and returns; callers stop at their next check.
-__device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned nblocks, int* err) {
+__device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned nblocks, int* err,
+                                             unsigned long long limit_ns = kBarrierLimitNs) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned g = ld_acquire_u32(bar + 1);
-    const unsigned prev = atom_add_release_u32(bar, 1u);
-    if (prev == nblocks - 1) {
-      st_relaxed_u32(bar, 0u);
-      fence_acq_rel_gpu();
-      atom_add_relaxed_u32(bar + 1, 1u);
-    } else {
-      const unsigned long long t0 = global_ns();
-      while (ld_acquire_u32(bar + 1) == g) {
+    const unsigned target = (++s_bar_epoch) * nblocks;
+    red_add_release_u32(bar, 1u);
+    const unsigned long long t0 = global_ns();
+    for (unsigned n = 1; (int)(ld_acquire_u32(bar) - target) < 0; ++n) {
+      if ((n & 63u) == 0) {
         if (ld_err(err) != 0) break;  // another CTA already gave up
-        if (global_ns() - t0 > kBarrierLimitNs) {
+        if (global_ns() - t0 > limit_ns) {
           atomicOr(err, kErrBarrierTimeout);
           break;
         }
-        __nanosleep(20);
       }
-      fence_acq_rel_gpu();
     }
+    fence_acq_rel_gpu();
   }
   __syncthreads();
 }
@@ -575,6 +565,7 @@ __global__ void __launch_bounds__(NT) k_pcg(DevProblem d, double tol, int max_it
                                             int refine_max, double refine_tol, int R, int maxnnz,
                                             int maxu) {
   extern __shared__ __align__(16) unsigned char smem[];
+  if (threadIdx.x == 0) s_bar_epoch = 0;
   int* err = &d.lm->error;
   const unsigned nb = gridDim.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -939,4 +930,63 @@ void launch_linear_solve(const DevProblem& d, const SolveConfig& cfg, cudaStream
   else linear_solve_t<double>(d, cfg, s);
 }
 
+// One grid barrier expecting `expected` arrivals from the launch's CTAs,
+// with the given wait limit: the self-test of the barrier's time-out.
+__global__ void k_barrier_selftest(unsigned* bar, unsigned expected, int* err,
+                                   unsigned long long limit_ns) {
+  if (threadIdx.x == 0) s_bar_epoch = 0;
+  grid_barrier(bar, expected, err, limit_ns);
+}
+
+extern thread_local std::string g_create_error;
+
 }  // namespace ba
+
+extern "C" ba_status ba_selftest_barrier(int32_t device, int32_t blocks, int32_t expected,
+                                         double limit_ms, int32_t* timed_out, double* waited_ms) {
+  using namespace ba;
+  if (!timed_out || blocks < 1 || blocks > 64 || expected < 1 || !(limit_ms > 0.0) ||
+      limit_ms > 1000.0) {
+    g_create_error = "ba_selftest_barrier: blocks in [1, 64], expected >= 1, limit_ms in (0, 1000]";
+    return BA_ERR_INVALID_ARG;
+  }
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaError_t e = cudaSetDevice(device);
+  unsigned* bar = nullptr;
+  int* err = nullptr;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  float ms = 0.f;
+  int herr = 0;
+  if (e == cudaSuccess) e = cudaMalloc(&bar, 64);
+  if (e == cudaSuccess) e = cudaMalloc(&err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(bar, 0, 64);
+  if (e == cudaSuccess) e = cudaMemset(err, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  if (e == cudaSuccess) {
+    unsigned ex = (unsigned)expected;
+    unsigned long long lim = (unsigned long long)(limit_ms * 1e6);
+    void* args[] = {&bar, &ex, &err, &lim};
+    cudaEventRecord(t0, 0);
+    // co-resident CTAs (a cooperative launch checks that they fit)
+    e = cudaLaunchCooperativeKernel((const void*)k_barrier_selftest, dim3(blocks), dim3(32), args,
+                                    0, 0);
+    cudaEventRecord(t1, 0);
+  }
+  if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+  if (e == cudaSuccess) e = cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  if (bar) cudaFree(bar);
+  if (err) cudaFree(err);
+  cudaSetDevice(prev);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("ba_selftest_barrier: ") + cudaGetErrorString(e);
+    return BA_ERR_CUDA;
+  }
+  *timed_out = (herr & kErrBarrierTimeout) ? 1 : 0;
+  if (waited_ms) *waited_ms = ms;
+  return BA_OK;
+}
