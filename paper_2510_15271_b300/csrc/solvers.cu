@@ -150,10 +150,59 @@ __device__ __forceinline__ void stage(const RowSet<T>& rs, const T* a, const T* 
   __syncthreads();
 }
 
+// The 36 elements of a 6x6 block of S in global memory (144 B for FP32,
+// 16-byte aligned) in vector loads: a lane's block is 144 or 288 B away from
+// its neighbour's, so each load instruction touches one line per lane and
+// wide loads cut the instructions and L1 wavefronts four- or twofold.
+__device__ __forceinline__ void ld_blk36(const float* B, float out[36]) {
+  const float4* q = reinterpret_cast<const float4*>(B);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const float4 v = q[i];
+    out[4 * i] = v.x;
+    out[4 * i + 1] = v.y;
+    out[4 * i + 2] = v.z;
+    out[4 * i + 3] = v.w;
+  }
+}
+__device__ __forceinline__ void ld_blk36(const double* B, double out[36]) {
+  const double2* q = reinterpret_cast<const double2*>(B);
+#pragma unroll
+  for (int i = 0; i < 18; ++i) {
+    const double2 v = q[i];
+    out[2 * i] = v.x;
+    out[2 * i + 1] = v.y;
+  }
+}
+
 // Warp computes out = S_i. v for block row i, v(c) supplied by vget (c is
 // the block's column index of rs.col); the result is in every lane.
 template <typename T, typename Get>
 __device__ __forceinline__ void row_spmv(const RowSet<T>& rs, int i, Get vget, T out[6]) {
+  if (!rs.local) {
+    // S in global memory: one block per lane per round, vector loads
+    const int lane = threadIdx.x & 31;
+    T acc[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    const int be = rs.re(i);
+    for (int b = rs.rb(i) + lane; b < be; b += 32) {
+      const int c = rs.col[b];
+      T blk[36];
+      ld_blk36(rs.blk(b), blk);
+      T v[6];
+#pragma unroll
+      for (int e = 0; e < 6; ++e) v[e] = vget(6 * c + e);
+#pragma unroll
+      for (int a = 0; a < 6; ++a) {
+        T s = acc[a];
+#pragma unroll
+        for (int e = 0; e < 6; ++e) s += blk[6 * a + e] * v[e];
+        acc[a] = s;
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 6; ++a) out[a] = warp_sum(acc[a]);
+    return;
+  }
   const int lane = threadIdx.x & 31;
   T acc[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
   const int be = rs.re(i);
