@@ -180,12 +180,24 @@ __device__ __forceinline__ void ld_blk36(const double* B, double out[36]) {
 template <typename T, typename Get>
 __device__ __forceinline__ void row_spmv(const RowSet<T>& rs, int i, Get vget, T out[6]) {
   if (!rs.local) {
-    // S in global memory: one block per lane per round, vector loads
+    // S in global memory: one block per lane per round, vector loads; the
+    // next round's block lines are prefetched into L1 and its column index
+    // loaded a round early, so a round costs one memory round trip
     const int lane = threadIdx.x & 31;
     T acc[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
     const int be = rs.re(i);
-    for (int b = rs.rb(i) + lane; b < be; b += 32) {
-      const int c = rs.col[b];
+    int b = rs.rb(i) + lane;
+    int cn = b < be ? rs.col[b] : 0;
+    for (; b < be; b += 32) {
+      const int c = cn;
+      const int bn = b + 32;
+      if (bn < be) {
+        cn = rs.col[bn];
+        const char* q = reinterpret_cast<const char*>(rs.blk(bn));
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(q));
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(q + 36 * sizeof(T) - 1));
+        if (sizeof(T) == 8) asm volatile("prefetch.global.L1 [%0];" ::"l"(q + 128));
+      }
       T blk[36];
       ld_blk36(rs.blk(b), blk);
       T v[6];
@@ -889,7 +901,10 @@ bool plan_pcg(int precision, int device, const std::vector<int32_t>& rowptr,
   int G = std::max(1, std::min(gmax, (C + kPcgWarps - 1) / kPcgWarps));
   int R = 1, rw = 1;
   // the cooperative grid must be co-resident with the variant it launches
-  // (more rows per warp: more registers, fewer CTAs per SM)
+  // (more rows per warp: more registers, fewer CTAs per SM); the most CTAs
+  // that fit, even where a CTA's warps then get 1 or 2 rows (measured faster
+  // on the city workload than rows-per-CTA a multiple of the warp count,
+  // which halves the CTAs)
   for (int attempt = 0;; ++attempt) {
     R = (C + G - 1) / G;
     G = (C + R - 1) / R;
@@ -900,8 +915,7 @@ bool plan_pcg(int precision, int device, const std::vector<int32_t>& rowptr,
     if (occ * sms >= G) break;
     if (occ < 1 || attempt >= 8) return false;
     G = occ * sms;
-  }
-  // per-CTA column lists
+  }  // per-CTA column lists
   plan.ucol.clear();
   plan.uptr.assign(G + 1, 0);
   plan.lcol.assign(col.size(), 0);
