@@ -266,20 +266,20 @@ __device__ __forceinline__ T pick6(const T v[6], int lane) {
 // Sum over the CTA of FP64 values held by lanes 0..5 of each warp (every
 // caller accumulates its dot products in the lanes that own the 6 elements
 // of a block row; the other lanes hold zeros) into slot[blockIdx.x * stride
-// + k].  Lane 0 adds its warp's six values: FP64 is slow on this part, so
-// no 32-lane butterfly.
+// + k].  Only the six lanes are summed (three shuffle levels): FP64 is slow
+// on this part, so no 32-lane butterfly.
 template <int NT, int NV>
 __device__ __forceinline__ void cta_partials(double (&v)[NV], double* red, double* slot,
                                              int stride) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // lanes 0..5 hold the terms, the others zeros: a three-level tree
+  // (0+4, 1+5, 2, 3; then +2; then +1) puts the sum in lane 0
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
     double s = v[k];
-#pragma unroll
-    for (int l = 1; l < 6; ++l) {
-      const double o = __shfl_sync(0xffffffffu, v[k], l);
-      if (lane == 0) s += o;
-    }
+    s += __shfl_down_sync(0xffffffffu, s, 4);
+    s += __shfl_down_sync(0xffffffffu, s, 2);
+    s += __shfl_down_sync(0xffffffffu, s, 1);
     v[k] = s;
   }
   if (lane == 0) {
@@ -305,7 +305,20 @@ __device__ __forceinline__ void all_partials(const double* slot, int stride, int
     double acc[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) acc[k] = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += 32)
+    // the first four of a lane's CTAs loaded together (one L2 round trip
+    // for up to 128 CTAs), then added in CTA order
+    double first[4][NV];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int b = threadIdx.x + 32 * j;
+#pragma unroll
+      for (int k = 0; k < NV; ++k) first[j][k] = b < nblocks ? __ldcg(slot + b * stride + k) : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) acc[k] += first[j][k];
+    for (int b = threadIdx.x + 128; b < nblocks; b += 32)
 #pragma unroll
       for (int k = 0; k < NV; ++k) acc[k] += __ldcg(slot + b * stride + k);
 #pragma unroll
@@ -369,10 +382,12 @@ __device__ int pcg_solve(const DevProblem& d, const RowSet<T>& rs, const T* __re
   __shared__ int s_go, s_stop;
   double rz = tot[0], rr = tot[1];
   const double bnorm = sqrt(rr);
+  // ||r|| > tol ||b|| tested on squares: no square root per iteration
+  const double thr2 = (tol * bnorm) * (tol * bnorm);
   int k = 0;
   if (threadIdx.x == 0) {
     s_bt = T(0);
-    s_go = (max_iters > 0 && sqrt(rr) > tol * bnorm && !ld_err(err)) ? 1 : 0;
+    s_go = (max_iters > 0 && rr > thr2 && !ld_err(err)) ? 1 : 0;
   }
   __syncthreads();
   while (s_go) {
@@ -436,13 +451,15 @@ __device__ int pcg_solve(const DevProblem& d, const RowSet<T>& rs, const T* __re
     }
     cta_partials<NT, 2>(l2, red, partB, 2);
     grid_barrier(d.barrier, nb, err);
+    // the error word is read alongside the partial sums (one round trip)
+    const int e_now = threadIdx.x == 0 ? ld_err(err) : 0;
     all_partials<2>(partB, 2, nb, tot);
     ++k;
     if (threadIdx.x == 0) {
       s_bt = (T)(tot[0] / rz);
       rz = tot[0];
       rr = tot[1];
-      s_go = (k < max_iters && sqrt(rr) > tol * bnorm && !ld_err(err)) ? 1 : 0;
+      s_go = (k < max_iters && rr > thr2 && !e_now) ? 1 : 0;
     }
     __syncthreads();
   }
@@ -512,7 +529,9 @@ __device__ int pcg_solve_pipelined(const DevProblem& d, const RowSet<T>& rs,
   // scalars: thread 0 (FP64 is slow on this part), broadcast
   __shared__ double s_al, s_bt;
   __shared__ int s_go;
-  double bnorm = -1.0, gamma_prev = 0.0, alpha_prev = 0.0, rr = 0.0;
+  // 1/gamma and 1/alpha of the previous iteration are kept, so an
+  // iteration divides twice; ||r|| > tol ||b|| is tested on squares
+  double bnorm = -1.0, thr2 = 0.0, inv_gamma_prev = 0.0, inv_alpha_prev = 0.0, rr = 0.0;
   int k = 0;
   for (;;) {
     // local: gamma = (r,u), delta = (w,u), (r,r); m = M w (published)
@@ -540,28 +559,33 @@ __device__ int pcg_solve_pipelined(const DevProblem& d, const RowSet<T>& rs,
     // the next product's input (m of the listed columns) and the partial sums
     // are read together (all_partials ends with a CTA barrier)
     if (STAGED) stage_nosync<T, NT>(rs, mo, (const T*)nullptr, T(0));
+    // the error word is read alongside the partial sums (one round trip)
+    const int e_now = threadIdx.x == 0 ? ld_err(err) : 0;
     double tot[3];
     all_partials<3>(partA, 3, nb, tot);
     if (threadIdx.x == 0) {
       const double gamma = tot[0], delta = tot[1];
       rr = tot[2];
-      if (bnorm < 0.0) bnorm = sqrt(rr);
-      int go = (k < max_iters && sqrt(rr) > tol * bnorm && !ld_err(err)) ? 1 : 0;
+      if (bnorm < 0.0) {
+        bnorm = sqrt(rr);
+        thr2 = (tol * bnorm) * (tol * bnorm);
+      }
+      int go = (k < max_iters && rr > thr2 && !e_now) ? 1 : 0;
       double beta = 0.0, alpha = 0.0;
       if (go) {
-        if (k == 0) {
-          alpha = gamma / delta;
-        } else {
-          beta = gamma / gamma_prev;
-          alpha = gamma / (delta - beta * gamma / alpha_prev);
-        }
+        // alpha = gamma / (delta - beta gamma / alpha_prev), beta = gamma /
+        // gamma_prev (beta = 0 at k = 0); 1/alpha = denominator / gamma
+        const double inv_gamma = 1.0 / gamma;
+        if (k > 0) beta = gamma * inv_gamma_prev;
+        const double den = k > 0 ? delta - beta * gamma * inv_alpha_prev : delta;
+        alpha = gamma / den;
+        inv_gamma_prev = inv_gamma;
+        inv_alpha_prev = den * inv_gamma;
         if (!(alpha > 0.0) || !isfinite(alpha)) go = 0;  // curvature not positive
       }
       s_go = go;
       s_al = alpha;
       s_bt = beta;
-      gamma_prev = gamma;
-      alpha_prev = alpha;
     }
     __syncthreads();
     if (!s_go) break;
