@@ -118,6 +118,7 @@ struct RowSet {
   const int32_t* ucol;  // SMEM: global camera of each listed column
   const int32_t* own;   // SMEM: list index of each owned row's own column
   T* sv;                // SMEM: staged vector
+  const double* Minv64;  // SMEM: the owned rows' inverse diagonal blocks in FP64
   int nu;               // SMEM: listed columns
   int sstride;
   int r0, r1;
@@ -131,6 +132,10 @@ struct RowSet {
     return Minv + 36 * (int64_t)(local ? i - r0 : i);
   }
   __device__ __forceinline__ int gcol(int b) const { return local ? ucol[col[b]] : col[b]; }
+  // element e of the inverse diagonal block of row i, in FP64
+  __device__ __forceinline__ double minv64(int i, int e) const {
+    return local ? Minv64[36 * (i - r0) + e] : (double)Minv[36 * (int64_t)i + e];
+  }
 };
 
 // sv = a + beta b over the listed columns (b may be null); coalesced: the 6
@@ -507,10 +512,9 @@ __device__ int pcg_solve_pipelined(const DevProblem& d, const RowSet<T>& rs,
     if (i >= rs.r1) continue;
     const double ri = lane < 6 ? (double)rhs[6 * i + el] : 0.0;
     rr_[m] = ri;
-    const T* M = rs.minv(i);
     double ui = 0.0;
 #pragma unroll
-    for (int f = 0; f < 6; ++f) ui += (double)M[6 * el + f] * __shfl_sync(0xffffffffu, ri, f);
+    for (int f = 0; f < 6; ++f) ui += rs.minv64(i, 6 * el + f) * __shfl_sync(0xffffffffu, ri, f);
     ur[m] = ui;
     if (lane < 6) ub[6 * i + el] = (T)ui;
   }
@@ -541,11 +545,10 @@ __device__ int pcg_solve_pipelined(const DevProblem& d, const RowSet<T>& rs,
     for (int m = 0; m < RW; ++m) {
       const int i = rs.r0 + warp + m * NW;
       if (i >= rs.r1) continue;
-      const T* M = rs.minv(i);
       const double wi = lane < 6 ? wr[m] : 0.0;
       double mi = 0.0;
 #pragma unroll
-      for (int f = 0; f < 6; ++f) mi += (double)M[6 * el + f] * __shfl_sync(0xffffffffu, wi, f);
+      for (int f = 0; f < 6; ++f) mi += rs.minv64(i, 6 * el + f) * __shfl_sync(0xffffffffu, wi, f);
       mr[m] = mi;
       if (lane < 6) {
         mo[6 * i + el] = (T)mi;
@@ -642,6 +645,8 @@ __host__ __device__ inline size_t pcg_smem_bytes(int maxnnz, int R, int maxu) {
   o += (size_t)(R + 1) * sizeof(int32_t);
   o += (size_t)maxu * sizeof(int32_t);
   o += (size_t)R * sizeof(int32_t);
+  o = (o + 7) & ~size_t(7);
+  o += (size_t)R * 36 * sizeof(double);
   return o + 16;
 }
 
@@ -674,6 +679,9 @@ __global__ void __launch_bounds__(NT) k_pcg(DevProblem d, double tol, int max_it
     int32_t* sucol = reinterpret_cast<int32_t*>(smem + o);
     o += (size_t)maxu * sizeof(int32_t);
     int32_t* sown = reinterpret_cast<int32_t*>(smem + o);
+    o += (size_t)R * sizeof(int32_t);
+    o = (o + 7) & ~size_t(7);
+    double* sM64 = reinterpret_cast<double*>(smem + o);
     const int nb0 = d.s_rowptr[r0];
     const int n = d.s_rowptr[r1] - nb0;
     const int u0 = d.pcg_uptr[blockIdx.x];
@@ -685,12 +693,16 @@ __global__ void __launch_bounds__(NT) k_pcg(DevProblem d, double tol, int max_it
     for (int e = threadIdx.x; e < nu; e += NT) sucol[e] = d.pcg_ucol[u0 + e];
     for (int e = threadIdx.x; e < r1 - r0; e += NT) sown[e] = d.pcg_lown[r0 + e];
     const T* Mg = (const T*)d.Minv + 36 * (int64_t)r0;
-    for (int e = threadIdx.x; e < (r1 - r0) * 36; e += NT) sM[e] = Mg[e];
+    for (int e = threadIdx.x; e < (r1 - r0) * 36; e += NT) {
+      sM[e] = Mg[e];
+      sM64[e] = (double)Mg[e];
+    }
     __syncthreads();
     rs.S = sS;
     rs.col = scol;
     rs.rowptr = srow;
     rs.Minv = sM;
+    rs.Minv64 = sM64;
     rs.ucol = sucol;
     rs.own = sown;
     rs.sv = sv;
@@ -702,6 +714,7 @@ __global__ void __launch_bounds__(NT) k_pcg(DevProblem d, double tol, int max_it
     rs.col = d.s_col;
     rs.rowptr = d.s_rowptr;
     rs.Minv = (const T*)d.Minv;
+    rs.Minv64 = nullptr;
     rs.ucol = nullptr;
     rs.own = nullptr;
     rs.sv = nullptr;
