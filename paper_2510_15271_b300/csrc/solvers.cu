@@ -292,10 +292,15 @@ __device__ __forceinline__ void cta_partials(double (&v)[NV], double* red, doubl
     for (int k = 0; k < NV; ++k) red[warp * NV + k] = v[k];
   }
   __syncthreads();
-  if (threadIdx.x < NV) {
-    double s = 0.0;
-    for (int w = 0; w < NT / 32; ++w) s += red[w * NV + threadIdx.x];
-    slot[blockIdx.x * stride + threadIdx.x] = s;
+  // the warps' sums: warp 0, NW lanes per value, a shuffle tree
+  constexpr int NW = NT / 32;
+  static_assert((NW & (NW - 1)) == 0 && NW * NV <= 32, "warp count a power of two");
+  if (warp == 0) {
+    const int k = lane / NW, w = lane % NW;
+    double s = k < NV ? red[w * NV + k] : 0.0;
+#pragma unroll
+    for (int o = NW / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (k < NV && w == 0) slot[blockIdx.x * stride + k] = s;
   }
 }
 
