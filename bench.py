@@ -412,7 +412,7 @@ def run_batched(args, local_rank):
                 sched = ba.ba_tune_batch(h, arrs) if tune else ba.ba_get_batch_schedule(h)
             for _ in range(max(1, args.warmup)):
                 ba.ba_solve_batch(h, arrs)
-            call, kern, h2d, d2h = [], [], [], []
+            call, kern, h2d, d2h, host = [], [], [], [], {}
             for _ in range(steps):
                 t = time.perf_counter()
                 res = ba.ba_solve_batch(h, arrs)
@@ -421,9 +421,13 @@ def run_batched(args, local_rank):
                 kern.append(st["batch_kernel"][1] / 1e3)
                 h2d.append(st["batch_h2d"][1] / 1e3)
                 d2h.append(st["batch_d2h"][1] / 1e3)
+                for k in ("prepare", "pack", "run", "finish"):
+                    host.setdefault(k, []).append(st["batch_host_" + k][1])
+        timed.host_ms = {k: round(float(np.mean(v)), 2) for k, v in host.items()}
         return res, sched, call, kern, h2d, d2h, [(a.q_out.copy(), a.p_out.copy()) for a in arrs]
 
     res32, sched, call, kern, h2d, d2h, st32 = timed("fp32", args.steps, True)
+    host32 = dict(timed.host_ms)
     # one more (untimed) solve with per-phase clocks, for the phase split
     o = ba.options_for_scene(ws[0], "fp32", device=local_rank, profile=1)
     with ba.ba_create(o) as h:
@@ -461,7 +465,8 @@ def run_batched(args, local_rank):
         "n_pts": int(sum(w.n_pts for w in ws)), "lm_iters": iters,
         "value": work / mean(kern), "unit": UNIT, "ms_per_step": 1e3 * mean(kern),
         "e2e": {"value": work / mean(call), "unit": UNIT, "ms_per_step": 1e3 * mean(call),
-                "h2d_ms": 1e3 * mean(h2d), "d2h_ms": 1e3 * mean(d2h)},
+                "h2d_ms": 1e3 * mean(h2d), "d2h_ms": 1e3 * mean(d2h),
+                "host_ms": host32},
         "schedule": {"threads": sched[0], "ctas_per_sm": sched[1]},
         "phase_cta_ms": ph,
         "fp64_batched": {"value": work / mean(kern64), "ms_per_step": 1e3 * mean(kern64)},

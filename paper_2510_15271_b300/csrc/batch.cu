@@ -8,6 +8,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <memory>
 #include <numeric>
 #include <string>
 #include <thread>
@@ -145,6 +148,19 @@ int64_t count_pairs(const ba_problem& q) {
   return s;
 }
 
+// The same count from a point index array (used on the packed copy, which
+// is in cache right after packing).
+int64_t count_pairs_raw(const int32_t* pt, int64_t N, int P) {
+  std::vector<int32_t> L((size_t)P, 0);
+  for (int64_t k = 0; k < N; ++k) {
+    const int j = pt[k];
+    if (j >= 0 && j < P) ++L[j];
+  }
+  int64_t s = 0;
+  for (int32_t l : L) s += (int64_t)l * (l + 1) / 2;
+  return s;
+}
+
 ProbBytes prob_bytes(int precision, int C, int P, int64_t N, int64_t npairs) {
   ProbBytes b;
   Carve ci(nullptr), co(nullptr), cw(nullptr);
@@ -264,7 +280,9 @@ struct ba_batch {
   int threads = 256;
   int ctas_per_sm = 0;  // 0: as many as fit
   int order = 0;        // 0 largest first, 1 as given
-  // device memory
+  // device memory: the inputs, and the outputs + work areas
+  char* in_arena = nullptr;
+  size_t in_arena_bytes = 0;
   char* arena = nullptr;
   size_t arena_bytes = 0;
   BProb* d_probs = nullptr;
@@ -294,6 +312,9 @@ struct ba_batch {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   float ms_h2d = 0.f, ms_kernel = 0.f, ms_d2h = 0.f;
   bool timed = false;
+  // host wall time of the last ba_solve_batch: checks + layout, packing,
+  // the launch and its wait, results
+  double ms_prepare = 0.0, ms_pack = 0.0, ms_run = 0.0, ms_finish = 0.0;
 };
 
 namespace ba {
@@ -305,6 +326,7 @@ void destroy_batch(ba_handle* h) {
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   for (cudaEvent_t e : b->ev)
     if (e) cudaEventDestroy(e);
+  dev_free(h, b->in_arena);
   dev_free(h, b->arena);
   dev_free(h, b->d_probs);
   dev_free(h, b->d_work);
@@ -322,10 +344,15 @@ void destroy_batch(ba_handle* h) {
 int batch_stats(ba_handle* h, ba_kernel_stat* out, int max) {
   const ba_batch* b = h->batch;
   if (!b || !b->timed) return 0;
-  const char* names[3] = {"batch_h2d", "batch_kernel", "batch_d2h"};
-  const float ms[3] = {b->ms_h2d, b->ms_kernel, b->ms_d2h};
+  // host: checks and layout, packing (with the pair counts) and the input
+  // copies it starts, the launch and its wait, results
+  const char* names[7] = {"batch_h2d",          "batch_kernel",    "batch_d2h",
+                          "batch_host_prepare", "batch_host_pack", "batch_host_run",
+                          "batch_host_finish"};
+  const double ms[7] = {b->ms_h2d,  b->ms_kernel, b->ms_d2h,   b->ms_prepare,
+                        b->ms_pack, b->ms_run,    b->ms_finish};
   int w = 0;
-  for (int i = 0; i < 3 && w < max; ++i, ++w) {
+  for (int i = 0; i < 7 && w < max; ++i, ++w) {
     memset(&out[w], 0, sizeof(out[w]));
     strncpy(out[w].name, names[i], sizeof(out[w].name) - 1);
     out[w].launches = 1;
@@ -458,86 +485,151 @@ ba_batch* get_batch(ba_handle* h) {
   return h->batch;
 }
 
-// Copy the problems' inputs into the pinned staging buffer (several host
-// threads for large batches).
-void pack_all(const ba_batch* b, int precision, int32_t n, const ba_problem* pr) {
-  size_t total = b->in_bytes;
-  int nth = total > (64u << 20) ? (int)std::min<unsigned>(8, std::thread::hardware_concurrency())
-                                : 1;
-  if (nth < 1) nth = 1;
-  auto job = [&](int t) {
-    for (int i = t; i < n; i += nth) pack_inputs(precision, pr[i], b->h_in + b->in_off[i]);
-  };
-  if (nth == 1) {
-    job(0);
-    return;
-  }
-  std::vector<std::thread> th;
-  for (int t = 0; t < nth; ++t) th.emplace_back(job, t);
-  for (auto& x : th) x.join();
+// Host threads for the per-problem passes over the inputs (packing, pair
+// counts, result copies): the cores, at most 16.
+int host_threads() {
+  return (int)std::min<unsigned>(16, std::max(1u, std::thread::hardware_concurrency()));
 }
 
-// Lay out a batch: arena offsets, descriptors, work order.  Allocates as
-// needed.  Returns BA_OK or an error with h->err set.
-ba_status prepare(ba_handle* h, ba_batch* b, int32_t n, const ba_problem* pr) {
+// Pack the problems' inputs into the pinned staging buffer, count each
+// problem's point pairs from its packed point indices (in cache right after
+// the copy), and copy the inputs to the input arena on the handle's stream:
+// host threads pack groups of consecutive problems in order while the calling
+// thread starts each group's copy as soon as it is packed, so the copy
+// overlaps the packing of the later groups.  ev[0] is recorded before the
+// first copy.
+ba_status pack_and_copy(ba_handle* h, ba_batch* b, int32_t n, const ba_problem* pr,
+                        std::vector<int64_t>& npairs) {
+  cudaStream_t s = h->stream;
+  const size_t total = b->in_bytes;
+  npairs.assign(n, 0);
+  if (cudaEventRecord(b->ev[0], s) != cudaSuccess) {
+    h->err = "ba_solve_batch: event record failed";
+    return BA_ERR_CUDA;
+  }
   const int prec = h->opts.precision;
-  b->in_off.assign(n, 0);
-  b->out_off.assign(n, 0);
-  std::vector<size_t> work_off(n);
-  std::vector<int64_t> npairs(n);
-  {
-    // pair counts need a pass over every problem's observations: host threads
-    int nth = (int)std::min<unsigned>(8, std::max(1u, std::thread::hardware_concurrency()));
-    if (n < 16) nth = 1;
-    auto job = [&](int t) {
-      for (int i = t; i < n; i += nth) npairs[i] = count_pairs(pr[i]);
+  auto pack_one = [&](int i) {
+    char* dst = b->h_in + b->in_off[i];
+    pack_inputs(prec, pr[i], dst);
+    Carve c(dst);
+    const InPtrs r = carve_in(c, pr[i].n_cams, pr[i].n_pts, pr[i].n_obs);
+    npairs[i] = count_pairs_raw(r.pt, pr[i].n_obs, pr[i].n_pts);
+  };
+  const int nth = (total > (32u << 20) && n >= 16) ? host_threads() : 1;
+  // groups of about total / (4 threads) bytes, at least 8 MB
+  const size_t target = std::max<size_t>((size_t)8 << 20, total / (4 * (size_t)nth));
+  std::vector<int> gbeg{0};
+  for (int i = 0; i + 1 < n; ++i)
+    if (b->in_off[i + 1] - b->in_off[gbeg.back()] >= target) gbeg.push_back(i + 1);
+  gbeg.push_back(n);
+  const int G = (int)gbeg.size() - 1;
+  cudaError_t e = cudaSuccess;
+  if (nth == 1 || G == 1) {
+    for (int i = 0; i < n; ++i) pack_one(i);
+    e = cudaMemcpyAsync(b->in_arena, b->h_in, total, cudaMemcpyHostToDevice, s);
+  } else {
+    std::atomic<int> next{0};
+    std::unique_ptr<std::atomic<int>[]> done(new std::atomic<int>[G]);
+    for (int g = 0; g < G; ++g) done[g].store(0, std::memory_order_relaxed);
+    auto worker = [&]() {
+      for (int g; (g = next.fetch_add(1)) < G;) {
+        for (int i = gbeg[g]; i < gbeg[g + 1]; ++i) pack_one(i);
+        done[g].store(1, std::memory_order_release);
+      }
     };
-    if (nth == 1) {
-      job(0);
-    } else {
-      std::vector<std::thread> th;
-      for (int t = 0; t < nth; ++t) th.emplace_back(job, t);
-      for (auto& x : th) x.join();
+    std::vector<std::thread> th;
+    for (int t = 0; t < std::min(nth, G); ++t) th.emplace_back(worker);
+    for (int g = 0; g < G; ++g) {
+      while (!done[g].load(std::memory_order_acquire)) std::this_thread::yield();
+      const size_t off = b->in_off[gbeg[g]];
+      const size_t len = (gbeg[g + 1] < n ? b->in_off[gbeg[g + 1]] : total) - off;
+      if (e == cudaSuccess && len)
+        e = cudaMemcpyAsync(b->in_arena + off, b->h_in + off, len, cudaMemcpyHostToDevice, s);
+    }
+    for (auto& x : th) x.join();
+  }
+  if (e != cudaSuccess) {
+    h->err = std::string("ba_solve_batch: input copy failed: ") + cudaGetErrorString(e);
+    return BA_ERR_CUDA;
+  }
+  return BA_OK;
+}
+
+// Drop the cached graph (it holds the arenas' addresses) before an arena is
+// replaced.
+void drop_graph(ba_handle* h, ba_batch* b) {
+  if (b->gexec) {
+    cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+  }
+  cudaStreamSynchronize(h->stream);
+}
+
+// Lay out a batch's inputs: offsets in the input arena (they depend on the
+// problems' sizes alone), the input arena and the pinned staging buffer.
+ba_status prepare_inputs(ba_handle* h, ba_batch* b, int32_t n, const ba_problem* pr) {
+  b->in_off.assign(n, 0);
+  size_t in = 0;
+  int max_cams = 1;
+  for (int i = 0; i < n; ++i) {
+    Carve ci(nullptr);
+    carve_in(ci, pr[i].n_cams, pr[i].n_pts, pr[i].n_obs);
+    b->in_off[i] = in;
+    in += ci.off;
+    max_cams = std::max(max_cams, (int)pr[i].n_cams);
+  }
+  b->in_bytes = in;
+  b->max_cams = max_cams;
+  if (b->in_arena_bytes < in || !b->in_arena) {
+    drop_graph(h, b);
+    dev_free(h, b->in_arena);
+    b->in_arena = (char*)dev_alloc(h, in);
+    b->in_arena_bytes = b->in_arena ? in : 0;
+    if (!b->in_arena) {
+      h->err = "ba_solve_batch: out of device memory for " + std::to_string(in) + " bytes";
+      return BA_ERR_OOM;
     }
   }
-  size_t in = 0, out = 0, work = 0;
-  int max_cams = 1;
+  if (!grow_host(b->h_in, b->h_in_bytes, in)) {
+    h->err = "ba_solve_batch: pinned host allocation failed";
+    return BA_ERR_OOM;
+  }
+  return BA_OK;
+}
+
+// Lay out the rest once the pair counts are known: the outputs + work arena,
+// the descriptors and the work order.  Allocates as needed.  Returns BA_OK or
+// an error with h->err set.
+ba_status prepare_work(ba_handle* h, ba_batch* b, int32_t n, const ba_problem* pr,
+                       const std::vector<int64_t>& npairs) {
+  const int prec = h->opts.precision;
+  b->out_off.assign(n, 0);
+  std::vector<size_t> work_off(n);
+  size_t out = 0, work = 0;
   for (int i = 0; i < n; ++i) {
     if (npairs[i] > (int64_t)INT32_MAX - 64) {
       h->err = "ba_solve_batch: problem " + std::to_string(i) + " has too many point pairs";
       return BA_ERR_INVALID_ARG;
     }
     const ProbBytes pb = prob_bytes(prec, pr[i].n_cams, pr[i].n_pts, pr[i].n_obs, npairs[i]);
-    b->in_off[i] = in;
     b->out_off[i] = out;
     work_off[i] = work;
-    in += pb.in;
     out += pb.out;
     work += pb.work;
-    max_cams = std::max(max_cams, (int)pr[i].n_cams);
   }
-  b->in_bytes = in;
   b->out_bytes = out;
-  b->max_cams = max_cams;
-  const size_t need = in + out + work;
+  const size_t need = out + work;
   if (b->arena_bytes < need || !b->arena) {
-    if (b->gexec) {
-      cudaGraphExecDestroy(b->gexec);
-      b->gexec = nullptr;
-    }
-    cudaStreamSynchronize(h->stream);
+    drop_graph(h, b);
     dev_free(h, b->arena);
-    b->arena = nullptr;
-    b->arena_bytes = 0;
-    void* p = dev_alloc(h, need);
-    if (!p) {
+    b->arena = (char*)dev_alloc(h, need);
+    b->arena_bytes = b->arena ? need : 0;
+    if (!b->arena) {
       h->err = "ba_solve_batch: out of device memory for " + std::to_string(need) + " bytes";
       return BA_ERR_OOM;
     }
-    b->arena = (char*)p;
-    b->arena_bytes = need;
   }
-  if (!grow_host(b->h_in, b->h_in_bytes, in) || !grow_host(b->h_out, b->h_out_bytes, out) ||
+  if (!grow_host(b->h_out, b->h_out_bytes, out) ||
       !grow_host(b->h_probs, b->h_probs_cap, (size_t)n) ||
       !grow_host(b->h_work, b->h_work_cap, (size_t)n)) {
     h->err = "ba_solve_batch: pinned host allocation failed";
@@ -560,9 +652,8 @@ ba_status prepare(ba_handle* h, ba_batch* b, int32_t n, const ba_problem* pr) {
     h->err = "ba_solve_batch: out of device memory";
     return BA_ERR_OOM;
   }
-  char* din = b->arena;
-  char* dout = b->arena + in;
-  char* dwork = b->arena + in + out;
+  char* dout = b->arena;
+  char* dwork = b->arena + out;
   const int iters = h->opts.max_lm_iters;
   for (int i = 0; i < n; ++i) {
     BProb& p = b->h_probs[i];
@@ -574,7 +665,7 @@ ba_status prepare(ba_handle* h, ba_batch* b, int32_t n, const ba_problem* pr) {
     p.K = Intrinsics{pr[i].K.fx, pr[i].K.fy, pr[i].K.cx, pr[i].K.cy};
     p.phase = kPhaseSetup;
     p.npairs = npairs[i];
-    assign_prob(prec, p, din + b->in_off[i], dout + b->out_off[i], dwork + work_off[i]);
+    assign_prob(prec, p, b->in_arena + b->in_off[i], dout + b->out_off[i], dwork + work_off[i]);
   }
   std::vector<int32_t> ord(n);
   std::iota(ord.begin(), ord.end(), 0);
@@ -592,7 +683,9 @@ cudaError_t record(cudaEvent_t e, cudaStream_t s, bool capturing) {
   return capturing ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) : cudaEventRecord(e, s);
 }
 
-// Record the copy-in, launch and copy-out on the handle's stream.
+// Record the descriptors' copy-in, the launch and (with `copies`) the
+// copy-out on the handle's stream.  With `copies`, the arena's inputs were
+// copied in by pack_and_copy, which recorded ev[0].
 ba_status enqueue(ba_handle* h, ba_batch* b, int threads, int ctas_per_sm, bool copies,
                   bool capturing) {
   size_t smem = 0;
@@ -604,10 +697,6 @@ ba_status enqueue(ba_handle* h, ba_batch* b, int threads, int ctas_per_sm, bool 
     return BA_ERR_INVALID_ARG;
   }
   cudaStream_t s = h->stream;
-  if (copies) {
-    BCK(record(b->ev[0], s, capturing));
-    BCK(cudaMemcpyAsync(b->arena, b->h_in, b->in_bytes, cudaMemcpyHostToDevice, s));
-  }
   BCK(cudaMemcpyAsync(b->d_probs, b->h_probs, sizeof(BProb) * b->n, cudaMemcpyHostToDevice, s));
   BCK(cudaMemcpyAsync(b->d_work, b->h_work, sizeof(int32_t) * b->n, cudaMemcpyHostToDevice, s));
   BCK(cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned), s));
@@ -633,7 +722,7 @@ ba_status enqueue(ba_handle* h, ba_batch* b, int threads, int ctas_per_sm, bool 
     BCK(cudaMemcpyAsync(b->h_phase, b->d_phase, sizeof(unsigned long long) * kPhaseCount,
                         cudaMemcpyDeviceToHost, s));
   if (copies) {
-    BCK(cudaMemcpyAsync(b->h_out, b->arena + b->in_bytes, b->out_bytes, cudaMemcpyDeviceToHost, s));
+    BCK(cudaMemcpyAsync(b->h_out, b->arena, b->out_bytes, cudaMemcpyDeviceToHost, s));
     BCK(record(b->ev[3], s, capturing));
   }
   return BA_OK;
@@ -648,7 +737,7 @@ ba_status run(ba_handle* h, ba_batch* b, int threads, int ctas_per_sm, bool copi
     return BA_OK;
   }
   std::vector<size_t> key = {(size_t)b->n,     b->in_bytes,         b->out_bytes,
-                             (size_t)b->arena, (size_t)b->h_in,     (size_t)b->h_out,
+                             (size_t)b->arena, (size_t)b->in_arena, (size_t)b->h_out,
                              (size_t)threads,  (size_t)ctas_per_sm, (size_t)b->max_cams,
                              (size_t)b->d_probs, (size_t)b->h_probs};
   if (!b->gexec || key != b->gkey) {
@@ -692,16 +781,30 @@ ba_status finish(ba_handle* h, ba_batch* b, int32_t n, const ba_problem* pr, ba_
   }
   ba_status overall = BA_OK;
   std::string why;
-  for (int i = 0; i < n; ++i) {
-    const BProb& p = b->h_probs[i];
-    fill_result(p, res[i]);
-    if (res[i].status == BA_OK) {
+  for (int i = 0; i < n; ++i) fill_result(b->h_probs[i], res[i]);
+  // the poses and points into the caller's arrays (host threads when large)
+  auto copy_out = [&](int t, int nt) {
+    for (int i = t; i < n; i += nt) {
+      if (res[i].status != BA_OK) continue;
+      const BProb& p = b->h_probs[i];
       Carve c(b->h_out + b->out_off[i]);
       const double* q = c.take<double>((size_t)p.C * 7);
       const double* x = c.take<double>((size_t)p.P * 3);
       if (pr[i].cam_qt_out) memcpy(pr[i].cam_qt_out, q, sizeof(double) * 7 * (size_t)p.C);
       if (pr[i].pts_out) memcpy(pr[i].pts_out, x, sizeof(double) * 3 * (size_t)p.P);
-    } else if (overall == BA_OK) {
+    }
+  };
+  const int nt = b->out_bytes > ((size_t)16 << 20) ? host_threads() : 1;
+  if (nt == 1) {
+    copy_out(0, 1);
+  } else {
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t) th.emplace_back(copy_out, t, nt);
+    for (auto& x : th) x.join();
+  }
+  for (int i = 0; i < n && overall == BA_OK; ++i) {
+    const BProb& p = b->h_probs[i];
+    if (res[i].status != BA_OK) {
       overall = (ba_status)res[i].status;
       why = "problem " + std::to_string(i) + ":" +
             (p.status ? describe_bits(p.status)
@@ -747,16 +850,35 @@ extern "C" {
 
 ba_status ba_solve_batch(ba_handle* h, int32_t n, const ba_problem* problems,
                          ba_result* results) {
+  using Clk = std::chrono::steady_clock;
+  auto ms = [](Clk::time_point a, Clk::time_point b) {
+    return std::chrono::duration<double, std::milli>(b - a).count();
+  };
+  const auto t0 = Clk::now();
   ba_status st = check_batch_args(h, n, problems, results);
   if (st != BA_OK) return st;
   BCK(cudaSetDevice(h->device));
   ba_batch* b = get_batch(h);
-  st = prepare(h, b, n, problems);
+  st = prepare_inputs(h, b, n, problems);
   if (st != BA_OK) return st;
-  pack_all(b, h->opts.precision, n, problems);
+  const auto t1 = Clk::now();
+  std::vector<int64_t> npairs;
+  st = pack_and_copy(h, b, n, problems, npairs);
+  if (st != BA_OK) return st;
+  const auto t2 = Clk::now();
+  st = prepare_work(h, b, n, problems, npairs);
+  if (st != BA_OK) return st;
+  const auto t2b = Clk::now();
   st = run(h, b, b->threads, b->ctas_per_sm, true);
   if (st != BA_OK) return st;
-  return finish(h, b, n, problems, results);
+  const auto t3 = Clk::now();
+  st = finish(h, b, n, problems, results);
+  const auto t4 = Clk::now();
+  b->ms_prepare = ms(t0, t1) + ms(t2, t2b);
+  b->ms_pack = ms(t1, t2);
+  b->ms_run = ms(t2b, t3);
+  b->ms_finish = ms(t3, t4);
+  return st;
 }
 
 ba_status ba_get_batch_schedule(const ba_handle* h, int32_t* threads, int32_t* ctas_per_sm) {
@@ -788,11 +910,14 @@ ba_status ba_tune_batch(ba_handle* h, int32_t n, const ba_problem* problems,
   if (!best_threads || !best_ctas_per_sm) return BA_ERR_INVALID_ARG;
   BCK(cudaSetDevice(h->device));
   ba_batch* b = get_batch(h);
-  st = prepare(h, b, n, problems);
+  st = prepare_inputs(h, b, n, problems);
   if (st != BA_OK) return st;
-  pack_all(b, h->opts.precision, n, problems);
   // inputs resident once; each candidate re-solves them from the same inputs
-  BCK(cudaMemcpyAsync(b->arena, b->h_in, b->in_bytes, cudaMemcpyHostToDevice, h->stream));
+  std::vector<int64_t> npairs;
+  st = pack_and_copy(h, b, n, problems, npairs);
+  if (st != BA_OK) return st;
+  st = prepare_work(h, b, n, problems, npairs);
+  if (st != BA_OK) return st;
   std::vector<BProb> fresh(b->h_probs, b->h_probs + n);
   std::vector<int32_t> order_lpt(b->h_work, b->h_work + n);
   cudaEvent_t e0, e1;
