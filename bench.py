@@ -343,15 +343,23 @@ _PROFILE_NAMES = {"pcg": "k_pcg", "schur": "k_schur", "backsub": "k_backsub",
                   "lin_cam": "k_lin_cam", "lin_pt": "k_lin_pt", "cost_trial": "k_cost"}
 
 
+# The sources of the single-problem path the driving profile covers: its
+# kernels, their headers, the layout kernels that build their inputs and the
+# host code that plans their launches (the multi-problem engine, the server
+# and the opt-in cluster PCG are not on this path).
+DRIVING_SOURCES = ("ba_api.cu", "ba_device.cuh", "ba_internal.h", "handle.h", "layout.cu",
+                   "layout.h", "lm.h", "lm_kernels.cu", "solvers.cu", "../../include/ba.h")
+
+
 def source_digest():
-    """sha256 (first 16 hex digits) of the kernel sources' names and bytes."""
+    """sha256 (first 16 hex digits) of the names and bytes of the driving
+    path's sources."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2510_15271_b300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(f.encode())
-            with open(os.path.join(d, f), "rb") as fh:
-                h.update(fh.read())
+    for f in sorted(DRIVING_SOURCES):
+        h.update(f.encode())
+        with open(os.path.normpath(os.path.join(d, f)), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
