@@ -207,3 +207,22 @@ def test_all_cameras_fixed_window_moves_only_points():
     rel = np.abs(res[0].costs() - ref.costs) / ref.costs
     assert rel.max() <= COST_RTOL
     np.testing.assert_allclose(arrs[0].q_out[:, 4:], s.cam_qt[:, 4:], atol=1e-12)
+
+
+def test_large_batch_packed_by_host_threads_matches_small_batches():
+    """Above 32 MB of inputs the host packs groups of windows on several
+    threads and copies each group as soon as it is packed, counting the pair
+    lists from the packed copies; the results must equal those of the same
+    windows solved in small batches (packed on one thread)."""
+    ws = scenes.make_windows(80, seed=21)
+    assert sum(len(w.obs_cam) for w in ws) * 24 > (36 << 20)
+    big_res, big_arrs = _batch(ws, "fp32")
+    small_res, small_arrs = [], []
+    for k in range(0, len(ws), 8):
+        r, a = _batch(ws[k:k + 8], "fp32")
+        small_res += r
+        small_arrs += a
+    for rb, ab, rs, as_ in zip(big_res, big_arrs, small_res, small_arrs):
+        assert rb.status == ba.BA_OK and rs.status == ba.BA_OK
+        assert np.array_equal(rb.costs(), rs.costs())
+        assert np.array_equal(ab.q_out, as_.q_out) and np.array_equal(ab.p_out, as_.p_out)
