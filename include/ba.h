@@ -242,6 +242,54 @@ ba_status ba_cost_noalloc(int device, void* cuda_stream, int32_t n_cams, int32_t
                           const int32_t* obs_cam, const int32_t* obs_pt, const double* obs_uv,
                           const ba_intrinsics* K, double huber_delta, double* cost_out);
 
+/* Reprojection error of every observation and its outlier classification:
+ * the step after each BA round of the paper's mapping loop (Sec. 4.3:
+ * reprojection errors are computed from the updated points and poses, and
+ * projections beyond the outlier threshold are removed).
+ *   device, cuda_stream  CUDA device ordinal; stream to run on (NULL: the
+ *                legacy default stream); the caller's current device is
+ *                restored
+ *   cam_qt [n_cams][7], pts [n_pts][3], obs_cam, obs_pt [n_obs],
+ *   obs_uv [n_obs][2], K   as in ba_set_problem
+ *   threshold_px the outlier threshold (>= 0)
+ *   err2_out     [n_obs] or NULL: ||pi(K (R X + t)) - p_obs||^2 in px^2,
+ *                +inf where the point's depth is below 1e-3
+ *   inlier_out   [n_obs] or NULL: 1 where err2 <= threshold_px^2, else 0
+ *   n_inliers    host pointer or NULL: the number of inliers
+ *   mem_kind     BA_MEM_HOST: every array pointer is host memory (copied
+ *                in and out; the call allocates device scratch);
+ *                BA_MEM_DEVICE: device memory of `device`
+ * FP64 throughout.  Blocks until the outputs are written.  Errors (message
+ * in ba_last_error(NULL)): INVALID_ARG (NULL input, sizes, threshold,
+ * intrinsics, an index out of range), OOM, CUDA. */
+ba_status ba_reprojection_errors(int32_t device, void* cuda_stream, int32_t n_cams, int32_t n_pts,
+                                 int64_t n_obs, const double* cam_qt, const double* pts,
+                                 const int32_t* obs_cam, const int32_t* obs_pt,
+                                 const double* obs_uv, const ba_intrinsics* K,
+                                 double threshold_px, double* err2_out, uint8_t* inlier_out,
+                                 int64_t* n_inliers, int32_t mem_kind);
+
+/* Triangulation of every point by the DLT of the paper's Sec. 4.3, Eq. (dlt),
+ * from its observations whose mask is set, with the given camera poses: the
+ * homogeneous point minimising the sum of ||P_j X - lambda_j p_j||^2, P_j =
+ * [R_j | t_j] and p_j the observation in normalised camera coordinates
+ * K^-1 (u, v, 1); that is the eigenvector of the smallest eigenvalue of A^T A,
+ * A the two rows x P_j^3 - P_j^1, y P_j^3 - P_j^2 of each observation.
+ *   obs_mask     [n_obs] or NULL (all observations): nonzero = use
+ *   pts_out      [n_pts][3]: the triangulated points, NaN where status != 0
+ *   status_out   [n_pts] or NULL: 0 triangulated; 1 fewer than 2 observations
+ *                used; 2 the solution lies at infinity (|X_4| <= 1e-12 ||X||);
+ *                3 behind a camera that observes it (depth below 1e-3)
+ * Other arguments as in ba_reprojection_errors.  FP64; each point's rows are
+ * summed in (point, camera) order, so results do not depend on the order of
+ * the observations.  Blocks until the outputs are written.  Errors:
+ * INVALID_ARG, OOM, CUDA. */
+ba_status ba_triangulate(int32_t device, void* cuda_stream, int32_t n_cams, int32_t n_pts,
+                         int64_t n_obs, const double* cam_qt, const int32_t* obs_cam,
+                         const int32_t* obs_pt, const double* obs_uv, const ba_intrinsics* K,
+                         const uint8_t* obs_mask, double* pts_out, int8_t* status_out,
+                         int32_t mem_kind);
+
 /* Self-test of the bounded grid barrier the PCG kernels wait at: launches
  * `blocks` co-resident CTAs (1..64) that meet at one grid barrier expecting
  * `expected` arrivals, each wait giving up after limit_ms (0 < limit_ms <=

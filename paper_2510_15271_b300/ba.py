@@ -130,6 +130,13 @@ _SIGNATURES = {
                                 c_void_p]),
     "ba_selftest_barrier": (c_int, [c_int32, c_int32, c_int32, c_double, POINTER(c_int32),
                                     POINTER(c_double)]),
+    "ba_reprojection_errors": (c_int, [c_int32, c_void_p, c_int32, c_int32, c_int64, c_void_p,
+                                       c_void_p, c_void_p, c_void_p, c_void_p,
+                                       POINTER(Intrinsics), c_double, c_void_p, c_void_p,
+                                       POINTER(c_int64), c_int32]),
+    "ba_triangulate": (c_int, [c_int32, c_void_p, c_int32, c_int32, c_int64, c_void_p, c_void_p,
+                               c_void_p, c_void_p, POINTER(Intrinsics), c_void_p, c_void_p,
+                               c_void_p, c_int32]),
 }
 
 EXPORTS = tuple(_SIGNATURES)
@@ -403,6 +410,49 @@ def ba_selftest_barrier(device: int = 0, blocks: int = 8, expected: int = 8,
     _check(lib().ba_selftest_barrier(device, blocks, expected, limit_ms, ctypes.byref(t),
                                      ctypes.byref(w)))
     return bool(t.value), w.value
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(c_void_p)
+
+
+def ba_reprojection_errors(cam_qt, pts, obs_cam, obs_pt, obs_uv, intrinsics, threshold_px,
+                           device: int = 0, want_err2: bool = True):
+    """(err2 or None, inlier mask (bool), inlier count) of every observation
+    (ba_reprojection_errors, host arrays)."""
+    q = _host(cam_qt, np.float64, (-1, 7))
+    X = _host(pts, np.float64, (-1, 3))
+    oc = _host(obs_cam, np.int32)
+    op = _host(obs_pt, np.int32)
+    uv = _host(obs_uv, np.float64, (-1, 2))
+    n = oc.shape[0]
+    err2 = np.empty(n) if want_err2 else None
+    inl = np.empty(n, dtype=np.uint8)
+    cnt = c_int64()
+    K = Intrinsics(*intrinsics)
+    _check(lib().ba_reprojection_errors(device, None, q.shape[0], X.shape[0], n, _ptr(q), _ptr(X),
+                                        _ptr(oc), _ptr(op), _ptr(uv), ctypes.byref(K),
+                                        float(threshold_px), _ptr(err2), _ptr(inl),
+                                        ctypes.byref(cnt), BA_MEM_HOST))
+    return err2, inl.astype(bool), int(cnt.value)
+
+
+def ba_triangulate(cam_qt, obs_cam, obs_pt, obs_uv, intrinsics, n_pts: int, mask=None,
+                   device: int = 0):
+    """(points (n_pts, 3), status (n_pts,) int8) by DLT (ba_triangulate, host
+    arrays)."""
+    q = _host(cam_qt, np.float64, (-1, 7))
+    oc = _host(obs_cam, np.int32)
+    op = _host(obs_pt, np.int32)
+    uv = _host(obs_uv, np.float64, (-1, 2))
+    m = None if mask is None else _host(np.asarray(mask).astype(np.uint8), np.uint8)
+    X = np.empty((n_pts, 3))
+    status = np.empty(n_pts, dtype=np.int8)
+    K = Intrinsics(*intrinsics)
+    _check(lib().ba_triangulate(device, None, q.shape[0], n_pts, oc.shape[0], _ptr(q), _ptr(oc),
+                                _ptr(op), _ptr(uv), ctypes.byref(K), _ptr(m), _ptr(X),
+                                _ptr(status), BA_MEM_HOST))
+    return X, status
 
 
 def options_for_scene(scene, precision: Optional[str] = None, **kw) -> Options:
