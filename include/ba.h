@@ -257,9 +257,12 @@ ba_status ba_cost_noalloc(int device, void* cuda_stream, int32_t n_cams, int32_t
  *   inlier_out   [n_obs] or NULL: 1 where err2 <= threshold_px^2, else 0
  *   n_inliers    host pointer or NULL: the number of inliers
  *   mem_kind     BA_MEM_HOST: every array pointer is host memory (copied
- *                in and out; the call allocates device scratch);
+ *                in and out through device scratch);
  *                BA_MEM_DEVICE: device memory of `device`
- * FP64 throughout.  Blocks until the outputs are written.  Errors (message
+ * FP64 throughout.  Blocks until the outputs are written.  This call and
+ * ba_triangulate keep their device scratch between calls (per device, grown
+ * as needed, released at process exit) and serialise concurrent calls on one
+ * device.  Errors (message
  * in ba_last_error(NULL)): INVALID_ARG (NULL input, sizes, threshold,
  * intrinsics, an index out of range), OOM, CUDA. */
 ba_status ba_reprojection_errors(int32_t device, void* cuda_stream, int32_t n_cams, int32_t n_pts,

@@ -22,6 +22,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 
 #include "../../include/ba.h"
@@ -48,6 +49,38 @@ __global__ void k_tri_cams(int C, const double* __restrict__ qt, double* __restr
   }
 }
 
+// Add two per-thread counts of the block to counts[0] and counts[1]: one
+// atomic per block, not per warp (tens of thousands of warps adding to one
+// address serialise at the L2).
+__device__ void block_count2(unsigned long long a, unsigned long long b,
+                             unsigned long long* counts) {
+  __shared__ unsigned long long sa[32], sb[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0) {
+    sa[warp] = a;
+    sb[warp] = b;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    a = lane < nw ? sa[lane] : 0;
+    b = lane < nw ? sb[lane] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, o);
+      b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+      if (a) atomicAdd(counts, a);
+      if (b) atomicAdd(counts + 1, b);
+    }
+  }
+}
+
 // counts[0]: inliers, counts[1]: observations with an index out of range.
 __global__ void k_reproj(int64_t N, int C, int P, const double* __restrict__ Rt,
                          const double* __restrict__ X, const int32_t* __restrict__ cam,
@@ -69,8 +102,10 @@ __global__ void k_reproj(int64_t N, int C, int P, const double* __restrict__ Rt,
       const double yc = R[3] * x0 + R[4] * x1 + R[5] * x2 + R[10];
       const double zc = R[6] * x0 + R[7] * x1 + R[8] * x2 + R[11];
       if (zc >= kZMin) {
-        const double du = K.fx * xc / zc + K.cx - uv[2 * k];
-        const double dv = K.fy * yc / zc + K.cy - uv[2 * k + 1];
+        // one division per observation (FP64 division is slow on this part)
+        const double iz = 1.0 / zc;
+        const double du = K.fx * xc * iz + K.cx - uv[2 * k];
+        const double dv = K.fy * yc * iz + K.cy - uv[2 * k + 1];
         e = du * du + dv * dv;
       } else {
         e = INFINITY;
@@ -81,27 +116,17 @@ __global__ void k_reproj(int64_t N, int C, int P, const double* __restrict__ Rt,
     if (err2) err2[k] = e;
     if (inl) inl[k] = in ? 1 : 0;
   }
-  // warp-aggregated counts
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    good += __shfl_down_sync(0xffffffffu, good, o);
-    bad += __shfl_down_sync(0xffffffffu, bad, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    if (good) atomicAdd(counts, good);
-    if (bad) atomicAdd(counts + 1, bad);
-  }
+  block_count2(good, bad, counts);
 }
 
+// counts[1]: observations with an index out of range.
 __global__ void k_tri_check(int64_t N, int C, int P, const int32_t* __restrict__ cam,
-                            const int32_t* __restrict__ pt, unsigned long long* __restrict__ bad) {
+                            const int32_t* __restrict__ pt, unsigned long long* __restrict__ counts) {
   unsigned long long b = 0;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N;
        k += (int64_t)gridDim.x * blockDim.x)
     if (cam[k] < 0 || cam[k] >= C || pt[k] < 0 || pt[k] >= P) ++b;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) b += __shfl_down_sync(0xffffffffu, b, o);
-  if ((threadIdx.x & 31) == 0 && b) atomicAdd(bad, b);
+  block_count2(0, b, counts);
 }
 
 __global__ void k_tri_counts(int64_t N, const int32_t* __restrict__ pt, int32_t* __restrict__ cnt) {
@@ -251,30 +276,53 @@ __global__ void k_tri_points(int P, const int32_t* __restrict__ ptr,
   }
 }
 
-unsigned grid_of(int64_t n, int threads) {
+unsigned grid_of(int64_t n, int threads, int per_sm = 32) {
   const int64_t g = (n + threads - 1) / threads;
-  return (unsigned)(g < 1 ? 1 : (g > 148 * 32 ? 148 * 32 : g));
+  const int64_t cap = (int64_t)148 * per_sm;
+  return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
 }
 
-// Device buffers of one call, freed on return.
+// Device scratch of the calls, kept per device between calls (grown when a
+// call needs more; held until the process exits): allocation and its
+// implicit synchronisation would otherwise cost more than the kernels.  A
+// call takes its device's lock for its whole duration and numbers its
+// buffers in a fixed order from its own first slot.
+constexpr int kMaxDevices = 64;
+constexpr int kSlots = 48;
+struct ScratchCache {
+  std::mutex mu;
+  void* p[kSlots] = {};
+  size_t cap[kSlots] = {};
+};
+ScratchCache g_scratch[kMaxDevices];
+
 struct Scratch {
-  std::string* err;
-  void* p[32] = {};
-  int n = 0;
+  ScratchCache& c;
+  int n;
   bool ok = true;
+  Scratch(int device, int first_slot) : c(g_scratch[device]), n(first_slot) {}
   template <typename X>
   X* get(size_t count) {
-    void* q = nullptr;
-    if (!ok || n >= 32 || cudaMalloc(&q, count ? count * sizeof(X) : 1) != cudaSuccess) {
-      cudaGetLastError();
+    const size_t bytes = count ? count * sizeof(X) : 1;
+    if (!ok || n >= kSlots) {
       ok = false;
       return nullptr;
     }
-    p[n++] = q;
-    return (X*)q;
-  }
-  ~Scratch() {
-    for (int i = 0; i < n; ++i) cudaFree(p[i]);
+    const int k = n++;
+    if (c.cap[k] < bytes) {
+      if (c.p[k]) cudaFree(c.p[k]);
+      c.p[k] = nullptr;
+      c.cap[k] = 0;
+      const size_t want = bytes + bytes / 4;
+      if (cudaMalloc(&c.p[k], want) != cudaSuccess) {
+        cudaGetLastError();
+        c.p[k] = nullptr;
+        ok = false;
+        return nullptr;
+      }
+      c.cap[k] = want;
+    }
+    return (X*)c.p[k];
   }
 };
 
@@ -308,7 +356,8 @@ bool common_checks(const char* fn, int32_t n_cams, int32_t n_pts, int64_t n_obs,
     return false;
   }
   int ndev = 0;
-  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev ||
+      device >= kMaxDevices) {
     cudaGetLastError();
     g_create_error = std::string(fn) + ": no such CUDA device";
     return false;
@@ -348,7 +397,8 @@ extern "C" ba_status ba_reprojection_errors(int32_t device, void* cuda_stream, i
   cudaStream_t s = (cudaStream_t)cuda_stream;
   ba_status st = BA_OK;
   {
-    Scratch sc{&g_create_error};
+    std::lock_guard<std::mutex> lock(g_scratch[device].mu);
+    Scratch sc(device, 0);
     const size_t N = (size_t)n_obs;
     const double* d_qt = input(sc, cam_qt, 7 * (size_t)n_cams, mem_kind, s);
     const double* d_pts = input(sc, pts, 3 * (size_t)n_pts, mem_kind, s);
@@ -364,7 +414,7 @@ extern "C" ba_status ba_reprojection_errors(int32_t device, void* cuda_stream, i
     if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, 2 * sizeof(unsigned long long), s);
     if (e == cudaSuccess) {
       k_tri_cams<<<grid_of(n_cams, 128), 128, 0, s>>>(n_cams, d_qt, d_Rt);
-      k_reproj<<<grid_of(n_obs, 256), 256, 0, s>>>(
+      k_reproj<<<grid_of(n_obs, 256, 8), 256, 0, s>>>(
           n_obs, n_cams, n_pts, d_Rt, d_pts, d_cam, d_pt, d_uv,
           Intrinsics{K->fx, K->fy, K->cx, K->cy}, threshold_px * threshold_px, d_err, d_inl,
           d_cnt);
@@ -414,7 +464,8 @@ extern "C" ba_status ba_triangulate(int32_t device, void* cuda_stream, int32_t n
   cudaStream_t s = (cudaStream_t)cuda_stream;
   ba_status st = BA_OK;
   {
-    Scratch sc{&g_create_error};
+    std::lock_guard<std::mutex> lock(g_scratch[device].mu);
+    Scratch sc(device, 16);
     const int64_t N = n_obs;
     const int P = n_pts, C = n_cams;
     const double* d_qt = input(sc, cam_qt, 7 * (size_t)C, mem_kind, s);
@@ -424,14 +475,14 @@ extern "C" ba_status ba_triangulate(int32_t device, void* cuda_stream, int32_t n
     const uint8_t* d_mask = input(sc, obs_mask, (size_t)N, mem_kind, s);
     double* d_X = mem_kind == BA_MEM_HOST ? sc.get<double>(3 * (size_t)P) : pts_out;
     int8_t* d_st = status_out && mem_kind == BA_MEM_HOST ? sc.get<int8_t>((size_t)P) : status_out;
-    unsigned long long* d_bad = sc.get<unsigned long long>(1);
+    unsigned long long* d_bad = sc.get<unsigned long long>(2);
     unsigned long long bad = 0;
     cudaError_t e = sc.ok ? cudaSuccess : cudaErrorMemoryAllocation;
     // indices first: the sort and the counts index by them
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, 2 * sizeof(unsigned long long), s);
     if (e == cudaSuccess) {
-      k_tri_check<<<grid_of(N, 256), 256, 0, s>>>(N, C, P, d_cam, d_pt, d_bad);
-      e = cudaMemcpyAsync(&bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, s);
+      k_tri_check<<<grid_of(N, 256, 8), 256, 0, s>>>(N, C, P, d_cam, d_pt, d_bad);
+      e = cudaMemcpyAsync(&bad, d_bad + 1, sizeof(bad), cudaMemcpyDeviceToHost, s);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess && bad) {
