@@ -459,6 +459,8 @@ class LMOptions:
     pcg_max_iters: int = 100
     mu0: float = 1e-4
     nu0: float = 2.0
+    prior_seq: float = 0.0       # lambda_c of the sequential pose prior (oracle/priors.py)
+    prior_abs: float = 0.0       # lambda_a of the absolute pose prior
 
 
 @dataclasses.dataclass
@@ -489,6 +491,14 @@ def solve_step(prob: Problem, lin, mu: float, opts: LMOptions):
     U, V, W, gc, gp = lin["U"], lin["V"], lin["W"], lin["gc"], lin["gp"]
     Us, Vs, Dc, Dp = damped_blocks(U, V, mu)
     S, b, Vinv, Wm = schur_system(prob, Us, Vs, W, gc, gp)
+    if lin.get("cpl") is not None:
+        # the sequential prior couples adjacent free cameras (undamped)
+        _, pos = _free_index(prob)
+        for i, B in enumerate(lin["cpl"]):
+            a, c = pos[i], pos[i + 1]
+            if a >= 0 and c >= 0:
+                S[6 * a:6 * a + 6, 6 * c:6 * c + 6] += B
+                S[6 * c:6 * c + 6, 6 * a:6 * a + 6] += B.T
     iters = 0
     if free.size == 0:
         dcf = np.zeros(0)
@@ -516,13 +526,31 @@ def model_decrease(h, D, g, mu):
     return 0.5 * float(h @ (mu * D * h - g))
 
 
-def _linearization(prob, st, opts):
+def _linearization(prob, st, opts, pri=None):
+    dU = dg = cpl = None
+    if pri is not None:
+        from .priors import prior_blocks
+        dU, dg, cpl = prior_blocks(st, pri, prob.cam_fixed)
     if opts.solver == "full":
         A, g = full_normal_equations(prob, st, opts.huber_delta)
+        if pri is not None:
+            free, pos = _free_index(prob)
+            for i in free:
+                a = 6 * pos[i]
+                A[a:a + 6, a:a + 6] += dU[i]
+                g[a:a + 6] += dg[i]
+            for i, B in enumerate(cpl):
+                a, c = pos[i], pos[i + 1]
+                if a >= 0 and c >= 0:
+                    A[6 * a:6 * a + 6, 6 * c:6 * c + 6] += B
+                    A[6 * c:6 * c + 6, 6 * a:6 * a + 6] += B.T
         return {"A": A, "g": g}
     r, w, Jc, Jp = linearize(prob, st, opts.huber_delta)
     U, V, W, gc, gp = block_sums(prob, r, w, Jc, Jp)
-    return {"U": U, "V": V, "W": W, "gc": gc, "gp": gp}
+    if pri is not None:
+        U = U + dU
+        gc = gc + dg
+    return {"U": U, "V": V, "W": W, "gc": gc, "gp": gp, "cpl": cpl}
 
 
 def lm_solve(prob: Problem, st0: State, opts: LMOptions) -> LMResult:
@@ -532,12 +560,20 @@ def lm_solve(prob: Problem, st0: State, opts: LMOptions) -> LMResult:
     linearisation (the state did not change) and raises the damping."""
     st = st0.copy()
     mu, nu = opts.mu0, opts.nu0
-    F = cost(prob, st, opts.huber_delta)
+    pri = None
+    if opts.prior_seq > 0 or opts.prior_abs > 0:
+        # pose priors (Sec. 4.2 Eq. seq, Sec. 4.3 Eq. abs), measured on st0
+        from .priors import Priors, prior_cost
+        pri = Priors(st0, opts.prior_seq, opts.prior_abs)
+        F_of = lambda x: cost(prob, x, opts.huber_delta) + prior_cost(x, pri)
+    else:
+        F_of = lambda x: cost(prob, x, opts.huber_delta)
+    F = F_of(st)
     costs, acc, mus, cg, gains, dLs = [F], [], [], [], [], []
     lin = None
     for _ in range(opts.lm_iters):
         if lin is None:
-            lin = _linearization(prob, st, opts)
+            lin = _linearization(prob, st, opts, pri)
         step = solve_step(prob, lin, mu, opts)
         if step is None:      # failed factorisation counts as a rejected step
             dL, F_new, iters = -np.inf, F, 0
@@ -545,7 +581,7 @@ def lm_solve(prob: Problem, st0: State, opts: LMOptions) -> LMResult:
             dc, dp, D, g, h, iters = step
             dL = model_decrease(h, D, g, mu)
             cand = retract(st, dc, dp)
-            F_new = cost(prob, cand, opts.huber_delta)
+            F_new = F_of(cand)
         gain = (F - F_new) / dL if dL > 0 else -np.inf
         mus.append(mu)
         cg.append(iters)
