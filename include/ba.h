@@ -121,6 +121,19 @@ typedef struct {
                                so that they do not share hardware queues with
                                the ticks, which would hold a tick behind a
                                long launch                                   */
+  double prior_seq_weight;  /* lambda_c of the sequential pose prior (Sec. 4.2,
+                               Eq. seq, adjacent frames; 0: off): adds
+                               1/2 lambda_c sum_i ||T_cw,i+1 T_wc,i - Q_i||^2,
+                               Q_i the relative pose of cameras i, i+1 (in
+                               index order) in the state given to
+                               ba_set_problem; Frobenius norm of the top 3x4
+                               blocks.  ba_solve only                         */
+  double prior_abs_weight;  /* lambda_a of the absolute pose prior (Sec. 4.3,
+                               Eq. abs; 0: off): adds 1/2 lambda_a sum_i
+                               ||T_wc,i - T_wc,i^0||^2 with T_wc^0 the
+                               camera-to-world pose given to ba_set_problem.
+                               ba_solve only (ba_solve_batch and
+                               ba_create_server refuse it)                    */
 } ba_options;
 
 typedef struct {
@@ -162,7 +175,7 @@ typedef struct {
  * PCG tol 1e-6 / 100, no refinement (5 steps, tol 1e-6 when enabled),
  * mu0 1e-4, dense_max_dim 1200, device 0, library stream, graphs on,
  * cudaMalloc, serving arena 0 (= 1/4 of free memory), 256 slots, 4096 queue,
- * tick 4 ms, split 10 ms. */
+ * tick 4 ms, split 10 ms, no pose priors. */
 void ba_options_default(ba_options* opts);
 
 /* Create a solver handle on opts->device.  *out receives the handle; the

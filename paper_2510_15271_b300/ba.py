@@ -47,7 +47,9 @@ class Options(Structure):
                 ("serve_slots", c_int), ("serve_queue", c_int), ("profile", c_int),
                 ("pcg_variant", c_int), ("mu_min", c_double),
                 ("serve_tick_ms", c_double),
-                ("serve_split_ms", c_double)]
+                ("serve_split_ms", c_double),
+                ("prior_seq_weight", c_double),
+                ("prior_abs_weight", c_double)]
 
 
 class Intrinsics(Structure):

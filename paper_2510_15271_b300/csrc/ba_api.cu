@@ -137,11 +137,18 @@ void ba_options_default(ba_options* o) {
   o->mu_min = -1.0;
   o->serve_tick_ms = 4.0;
   o->serve_split_ms = 10.0;
+  o->prior_seq_weight = 0.0;
+  o->prior_abs_weight = 0.0;
 }
 
 static ba_status check_options(const ba_options* o, std::string& err) {
   if (o->precision != BA_FP64 && o->precision != BA_FP32) {
     err = "precision must be BA_FP64 or BA_FP32";
+    return BA_ERR_INVALID_ARG;
+  }
+  if (!(o->prior_seq_weight >= 0.0) || !isfinite(o->prior_seq_weight) ||
+      !(o->prior_abs_weight >= 0.0) || !isfinite(o->prior_abs_weight)) {
+    err = "prior_seq_weight and prior_abs_weight must be finite and >= 0";
     return BA_ERR_INVALID_ARG;
   }
   if (!isfinite(o->serve_tick_ms) || !isfinite(o->serve_split_ms)) {
@@ -311,6 +318,8 @@ ba_status ba_set_problem(ba_handle* h, int32_t n_cams, int32_t n_pts, int64_t n_
   d.K = Intrinsics{K->fx, K->fy, K->cx, K->cy};
   d.precision = prec;
   d.mu_min = h->opts.mu_min >= 0.0 ? h->opts.mu_min : (prec == BA_FP32 ? kMuMinFp32 : 0.0);
+  d.lam_c = h->opts.prior_seq_weight;
+  d.lam_a = h->opts.prior_abs_weight;
 
   // ---- validation and counts
   int32_t* cam_cnt = (int32_t*)tmp.get(C * sizeof(int32_t));
@@ -569,11 +578,19 @@ ba_status ba_set_problem(ba_handle* h, int32_t n_cams, int32_t n_pts, int64_t n_
       return BA_ERR_OOM;
     }
   }
+  if (priors_on(d) &&
+      (!keep(h, d.prior_anchor, (size_t)C * 12 * sizeof(double)) ||
+       !keep(h, d.prior_meas, (size_t)std::max(C - 1, 1) * 12 * sizeof(double)))) {
+    h->err = "ba_set_problem: out of device memory (pose priors)";
+    free_problem(h);
+    return BA_ERR_OOM;
+  }
   CK(cudaMemsetAsync(d.barrier, 0, 64, s));
   CK(cudaMemsetAsync(d.lm, 0, sizeof(LmScalars), s));
   CK(cudaMemsetAsync(d.part, 0, kPartTotal * sizeof(double), s));
   CK(cudaMemsetAsync(d.rep.cost, 0, (BA_MAX_ITERS + 1) * sizeof(double), s));
   launch_init_cams(C, d_qt, d.R, d.t, d.Cc, d.cam32, s);
+  if (priors_on(d)) launch_prior_setup(d, s);  // measured on the given state
   CK(cudaMemcpyAsync(d.X, d_pts, (size_t)P * 3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
   if (d.X32) launch_split_points(P, d.X, d.X32, s);
   if (d.cam32b) CK(cudaMemcpyAsync(d.cam32b, d.cam32, (size_t)C * kCam32 * sizeof(float), cudaMemcpyDeviceToDevice, s));

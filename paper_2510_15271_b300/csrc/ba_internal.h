@@ -70,6 +70,10 @@ struct DevProblem {
   int precision = BA_FP64;
   int n_fixed = 0;
   double mu_min = 0.0;  // floor of the damping used in the linear system
+  // pose priors (weights > 0): measurements on the state given to ba_set_problem
+  double lam_c = 0.0, lam_a = 0.0;  // sequential, absolute
+  double* prior_anchor = nullptr;   // [C][12] T_wc top rows of the initial poses
+  double* prior_meas = nullptr;     // [C - 1][12] initial relative poses T_cw,i+1 T_wc,i
   // state (FP64) and trial state
   double *R = nullptr, *t = nullptr, *Cc = nullptr, *X = nullptr;
   double *R2 = nullptr, *t2 = nullptr, *Cc2 = nullptr, *X2 = nullptr;
@@ -178,5 +182,6 @@ constexpr int kPartCost = 0;
 constexpr int kPartDl = kCostParts;
 constexpr int kPartPcg = kCostParts + kDlParts;
 constexpr int kPartMisc = kCostParts + kDlParts + kPcgParts;
+constexpr int kPriorParts = 16;  // prior-cost partial sums at kPartMisc (of 64)
 
 }  // namespace ba

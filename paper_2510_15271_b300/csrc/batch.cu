@@ -831,6 +831,10 @@ ba_status check_batch_args(ba_handle* h, int32_t n, const ba_problem* pr, ba_res
     h->err = "ba_solve_batch: max_lm_iters out of range";
     return BA_ERR_INVALID_ARG;
   }
+  if (h->opts.prior_seq_weight > 0.0 || h->opts.prior_abs_weight > 0.0) {
+    h->err = "ba_solve_batch: pose priors are supported by ba_solve only";
+    return BA_ERR_INVALID_ARG;
+  }
   ba_status st = BA_OK;
   for (int i = 0; i < n; ++i) {
     memset(&res[i], 0, sizeof(res[i]));

@@ -310,7 +310,7 @@ __global__ void k_pattern(int C, const int32_t* __restrict__ cam_ptr,
                           const int32_t* __restrict__ oc_pt, const int32_t* __restrict__ pt_ptr,
                           const int32_t* __restrict__ po_cam, int32_t* __restrict__ row_nnz,
                           const int32_t* __restrict__ rowptr, int32_t* __restrict__ col,
-                          int32_t* __restrict__ diag, int fill) {
+                          int32_t* __restrict__ diag, int fill, int seq) {
   extern __shared__ uint32_t bits[];
   __shared__ int32_t wt[33];
   const int i = blockIdx.x;
@@ -324,7 +324,13 @@ __global__ void k_pattern(int C, const int32_t* __restrict__ cam_ptr,
       atomicOr(&bits[c >> 5], 1u << (c & 31));
     }
   }
-  if (threadIdx.x == 0) atomicOr(&bits[i >> 5], 1u << (i & 31));
+  if (threadIdx.x == 0) {
+    atomicOr(&bits[i >> 5], 1u << (i & 31));
+    if (seq) {  // the sequential pose prior couples adjacent cameras
+      if (i > 0) atomicOr(&bits[(i - 1) >> 5], 1u << ((i - 1) & 31));
+      if (i + 1 < C) atomicOr(&bits[(i + 1) >> 5], 1u << ((i + 1) & 31));
+    }
+  }
   __syncthreads();
   // each thread owns a contiguous range of words
   const int per = (nw + blockDim.x - 1) / blockDim.x;
@@ -439,7 +445,7 @@ void launch_pattern(const DevProblem& d, int32_t* row_nnz, const int32_t* rowptr
   if (sm > 48 * 1024)
     cudaFuncSetAttribute(k_pattern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_pattern<<<d.C, 256, sm, s>>>(d.C, d.cam_ptr, d.oc_pt, d.pt_ptr, d.po_cam, row_nnz, rowptr,
-                                 d.s_col, d.s_diag, fill);
+                                 d.s_col, d.s_diag, fill, d.lam_c > 0.0 ? 1 : 0);
 }
 
 void launch_init_cams(int C, const double* qt, double* R, double* t, double* Cc, float* cam32,

@@ -60,6 +60,13 @@ struct SolveConfig {
 void mark(const SolveConfig& cfg, int k, cudaStream_t s);
 
 int cost_blocks(const DevProblem& d);
+// pose priors (priors.cu)
+bool priors_on(const DevProblem& d);
+int prior_blocks(const DevProblem& d);  // partial sums of the prior cost (0 when off)
+void launch_prior_setup(const DevProblem& d, cudaStream_t s);
+void launch_prior_lin(const DevProblem& d, cudaStream_t s);
+void launch_prior_coupling(const DevProblem& d, cudaStream_t s);
+void launch_prior_cost(const DevProblem& d, int trial, cudaStream_t s);
 int backsub_blocks(const DevProblem& d);
 int retract_blocks(const DevProblem& d);
 size_t schur_smem(int precision, int colcap, int max_subs);

@@ -657,8 +657,9 @@ __device__ double block_strided_sum(const double* __restrict__ p, int n, int str
   return tot;
 }
 
-__global__ void k_lm_init(DevProblem d, int ncost, double mu0, int iters) {
-  const double F = block_strided_sum(d.part, ncost, 1, kPartCost);
+__global__ void k_lm_init(DevProblem d, int ncost, int nprior, double mu0, int iters) {
+  const double F = block_strided_sum(d.part, ncost, 1, kPartCost) +
+                   block_strided_sum(d.part, nprior, 1, kPartMisc);
   if (threadIdx.x != 0) return;
   LmScalars* lm = d.lm;
   lm->F = F;
@@ -678,8 +679,9 @@ __global__ void k_lm_init(DevProblem d, int ncost, double mu0, int iters) {
   d.rep.cost[0] = F;
 }
 
-__global__ void k_gain(DevProblem d, int ncost, int ndl_pt, int ndl_cam) {
-  const double Fn = block_strided_sum(d.part, ncost, 1, kPartCost);
+__global__ void k_gain(DevProblem d, int ncost, int nprior, int ndl_pt, int ndl_cam) {
+  const double Fn = block_strided_sum(d.part, ncost, 1, kPartCost) +
+                    block_strided_sum(d.part, nprior, 1, kPartMisc);
   const double hp = block_strided_sum(d.part, ndl_pt, 1, kPartDl);
   const double hc = block_strided_sum(d.part, ndl_cam, 1, kPartDl + kDlParts / 2);
   if (threadIdx.x != 0) return;
@@ -797,6 +799,7 @@ static void lm_iteration_t(const DevProblem& d, const SolveConfig& cfg, cudaStre
   const T delta = (T)cfg.huber_delta;
   const unsigned gp = grid_cap(d.P, 256, 148 * 8);
   k_lin_cam<T, 256><<<d.C, 256, 0, s>>>(d, delta);
+  launch_prior_lin(d, s);  // pose priors into U and g_c (none when off)
   mark(cfg, kKLinCam, s);
   k_lin_pt<T><<<gp, 256, 0, s>>>(d, delta);
   mark(cfg, kKLinPt, s);
@@ -804,6 +807,7 @@ static void lm_iteration_t(const DevProblem& d, const SolveConfig& cfg, cudaStre
   mark(cfg, kKDampPt, s);
   const size_t sm = schur_smem_bytes<T>(cfg.schur_colcap, d.max_chunk_subs);
   k_schur<T, 256><<<d.C, 256, sm, s>>>(d, cfg.schur_colcap);
+  launch_prior_coupling(d, s);  // adjacent cameras' prior blocks into S
   mark(cfg, kKSchur, s);
   launch_linear_solve(d, cfg, s);
   mark(cfg, kKSolve, s);
@@ -812,8 +816,10 @@ static void lm_iteration_t(const DevProblem& d, const SolveConfig& cfg, cudaStre
   k_retract<T><<<retract_blocks(d), 128, 0, s>>>(d);
   mark(cfg, kKRetract, s);
   k_cost<T><<<cost_blocks(d), 256, 0, s>>>(d, 1, delta, 0);
+  launch_prior_cost(d, 1, s);
   mark(cfg, kKCost, s);
-  k_gain<<<1, 256, 0, s>>>(d, cost_blocks(d), backsub_blocks(d), retract_blocks(d));
+  k_gain<<<1, 256, 0, s>>>(d, cost_blocks(d), prior_blocks(d), backsub_blocks(d),
+                          retract_blocks(d));
   mark(cfg, kKGain, s);
   k_commit<<<grid_cap(d.C > d.P ? d.C : d.P, 256, 148 * 8), 256, 0, s>>>(d);
   mark(cfg, kKCommit, s);
@@ -822,8 +828,9 @@ static void lm_iteration_t(const DevProblem& d, const SolveConfig& cfg, cudaStre
 template <typename T>
 static void lm_begin_t(const DevProblem& d, const SolveConfig& cfg, cudaStream_t s) {
   k_cost<T><<<cost_blocks(d), 256, 0, s>>>(d, 0, (T)cfg.huber_delta, 0);
+  launch_prior_cost(d, 0, s);
   mark(cfg, kKCostBegin, s);
-  k_lm_init<<<1, 256, 0, s>>>(d, cost_blocks(d), cfg.mu0, cfg.iters);
+  k_lm_init<<<1, 256, 0, s>>>(d, cost_blocks(d), prior_blocks(d), cfg.mu0, cfg.iters);
   mark(cfg, kKLmInit, s);
 }
 

@@ -657,7 +657,8 @@ ba_status ba_create_server(const ba_options* opts, ba_handle** out) {
   ba_status st = ba_create(opts, &h);
   if (st != BA_OK) return st;
   if (opts->serve_slots < 1 || opts->serve_slots > 65536 || opts->serve_queue < 1 ||
-      opts->max_lm_iters < 1 || opts->max_lm_iters > BA_MAX_ITERS) {
+      opts->max_lm_iters < 1 || opts->max_lm_iters > BA_MAX_ITERS ||
+      opts->prior_seq_weight > 0.0 || opts->prior_abs_weight > 0.0) {
     ba_destroy(h);
     *out = nullptr;
     return BA_ERR_INVALID_ARG;

@@ -55,7 +55,7 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
         "sizeof(ba_problem), sizeof(ba_result), sizeof(ba_intrinsics));\n"
         'printf("%zu %zu %zu %zu %zu\\n", offsetof(ba_options, cuda_stream), '
         "offsetof(ba_options, serve_arena_bytes), offsetof(ba_report, rmse_px), "
-        "offsetof(ba_problem, K), offsetof(ba_options, serve_split_ms));\n"
+        "offsetof(ba_problem, K), offsetof(ba_options, prior_abs_weight));\n"
         "return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)],
@@ -68,7 +68,7 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
                      ctypes.sizeof(ba.Intrinsics)]
     assert offs == [ba.Options.cuda_stream.offset, ba.Options.serve_arena_bytes.offset,
                     ba.Report.rmse_px.offset, ba.Problem.K.offset,
-                    ba.Options.serve_split_ms.offset]
+                    ba.Options.prior_abs_weight.offset]
 
 
 def test_option_defaults(built):
@@ -77,6 +77,7 @@ def test_option_defaults(built):
     assert o.pcg_tol == 1e-6 and o.mu0 == 1e-4 and o.use_graph == 1 and o.refine_max == 5
     assert o.mu_min == -1.0 and o.pcg_variant == 0 and o.serve_tick_ms == 4.0
     assert o.serve_split_ms == 10.0
+    assert o.prior_seq_weight == 0.0 and o.prior_abs_weight == 0.0
 
 
 def test_invalid_calls_fail_cleanly_without_a_device(built):
