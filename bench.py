@@ -640,6 +640,36 @@ def run_outer(args, s, local_rank, peak):
     }
 
 
+def run_priors(args, s, local_rank):
+    """The driving solve with both pose priors on (sequential Sec. 4.2 Eq.
+    seq, absolute Sec. 4.3 Eq. abs; weights 3e3 and 50), FP32 path, from the
+    same start each step: obs*iters/s, the per-iteration kernel time it adds
+    and the PCG iterations (the trajectory differs from the prior-free one)."""
+    from paper_2510_15271_b300 import ba
+    lam_c, lam_a = 3e3, 50.0
+    o = ba.options_for_scene(s, "fp32", device=local_rank, prior_seq_weight=lam_c,
+                             prior_abs_weight=lam_a, profile=1)
+    ms, reps = [], []
+    with ba.ba_create(o) as h:
+        ba.ba_set_problem(h, s.cam_qt, s.pts, s.obs_cam, s.obs_pt, s.obs_uv, s.intrinsics(),
+                          s.cam_fixed)
+        for k in range(max(3, args.warmup) + args.steps):
+            ba.ba_set_state(h, s.cam_qt, s.pts)
+            rep = ba.ba_solve(h)
+            if k >= max(3, args.warmup):
+                ms.append(rep["solve_ms"])
+                reps.append(rep)
+        st = ba.ba_kernel_stats(h)
+    mean_ms = float(np.mean(ms))
+    return {"workload": f"driving, pose priors lambda_c {lam_c:g}, lambda_a {lam_a:g}",
+            "value": s.n_obs * s.lm_iters / (mean_ms * 1e-3), "unit": UNIT,
+            "ms_per_step": round(mean_ms, 3),
+            "pcg_iters": int(np.sum(reps[-1]["pcg_iters"])),
+            "final_cost": float(reps[-1]["costs"][-1]),
+            "kernels_ms": {k: round(v[1], 3) for k, v in st.items()
+                           if k in ("lin_cam", "schur", "pcg", "cost_trial")}}
+
+
 # --------------------------------------------------------------------------- reference arm
 
 def run_reference(args):
@@ -706,6 +736,7 @@ def main():
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-outer", action="store_true",
                     help="skip the reprojection-error / triangulation leg")
+    ap.add_argument("--no-priors", action="store_true", help="skip the pose-prior leg")
     ap.add_argument("--windows", type=int, default=512)
     ap.add_argument("--batch-schedule", default="",
                     help="threads,ctas_per_sm for the batched solver instead of the autotuner")
@@ -769,6 +800,8 @@ def main():
         line["batched"] = run_batched(args, 0)
     if not args.no_outer:
         line["outer_loop"] = run_outer(args, s, 0, peak)
+    if not args.no_priors and args.workload == "driving":
+        line["pose_priors"] = run_priors(args, s, 0)
     if not args.no_served:
         line["served"] = run_served(args, 0)
         line["local_ba_p50_ms"] = line["served"]["p50_ms"]
