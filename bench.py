@@ -670,6 +670,55 @@ def run_priors(args, s, local_rank):
                            if k in ("lin_cam", "schur", "pcg", "cost_trial")}}
 
 
+def run_pose_graph(args, local_rank):
+    """Pose-graph optimisation (Sec. 4.2) of the synthetic rig graph: 3,000
+    frames x 3 cameras (9,000 nodes), sequential (k = 1, 2), rig and
+    loop-closure edges, from the dead-reckoned start each step; FP32 system
+    and PCG (tol 1e-6, max 100) and the FP64 path; edges*iters/s.  With the
+    CPU legs on, the FP64 oracle's time for one LM iteration on the same
+    graph (sparse direct solve) on the host cores."""
+    from paper_2510_15271_b300 import ba, pose_graphs
+    s = pose_graphs.make_pose_graph()
+    out = {"workload": f"rig pose graph: {s.n_frames} frames x {s.rig} cameras = {s.n_nodes} "
+                       f"nodes, {s.n_edges} edges "
+                       f"({int(np.sum(s.edge_kind == pose_graphs.EDGE_LOOP))} loop closures), "
+                       f"{s.lm_iters} LM iterations, PCG tol 1e-6 / max 100",
+           "unit": "edges*iters/s"}
+    for prec in ("fp32", "fp64"):
+        o = ba.ba_options_default(precision=ba.BA_FP32 if prec == "fp32" else ba.BA_FP64,
+                                  solver=ba.BA_SOLVER_PCG, max_lm_iters=s.lm_iters,
+                                  device=local_rank)
+        ms, reps = [], []
+        with ba.ba_pg_create(o) as g:
+            for k in range(max(3, args.warmup) + args.steps):
+                ba.ba_pg_set_graph(g, s.node_qt_init, s.edge_ij, s.edge_qt, s.edge_w, s.fixed)
+                rep = ba.ba_pg_solve(g)
+                if k >= max(3, args.warmup):
+                    ms.append(rep["solve_ms"])
+                    reps.append(rep)
+        mean_ms = float(np.mean(ms))
+        pcg = int(np.sum(reps[-1]["pcg_iters"]))
+        out[prec] = {"value": s.n_edges * s.lm_iters / (mean_ms * 1e-3),
+                     "ms_per_step": round(mean_ms, 3), "pcg_iters": pcg,
+                     "us_per_lm_iter": round(1e3 * mean_ms / s.lm_iters, 1),
+                     "initial_cost": float(reps[-1]["costs"][0]),
+                     "final_cost": float(reps[-1]["costs"][-1]),
+                     "accepted": int(reps[-1]["n_accepted"]),
+                     "gpu_launches_per_step": int(reps[-1]["n_kernels"])}
+    out["value"] = out["fp32"]["value"]
+    if not args.no_cpu:
+        from oracle import pose_graph as PG   # the CPU comparison only
+        pg = PG.pose_graph_from_arrays(s.n_nodes, s.edge_ij, s.edge_qt, s.edge_w, s.fixed)
+        R, t = PG._qt_to_rt(s.node_qt_init)
+        t0 = time.perf_counter()
+        PG.pg_lm_solve(pg, R, t, PG.PGOptions(lm_iters=1, solver="sparse"))
+        dt = time.perf_counter() - t0
+        out["cpu_oracle"] = {"value": s.n_edges / dt, "unit": "edges*iters/s",
+                             "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                             "sample": "one LM iteration on the same graph, sparse direct solve"}
+    return out
+
+
 # --------------------------------------------------------------------------- reference arm
 
 def run_reference(args):
@@ -737,6 +786,7 @@ def main():
     ap.add_argument("--no-outer", action="store_true",
                     help="skip the reprojection-error / triangulation leg")
     ap.add_argument("--no-priors", action="store_true", help="skip the pose-prior leg")
+    ap.add_argument("--no-pgo", action="store_true", help="skip the pose-graph leg")
     ap.add_argument("--windows", type=int, default=512)
     ap.add_argument("--batch-schedule", default="",
                     help="threads,ctas_per_sm for the batched solver instead of the autotuner")
@@ -802,6 +852,8 @@ def main():
         line["outer_loop"] = run_outer(args, s, 0, peak)
     if not args.no_priors and args.workload == "driving":
         line["pose_priors"] = run_priors(args, s, 0)
+    if not args.no_pgo:
+        line["pose_graph"] = run_pose_graph(args, 0)
     if not args.no_served:
         line["served"] = run_served(args, 0)
         line["local_ba_p50_ms"] = line["served"]["p50_ms"]

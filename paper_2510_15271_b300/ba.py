@@ -139,6 +139,14 @@ _SIGNATURES = {
     "ba_triangulate": (c_int, [c_int32, c_void_p, c_int32, c_int32, c_int64, c_void_p, c_void_p,
                                c_void_p, c_void_p, POINTER(Intrinsics), c_void_p, c_void_p,
                                c_void_p, c_int32]),
+    # pose-graph optimisation (ba_pose_graph.h)
+    "ba_pg_create": (c_int, [POINTER(Options), POINTER(c_void_p)]),
+    "ba_pg_set_graph": (c_int, [c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_void_p,
+                                c_void_p, c_void_p, c_int]),
+    "ba_pg_solve": (c_int, [c_void_p, POINTER(Report)]),
+    "ba_pg_get_state": (c_int, [c_void_p, c_void_p, c_int]),
+    "ba_pg_last_error": (c_char_p, [c_void_p]),
+    "ba_pg_destroy": (None, [c_void_p]),
 }
 
 EXPORTS = tuple(_SIGNATURES)
@@ -321,6 +329,89 @@ def ba_kernel_stats(h: Handle) -> dict:
     n = c_int32()
     _check(lib().ba_kernel_stats(h.ptr, arr, 32, ctypes.byref(n)), h.ptr)
     return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms) for i in range(n.value)}
+
+
+# --------------------------------------------------------------------------- pose graphs
+
+class PoseGraphHandle:
+    """Owns one ba_pose_graph."""
+
+    def __init__(self, ptr, keep=()):
+        self.ptr = ptr
+        self._keep = keep
+
+    def close(self):
+        if self.ptr:
+            lib().ba_pg_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def _pg_check(status, g):
+    if status != BA_OK:
+        msg = lib().ba_pg_last_error(g)
+        raise BAError(status, msg.decode() if msg else "")
+
+
+def ba_pg_create(opts: Optional[Options] = None, use_torch: bool = False,
+                 **kw) -> PoseGraphHandle:
+    """Create a pose-graph solver; use_torch as for ba_create."""
+    o = opts if opts is not None else ba_options_default()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    keep = ()
+    if use_torch:
+        import torch
+        mem = _TorchMemory(o.device)
+        o.alloc = mem.alloc
+        o.free_fn = mem.free
+        o.cuda_stream = torch.cuda.current_stream(o.device).cuda_stream
+        keep = (mem,)
+    g = c_void_p()
+    _pg_check(lib().ba_pg_create(ctypes.byref(o), ctypes.byref(g)), None)
+    return PoseGraphHandle(g, keep)
+
+
+def ba_pg_set_graph(g: PoseGraphHandle, node_qt, edge_ij, edge_qt, edge_w, node_fixed=None):
+    """Load a graph from host arrays: node_qt (n, 7), edge_ij (E, 2), edge_qt
+    (E, 7) measured pose of node i in node j, edge_w (E,), node_fixed (n,)."""
+    q = _host(node_qt, np.float64).reshape(-1, 7)
+    ij = _host(edge_ij, np.int32).reshape(-1, 2)
+    eq = _host(edge_qt, np.float64).reshape(-1, 7)
+    w = _host(edge_w, np.float64).reshape(-1)
+    fx = None if node_fixed is None else _host(node_fixed, np.uint8)
+    st = lib().ba_pg_set_graph(g.ptr, q.shape[0], q.ctypes.data, ij.shape[0], ij.ctypes.data,
+                               eq.ctypes.data, w.ctypes.data,
+                               None if fx is None else fx.ctypes.data, BA_MEM_HOST)
+    _pg_check(st, g.ptr)
+
+
+def ba_pg_solve(g: PoseGraphHandle) -> dict:
+    r = Report()
+    st = lib().ba_pg_solve(g.ptr, ctypes.byref(r))
+    _pg_check(st, g.ptr)
+    return r.as_dict()
+
+
+def ba_pg_get_state(g: PoseGraphHandle, n_nodes: int) -> np.ndarray:
+    q = np.empty((n_nodes, 7))
+    _pg_check(lib().ba_pg_get_state(g.ptr, q.ctypes.data, BA_MEM_HOST), g.ptr)
+    return q
+
+
+def ba_pg_destroy(g: PoseGraphHandle):
+    g.close()
 
 
 # --------------------------------------------------------------------------- batch / serve

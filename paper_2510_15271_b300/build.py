@@ -24,7 +24,7 @@ def _sources():
 
 def _deps():
     return _sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(
-        os.path.join(CSRC, "*.cuh")) + [os.path.join(ROOT, "include", "ba.h")]
+        os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
 
 
 def up_to_date() -> bool:

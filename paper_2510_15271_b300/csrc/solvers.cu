@@ -898,6 +898,8 @@ static const void* pcg_fn_p(bool smem, int rw) {
     switch (rw) {
       case 1: return (const void*)k_pcg<T, kPcgThreads, true, 1, PIPE>;
       case 2: return (const void*)k_pcg<T, kPcgThreads, true, 2, PIPE>;
+      case 4: return (const void*)k_pcg<T, kPcgThreads, true, 4, PIPE>;
+      case 8: return (const void*)k_pcg<T, kPcgThreads, true, 8, PIPE>;
       default: return nullptr;
     }
   }
@@ -931,6 +933,40 @@ static int pcg_occupancy(const void* fn, size_t smem) {
 // rows of S held in shared memory (with the list of columns they reference)
 // when they fit.  Returns false if the problem has more rows than the kernel
 // variants cover.
+// Per-CTA column lists of G CTAs of R contiguous rows each; returns the most
+// blocks and the most distinct columns of one CTA.
+static void pcg_lists(int G, int R, const std::vector<int32_t>& rowptr,
+                      const std::vector<int32_t>& col, PcgPlan& plan, int& maxnnz, int& maxu) {
+  const int C = (int)rowptr.size() - 1;
+  plan.ucol.clear();
+  plan.uptr.assign(G + 1, 0);
+  plan.lcol.assign(col.size(), 0);
+  plan.lown.assign(C, 0);
+  maxnnz = 0;
+  maxu = 0;
+  std::vector<int32_t> cols;
+  for (int b = 0; b < G; ++b) {
+    const int r0 = std::min(C, b * R), r1 = std::min(C, r0 + R);
+    maxnnz = std::max(maxnnz, rowptr[r1] - rowptr[r0]);
+    cols.assign(col.begin() + rowptr[r0], col.begin() + rowptr[r1]);
+    std::sort(cols.begin(), cols.end());
+    cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+    plan.uptr[b] = (int32_t)plan.ucol.size();
+    plan.ucol.insert(plan.ucol.end(), cols.begin(), cols.end());
+    maxu = std::max(maxu, (int)cols.size());
+    for (int k = rowptr[r0]; k < rowptr[r1]; ++k)
+      plan.lcol[k] = (int32_t)(std::lower_bound(cols.begin(), cols.end(), col[k]) - cols.begin());
+    for (int i = r0; i < r1; ++i)
+      plan.lown[i] = (int32_t)(std::lower_bound(cols.begin(), cols.end(), i) - cols.begin());
+  }
+  plan.uptr[G] = (int32_t)plan.ucol.size();
+}
+
+static size_t pcg_smem_need(int precision, int maxnnz, int R, int maxu) {
+  return precision == BA_FP32 ? pcg_smem_bytes<float>(maxnnz, R, maxu)
+                              : pcg_smem_bytes<double>(maxnnz, R, maxu);
+}
+
 bool plan_pcg(int precision, int device, const std::vector<int32_t>& rowptr,
               const std::vector<int32_t>& col, size_t smem_limit, SolveConfig& cfg,
               PcgPlan& plan) {
@@ -938,6 +974,34 @@ bool plan_pcg(int precision, int device, const std::vector<int32_t>& rowptr,
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   const bool pipe = cfg.pcg_pipelined != 0;
+  int maxnnz = 0, maxu = 0;
+  // Many short rows (a pose graph: about 7 blocks per row): one warp per row
+  // would launch a CTA per 8 rows, and every iteration's grid barrier takes
+  // one arrival per CTA while every CTA reads every CTA's partial sums (G^2
+  // loads).  Try fewer CTAs with several rows per warp first (2, then 1 per
+  // SM), kept when the rows of S still fit in shared memory.
+  if ((C + kPcgWarps - 1) / kPcgWarps > 2 * sms) {
+    for (int Gt : {2 * sms, sms}) {
+      int R = (C + Gt - 1) / Gt;
+      const int G = (C + R - 1) / R;
+      int rw = 1;
+      while (rw * kPcgWarps < R) rw *= 2;
+      const void* fs = pcg_fn_prec(precision, true, rw, pipe);
+      if (!fs) continue;
+      pcg_lists(G, R, rowptr, col, plan, maxnnz, maxu);
+      const size_t need = pcg_smem_need(precision, maxnnz, R, maxu);
+      if (need > smem_limit) continue;
+      cudaFuncSetAttribute(fs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+      if (pcg_occupancy(fs, need) * sms < G) continue;
+      cfg.pcg_blocks = G;
+      cfg.pcg_rows = R;
+      cfg.pcg_rw = rw;
+      cfg.pcg_maxnnz = maxnnz;
+      cfg.pcg_maxu = maxu;
+      cfg.pcg_smem = need;
+      return true;
+    }
+  }
   const int per_sm_plain = pcg_occupancy(pcg_fn_prec(precision, false, 1, pipe), 0);
   const int gmax = std::max(1, std::min(per_sm_plain * sms, 1024));
   int G = std::max(1, std::min(gmax, (C + kPcgWarps - 1) / kPcgWarps));
@@ -957,30 +1021,9 @@ bool plan_pcg(int precision, int device, const std::vector<int32_t>& rowptr,
     if (occ * sms >= G) break;
     if (occ < 1 || attempt >= 8) return false;
     G = occ * sms;
-  }  // per-CTA column lists
-  plan.ucol.clear();
-  plan.uptr.assign(G + 1, 0);
-  plan.lcol.assign(col.size(), 0);
-  plan.lown.assign(C, 0);
-  int maxnnz = 0, maxu = 0;
-  std::vector<int32_t> cols;
-  for (int b = 0; b < G; ++b) {
-    const int r0 = std::min(C, b * R), r1 = std::min(C, r0 + R);
-    maxnnz = std::max(maxnnz, rowptr[r1] - rowptr[r0]);
-    cols.assign(col.begin() + rowptr[r0], col.begin() + rowptr[r1]);
-    std::sort(cols.begin(), cols.end());
-    cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
-    plan.uptr[b] = (int32_t)plan.ucol.size();
-    plan.ucol.insert(plan.ucol.end(), cols.begin(), cols.end());
-    maxu = std::max(maxu, (int)cols.size());
-    for (int k = rowptr[r0]; k < rowptr[r1]; ++k)
-      plan.lcol[k] = (int32_t)(std::lower_bound(cols.begin(), cols.end(), col[k]) - cols.begin());
-    for (int i = r0; i < r1; ++i)
-      plan.lown[i] = (int32_t)(std::lower_bound(cols.begin(), cols.end(), i) - cols.begin());
   }
-  plan.uptr[G] = (int32_t)plan.ucol.size();
-  const size_t need = precision == BA_FP32 ? pcg_smem_bytes<float>(maxnnz, R, maxu)
-                                           : pcg_smem_bytes<double>(maxnnz, R, maxu);
+  pcg_lists(G, R, rowptr, col, plan, maxnnz, maxu);
+  const size_t need = pcg_smem_need(precision, maxnnz, R, maxu);
   bool smem = false;
   const void* fs = pcg_fn_prec(precision, true, rw, pipe);
   if (fs && need <= smem_limit) {

@@ -5,8 +5,9 @@ drives a route; every camera of every frame is a node.  A simulated
 relative-pose sensor measures, for each edge (i, j), the pose of camera i in
 camera j from the true poses (as 4 x 4 homogeneous matrices) and perturbs it
 with a small random rotation and translation.  The starting state is the
-true trajectory with accumulated odometry drift.  Nothing here evaluates a
-residual, a Jacobian or a cost of the solver.
+dead-reckoned trajectory: the true frame-to-frame motion of the vehicle with
+a small random error per step, composed from the first frame.  Nothing here
+evaluates a residual, a Jacobian or a cost of the solver.
 
 Edges, as the three constraint kinds of cuSfM's pose graph (Sec. 4.2):
   * sequential: camera c of frame f and of frame f + k, k = 1 .. seq_k;
@@ -124,15 +125,15 @@ def make_pose_graph(seed: int = 7, n_frames: int = 3000, rig: int = 3, *, spacin
     # true node poses (world -> camera), node = f * rig + c
     T_vw = np.linalg.inv(T_wv)
     T_cw = np.einsum("cab,fbd->fcad", T_cv, T_vw).reshape(-1, 4, 4)
-    # drifted start: odometry drift accumulated along the route
-    steps = _noisy(rng, np.broadcast_to(np.eye(4), (n_frames, 4, 4)).copy(), drift_rot,
+    # drifted start: dead reckoning, the true frame-to-frame motion of the
+    # vehicle composed with a small random error in the vehicle frame per step
+    noise = _noisy(rng, np.broadcast_to(np.eye(4), (n_frames, 4, 4)).copy(), drift_rot,
                    drift_pos)
-    drift = np.empty_like(steps)
-    acc = np.eye(4)
-    for f in range(n_frames):
-        acc = acc @ steps[f]
-        drift[f] = acc
-    T_wv0 = np.einsum("fab,fbc->fac", drift, T_wv)
+    T_wv0 = np.empty_like(T_wv)
+    T_wv0[0] = T_wv[0]
+    for f in range(1, n_frames):
+        step = np.linalg.inv(T_wv[f - 1]) @ T_wv[f]
+        T_wv0[f] = T_wv0[f - 1] @ step @ noise[f]
     T_cw0 = np.einsum("cab,fbd->fcad", T_cv, np.linalg.inv(T_wv0)).reshape(-1, 4, 4)
     # edges
     ei, ej, kind, sig = [], [], [], []

@@ -1,5 +1,6 @@
 """Host checks of the C ABI: the library loads, exports every function that
-include/ba.h declares, and its structs have the layout the binding assumes.
+the headers under include/ declare, and its structs have the layout the
+binding assumes.
 No compute call is made (no GPU needed)."""
 import ctypes
 import os
@@ -11,7 +12,7 @@ import pytest
 from paper_2510_15271_b300 import ba
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "ba.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("ba.h", "ba_pose_graph.h")]
 
 
 @pytest.fixture(scope="module")
@@ -22,7 +23,7 @@ def built():
 
 
 def _declared_functions():
-    src = open(HEADER).read()
+    src = "".join(open(h).read() for h in HEADERS)
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     names = re.findall(r"^\s*(?:ba_status|void|const char\s*\*)\s+(ba_\w+)\s*\(", src, flags=re.M)
     return sorted(set(names))
@@ -31,7 +32,8 @@ def _declared_functions():
 def test_header_declares_the_boundary_calls():
     names = _declared_functions()
     for required in ("ba_create", "ba_set_problem", "ba_solve", "ba_get_state", "ba_submit",
-                     "ba_poll", "ba_destroy", "ba_solve_batch", "ba_last_error"):
+                     "ba_poll", "ba_destroy", "ba_solve_batch", "ba_last_error",
+                     "ba_pg_create", "ba_pg_set_graph", "ba_pg_solve", "ba_pg_get_state"):
         assert required in names
 
 
