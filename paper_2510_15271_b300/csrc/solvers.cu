@@ -483,45 +483,94 @@ __device__ int pcg_solve(const DevProblem& d, const RowSet<T>& rs, const T* __re
   return k;
 }
 
+// Sum over the CTA of FP64 values held by every thread (the lane-dense
+// recurrence below) into slot[blockIdx.x * stride + k]: a butterfly in the
+// warps that hold terms (the others contribute zeros without shuffling), then
+// warp 0 over the warps' sums; a fixed order, so every launch sums alike.
+template <int NT, int NV>
+__device__ __forceinline__ void cta_partials_dense(double (&v)[NV], double* red, double* slot,
+                                                   int stride, bool warp_has_terms) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp_has_terms) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) red[warp * NV + k] = warp_has_terms ? v[k] : 0.0;
+  }
+  __syncthreads();
+  constexpr int NW = NT / 32;
+  static_assert((NW & (NW - 1)) == 0 && NW * NV <= 32, "warp count a power of two");
+  if (warp == 0) {
+    const int k = lane / NW, w = lane % NW;
+    double s = k < NV ? red[w * NV + k] : 0.0;
+#pragma unroll
+    for (int o = NW / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (k < NV && w == 0) slot[blockIdx.x * stride + k] = s;
+  }
+}
+
 // Pipelined PCG (Ghysels & Vanroose 2014, "Hiding global synchronization
 // latency in the preconditioned conjugate gradient algorithm", Alg. 3): the
 // same Krylov iterates as PCG in exact arithmetic, with the two dot products
 // of an iteration reduced together and overlapped with the product n = S m,
-// m = M w, so each iteration needs one grid barrier instead of two.  Lane
-// e < 6 of the owning warp keeps element e of x, r, u, w, z, q, s, p of its
-// rows in registers; m is exchanged through global memory (double-buffered).
-// Same stopping rule as pcg_solve (||r|| <= tol ||b||, at most max_iters
-// products with S after the initial one, stop if the curvature term is not
-// positive).
+// m = M w, so each iteration needs one grid barrier instead of two.
+//
+// The products with S run a warp per block row (lanes over the row's
+// blocks); everything else runs lane-dense: thread t of the CTA owns element
+// t % 6 of the CTA's local row t / 6 (and, with more than NT / 6 rows, also
+// element (t + NT) % 6 of row (t + NT) / 6), keeping x, r, u, w, z, q, s, p, m
+// of that element in FP64 registers.  FP64 issues at a small fraction of the
+// FP32 rate on this part, so a recurrence step costs one FP64 instruction
+// per 32 elements instead of one per block row.  Rows meet through shared
+// memory: the product's outputs (sn) and w (sw, for m = M w).  m is
+// exchanged between CTAs through global memory (double-buffered).  Same
+// stopping rule as pcg_solve (||r|| <= tol ||b||, at most max_iters products
+// with S after the initial one, stop if the curvature term is not positive).
 template <typename T, int NT, int RW, bool STAGED>
 __device__ int pcg_solve_pipelined(const DevProblem& d, const RowSet<T>& rs,
                                    const T* __restrict__ rhs, T* __restrict__ x, double tol,
                                    int max_iters, double* rel, int* err) {
-  __shared__ double red[(NT / 32) * 3];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int NW = NT / 32;
+  constexpr int RMAX = NW * RW;                  // rows a CTA can own
+  constexpr int ND = (6 * RMAX + NT - 1) / NT;   // elements per thread
+  __shared__ double red[NW * 3];
+  __shared__ double sw[6 * RMAX];  // w of the CTA's rows
+  __shared__ double sn[6 * RMAX];  // n = S m of the CTA's rows
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned nb = gridDim.x;
   T* mb[2] = {(T*)d.p0, (T*)d.p1};  // M w, exchanged
   T* ub = (T*)d.z;                  // u at the start, exchanged once
   double* partA = d.part + kPartPcg;  // [nb][3]
-  const int el = lane < 6 ? lane : 0;
+  const int nrow = rs.r1 - rs.r0;
+  const int nel = 6 * nrow;
+  const bool warp_has_terms = warp * 32 < nel || (ND > 1 && warp * 32 + NT < nel);
 
   // The recurrence vectors are FP64 on both paths (S, M and the exchanged
   // vectors stay in T): the pipelined recurrences drift in FP32.
-  double xr[RW], rr_[RW], ur[RW], wr[RW], zr[RW], qr[RW], sr[RW], pr[RW], mr[RW];
-  // r = rhs, u = M r (published for w = S u)
+  double xr[ND], rr_[ND], ur[ND], wr[ND], zr[ND], qr[ND], sr[ND], pr[ND], mr[ND];
+  // r = rhs; u = M r (published for w = S u)
 #pragma unroll
-  for (int m = 0; m < RW; ++m) {
-    const int i = rs.r0 + warp + m * NW;
-    xr[m] = rr_[m] = ur[m] = wr[m] = zr[m] = qr[m] = sr[m] = pr[m] = mr[m] = 0.0;
-    if (i >= rs.r1) continue;
-    const double ri = lane < 6 ? (double)rhs[6 * i + el] : 0.0;
-    rr_[m] = ri;
+  for (int j = 0; j < ND; ++j) {
+    const int t = threadIdx.x + j * NT;
+    xr[j] = rr_[j] = ur[j] = wr[j] = zr[j] = qr[j] = sr[j] = pr[j] = mr[j] = 0.0;
+    if (t < nel) {
+      rr_[j] = (double)rhs[6 * rs.r0 + t];
+      sw[t] = rr_[j];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < ND; ++j) {
+    const int t = threadIdx.x + j * NT;
+    if (t >= nel) continue;
+    const int lr = t / 6, e = t - 6 * lr;
     double ui = 0.0;
 #pragma unroll
-    for (int f = 0; f < 6; ++f) ui += rs.minv64(i, 6 * el + f) * __shfl_sync(0xffffffffu, ri, f);
-    ur[m] = ui;
-    if (lane < 6) ub[6 * i + el] = (T)ui;
+    for (int f = 0; f < 6; ++f) ui += rs.minv64(rs.r0 + lr, 6 * e + f) * sw[6 * lr + f];
+    ur[j] = ui;
+    ub[6 * rs.r0 + t] = (T)ui;
   }
   grid_barrier(d.barrier, nb, err);
   // w = S u
@@ -533,8 +582,18 @@ __device__ int pcg_solve_pipelined(const DevProblem& d, const RowSet<T>& rs,
     T wi[6];
     if (STAGED) row_spmv<T>(rs, i, [&](int idx) { return rs.sv[idx]; }, wi);
     else row_spmv<T>(rs, i, [&](int idx) { return ldcg(ub + idx); }, wi);
-    wr[m] = (double)pick6(wi, el);
+    if (lane < 6) sn[6 * (i - rs.r0) + lane] = (double)pick6(wi, lane);
   }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < ND; ++j) {
+    const int t = threadIdx.x + j * NT;
+    if (t < nel) {
+      wr[j] = sn[t];
+      sw[t] = wr[j];
+    }
+  }
+  __syncthreads();
   // scalars: thread 0 (FP64 is slow on this part), broadcast
   __shared__ double s_al, s_bt;
   __shared__ int s_go;
@@ -547,22 +606,20 @@ __device__ int pcg_solve_pipelined(const DevProblem& d, const RowSet<T>& rs,
     T* mo = mb[k & 1];
     double loc[3] = {0.0, 0.0, 0.0};
 #pragma unroll
-    for (int m = 0; m < RW; ++m) {
-      const int i = rs.r0 + warp + m * NW;
-      if (i >= rs.r1) continue;
-      const double wi = lane < 6 ? wr[m] : 0.0;
+    for (int j = 0; j < ND; ++j) {
+      const int t = threadIdx.x + j * NT;
+      if (t >= nel) continue;
+      const int lr = t / 6, e = t - 6 * lr;
       double mi = 0.0;
 #pragma unroll
-      for (int f = 0; f < 6; ++f) mi += rs.minv64(i, 6 * el + f) * __shfl_sync(0xffffffffu, wi, f);
-      mr[m] = mi;
-      if (lane < 6) {
-        mo[6 * i + el] = (T)mi;
-        loc[0] += rr_[m] * ur[m];
-        loc[1] += wr[m] * ur[m];
-        loc[2] += rr_[m] * rr_[m];
-      }
+      for (int f = 0; f < 6; ++f) mi += rs.minv64(rs.r0 + lr, 6 * e + f) * sw[6 * lr + f];
+      mr[j] = mi;
+      mo[6 * rs.r0 + t] = (T)mi;
+      loc[0] += rr_[j] * ur[j];
+      loc[1] += wr[j] * ur[j];
+      loc[2] += rr_[j] * rr_[j];
     }
-    cta_partials<NT, 3>(loc, red, partA, 3);
+    cta_partials_dense<NT, 3>(loc, red, partA, 3, warp_has_terms);
     grid_barrier(d.barrier, nb, err);
     // the next product's input (m of the listed columns) and the partial sums
     // are read together (all_partials ends with a CTA barrier)
@@ -598,7 +655,7 @@ __device__ int pcg_solve_pipelined(const DevProblem& d, const RowSet<T>& rs,
     __syncthreads();
     if (!s_go) break;
     const double bt = s_bt, al = s_al;
-    // n = S m (m staged above); recurrences
+    // n = S m (m staged above), a warp per row
 #pragma unroll
     for (int m = 0; m < RW; ++m) {
       const int i = rs.r0 + warp + m * NW;
@@ -606,22 +663,32 @@ __device__ int pcg_solve_pipelined(const DevProblem& d, const RowSet<T>& rs,
       T ni6[6];
       if (STAGED) row_spmv<T>(rs, i, [&](int idx) { return rs.sv[idx]; }, ni6);
       else row_spmv<T>(rs, i, [&](int idx) { return ldcg(mo + idx); }, ni6);
-      const double ni = (double)pick6(ni6, el);
-      zr[m] = ni + bt * zr[m];
-      qr[m] = mr[m] + bt * qr[m];
-      sr[m] = wr[m] + bt * sr[m];
-      pr[m] = ur[m] + bt * pr[m];
-      xr[m] = xr[m] + al * pr[m];
-      rr_[m] = rr_[m] - al * sr[m];
-      ur[m] = ur[m] - al * qr[m];
-      wr[m] = wr[m] - al * zr[m];
+      if (lane < 6) sn[6 * (i - rs.r0) + lane] = (double)pick6(ni6, lane);
     }
+    __syncthreads();
+    // recurrences, lane-dense
+#pragma unroll
+    for (int j = 0; j < ND; ++j) {
+      const int t = threadIdx.x + j * NT;
+      if (t >= nel) continue;
+      const double ni = sn[t];
+      zr[j] = ni + bt * zr[j];
+      qr[j] = mr[j] + bt * qr[j];
+      sr[j] = wr[j] + bt * sr[j];
+      pr[j] = ur[j] + bt * pr[j];
+      xr[j] = xr[j] + al * pr[j];
+      rr_[j] = rr_[j] - al * sr[j];
+      ur[j] = ur[j] - al * qr[j];
+      wr[j] = wr[j] - al * zr[j];
+      sw[t] = wr[j];
+    }
+    __syncthreads();
     ++k;
   }
 #pragma unroll
-  for (int m = 0; m < RW; ++m) {
-    const int i = rs.r0 + warp + m * NW;
-    if (i < rs.r1 && lane < 6) x[6 * i + el] = (T)xr[m];
+  for (int j = 0; j < ND; ++j) {
+    const int t = threadIdx.x + j * NT;
+    if (t < nel) x[6 * rs.r0 + t] = (T)xr[j];
   }
   // rr (and so *rel) is current in thread 0 only
   *rel = bnorm > 0.0 ? sqrt(rr) / bnorm : 0.0;
@@ -967,6 +1034,17 @@ static size_t pcg_smem_need(int precision, int maxnnz, int R, int maxu) {
                               : pcg_smem_bytes<double>(maxnnz, R, maxu);
 }
 
+// Static shared memory of a kernel variant (the pipelined recurrence's row
+// exchange grows with the rows per warp).
+static size_t static_smem(const void* fn) {
+  cudaFuncAttributes a{};
+  if (cudaFuncGetAttributes(&a, fn) != cudaSuccess) {
+    cudaGetLastError();
+    return 64 * 1024;
+  }
+  return a.sharedSizeBytes;
+}
+
 bool plan_pcg(int precision, int device, const std::vector<int32_t>& rowptr,
               const std::vector<int32_t>& col, size_t smem_limit, SolveConfig& cfg,
               PcgPlan& plan) {
@@ -990,7 +1068,7 @@ bool plan_pcg(int precision, int device, const std::vector<int32_t>& rowptr,
       if (!fs) continue;
       pcg_lists(G, R, rowptr, col, plan, maxnnz, maxu);
       const size_t need = pcg_smem_need(precision, maxnnz, R, maxu);
-      if (need > smem_limit) continue;
+      if (need + static_smem(fs) > smem_limit) continue;
       cudaFuncSetAttribute(fs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
       if (pcg_occupancy(fs, need) * sms < G) continue;
       cfg.pcg_blocks = G;
@@ -1026,7 +1104,7 @@ bool plan_pcg(int precision, int device, const std::vector<int32_t>& rowptr,
   const size_t need = pcg_smem_need(precision, maxnnz, R, maxu);
   bool smem = false;
   const void* fs = pcg_fn_prec(precision, true, rw, pipe);
-  if (fs && need <= smem_limit) {
+  if (fs && need + static_smem(fs) <= smem_limit) {
     cudaFuncSetAttribute(fs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
     smem = pcg_occupancy(fs, need) * sms >= G;
   }
