@@ -518,7 +518,8 @@ __device__ __forceinline__ void cta_partials_dense(double (&v)[NV], double* red,
 // m = M w, so each iteration needs one grid barrier instead of two.
 //
 // The products with S run a warp per block row (lanes over the row's
-// blocks); everything else runs lane-dense: thread t of the CTA owns element
+// blocks; inside the loop on warps 1.., while thread 0 computes the
+// iteration's scalars); everything else runs lane-dense: thread t of the CTA owns element
 // t % 6 of the CTA's local row t / 6 (and, with more than NT / 6 rows, also
 // element (t + NT) % 6 of row (t + NT) / 6), keeping x, r, u, w, z, q, s, p, m
 // of that element in FP64 registers.  FP64 issues at a small fraction of the
@@ -628,44 +629,45 @@ __device__ int pcg_solve_pipelined(const DevProblem& d, const RowSet<T>& rs,
     const int e_now = threadIdx.x == 0 ? ld_err(err) : 0;
     double tot[3];
     all_partials<3>(partA, 3, nb, tot);
-    if (threadIdx.x == 0) {
-      const double gamma = tot[0], delta = tot[1];
-      rr = tot[2];
-      if (bnorm < 0.0) {
-        bnorm = sqrt(rr);
-        thr2 = (tol * bnorm) * (tol * bnorm);
+    // thread 0 computes the scalars while warps 1.. form n = S m (m staged
+    // above; n does not depend on alpha or beta, and is simply unused when
+    // the loop stops): the FP64 divisions overlap the product
+    if (warp == 0) {
+      if (threadIdx.x == 0) {
+        const double gamma = tot[0], delta = tot[1];
+        rr = tot[2];
+        if (bnorm < 0.0) {
+          bnorm = sqrt(rr);
+          thr2 = (tol * bnorm) * (tol * bnorm);
+        }
+        int go = (k < max_iters && rr > thr2 && !e_now) ? 1 : 0;
+        double beta = 0.0, alpha = 0.0;
+        if (go) {
+          // alpha = gamma / (delta - beta gamma / alpha_prev), beta = gamma /
+          // gamma_prev (beta = 0 at k = 0); 1/alpha = denominator / gamma
+          const double inv_gamma = 1.0 / gamma;
+          if (k > 0) beta = gamma * inv_gamma_prev;
+          const double den = k > 0 ? delta - beta * gamma * inv_alpha_prev : delta;
+          alpha = gamma / den;
+          inv_gamma_prev = inv_gamma;
+          inv_alpha_prev = den * inv_gamma;
+          if (!(alpha > 0.0) || !isfinite(alpha)) go = 0;  // curvature not positive
+        }
+        s_go = go;
+        s_al = alpha;
+        s_bt = beta;
       }
-      int go = (k < max_iters && rr > thr2 && !e_now) ? 1 : 0;
-      double beta = 0.0, alpha = 0.0;
-      if (go) {
-        // alpha = gamma / (delta - beta gamma / alpha_prev), beta = gamma /
-        // gamma_prev (beta = 0 at k = 0); 1/alpha = denominator / gamma
-        const double inv_gamma = 1.0 / gamma;
-        if (k > 0) beta = gamma * inv_gamma_prev;
-        const double den = k > 0 ? delta - beta * gamma * inv_alpha_prev : delta;
-        alpha = gamma / den;
-        inv_gamma_prev = inv_gamma;
-        inv_alpha_prev = den * inv_gamma;
-        if (!(alpha > 0.0) || !isfinite(alpha)) go = 0;  // curvature not positive
+    } else {
+      for (int i = rs.r0 + warp - 1; i < rs.r1; i += NW - 1) {
+        T ni6[6];
+        if (STAGED) row_spmv<T>(rs, i, [&](int idx) { return rs.sv[idx]; }, ni6);
+        else row_spmv<T>(rs, i, [&](int idx) { return ldcg(mo + idx); }, ni6);
+        if (lane < 6) sn[6 * (i - rs.r0) + lane] = (double)pick6(ni6, lane);
       }
-      s_go = go;
-      s_al = alpha;
-      s_bt = beta;
     }
     __syncthreads();
     if (!s_go) break;
     const double bt = s_bt, al = s_al;
-    // n = S m (m staged above), a warp per row
-#pragma unroll
-    for (int m = 0; m < RW; ++m) {
-      const int i = rs.r0 + warp + m * NW;
-      if (i >= rs.r1) continue;
-      T ni6[6];
-      if (STAGED) row_spmv<T>(rs, i, [&](int idx) { return rs.sv[idx]; }, ni6);
-      else row_spmv<T>(rs, i, [&](int idx) { return ldcg(mo + idx); }, ni6);
-      if (lane < 6) sn[6 * (i - rs.r0) + lane] = (double)pick6(ni6, lane);
-    }
-    __syncthreads();
     // recurrences, lane-dense
 #pragma unroll
     for (int j = 0; j < ND; ++j) {
