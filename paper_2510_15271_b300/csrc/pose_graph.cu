@@ -421,6 +421,7 @@ struct ba_pose_graph {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   double setup_ms = 0.0;
   int launches = 0;
+  double* qt = nullptr;  // [n][7] device: the input poses, then ba_pg_get_state's output
 };
 
 namespace {
@@ -459,6 +460,7 @@ void pg_free(ba_pose_graph* g) {
   g->bufs.clear();
   g->d = DevProblem();
   g->p = PgDev();
+  g->qt = nullptr;
   g->loaded = false;
 }
 
@@ -763,6 +765,7 @@ ba_status ba_pg_set_graph(ba_pose_graph* g, int32_t n_nodes, const double* node_
     pg_free(g);
     return BA_ERR_OOM;
   }
+  g->qt = d_qt;
   cudaStream_t s = g->stream;
   std::vector<int32_t> hei(E), hej(E);
   for (int e = 0; e < E; ++e) {
@@ -963,15 +966,12 @@ ba_status ba_pg_get_state(const ba_pose_graph* gc, double* node_qt_out, int mem_
   }
   PG_CK(cudaSetDevice(g->device));
   const int n = g->d.C;
-  double* q = nullptr;
-  PG_CK(cudaMalloc(&q, (size_t)n * 7 * sizeof(double)));
-  launch_cams_to_qt(n, g->d.R, g->d.t, q, g->stream);
-  cudaError_t e = cudaMemcpyAsync(node_qt_out, q, (size_t)n * 7 * sizeof(double),
+  launch_cams_to_qt(n, g->d.R, g->d.t, g->qt, g->stream);
+  cudaError_t e = cudaMemcpyAsync(node_qt_out, g->qt, (size_t)n * 7 * sizeof(double),
                                   mem_kind == BA_MEM_HOST ? cudaMemcpyDeviceToHost
                                                           : cudaMemcpyDeviceToDevice,
                                   g->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
-  cudaFree(q);
   if (e != cudaSuccess) {
     g->err = std::string("ba_pg_get_state: ") + cudaGetErrorString(e);
     return BA_ERR_CUDA;
