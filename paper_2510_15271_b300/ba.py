@@ -147,6 +147,15 @@ _SIGNATURES = {
     "ba_pg_get_state": (c_int, [c_void_p, c_void_p, c_int]),
     "ba_pg_last_error": (c_char_p, [c_void_p]),
     "ba_pg_destroy": (None, [c_void_p]),
+    # rig BA with extrinsic refinement (ba_rig.h)
+    "ba_rig_create": (c_int, [POINTER(Options), POINTER(c_void_p)]),
+    "ba_rig_set_problem": (c_int, [c_void_p, c_int32, c_int32, c_int32, c_int64, c_void_p,
+                                   c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                   POINTER(Intrinsics), c_void_p, c_void_p]),
+    "ba_rig_solve": (c_int, [c_void_p, POINTER(Report)]),
+    "ba_rig_get_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ba_rig_last_error": (c_char_p, [c_void_p]),
+    "ba_rig_destroy": (None, [c_void_p]),
 }
 
 EXPORTS = tuple(_SIGNATURES)
@@ -412,6 +421,85 @@ def ba_pg_get_state(g: PoseGraphHandle, n_nodes: int) -> np.ndarray:
 
 def ba_pg_destroy(g: PoseGraphHandle):
     g.close()
+
+
+# --------------------------------------------------------------------------- rig BA
+
+class RigHandle:
+    """Owns one ba_rig."""
+
+    def __init__(self, ptr):
+        self.ptr = ptr
+        self.sizes = None
+
+    def close(self):
+        if self.ptr:
+            lib().ba_rig_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def _rig_check(status, g):
+    if status != BA_OK:
+        msg = lib().ba_rig_last_error(g)
+        raise BAError(status, msg.decode() if msg else "")
+
+
+def ba_rig_create(opts: Optional[Options] = None, **kw) -> RigHandle:
+    o = opts if opts is not None else ba_options_default()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    g = c_void_p()
+    _rig_check(lib().ba_rig_create(ctypes.byref(o), ctypes.byref(g)), None)
+    return RigHandle(g)
+
+
+def ba_rig_set_problem(g: RigHandle, vehicle_qt, extr_qt, pts, obs_frame, obs_rc, obs_pt, obs_uv,
+                       intrinsics, frame_fixed=None, rc_fixed=None):
+    """Host arrays: vehicle_qt (F, 7) world -> vehicle, extr_qt (R, 7)
+    vehicle -> camera, pts (P, 3), observations, intrinsics (fx, fy, cx, cy)."""
+    vq = _host(vehicle_qt, np.float64).reshape(-1, 7)
+    eq = _host(extr_qt, np.float64).reshape(-1, 7)
+    p = _host(pts, np.float64).reshape(-1, 3)
+    f = _host(obs_frame, np.int32)
+    c = _host(obs_rc, np.int32)
+    j = _host(obs_pt, np.int32)
+    uv = _host(obs_uv, np.float64).reshape(-1, 2)
+    K = Intrinsics(*[float(v) for v in intrinsics])
+    ff = None if frame_fixed is None else _host(frame_fixed, np.uint8)
+    rf = None if rc_fixed is None else _host(rc_fixed, np.uint8)
+    st = lib().ba_rig_set_problem(g.ptr, vq.shape[0], eq.shape[0], p.shape[0], f.shape[0],
+                                  vq.ctypes.data, eq.ctypes.data, p.ctypes.data, f.ctypes.data,
+                                  c.ctypes.data, j.ctypes.data, uv.ctypes.data, ctypes.byref(K),
+                                  None if ff is None else ff.ctypes.data,
+                                  None if rf is None else rf.ctypes.data)
+    _rig_check(st, g.ptr)
+    g.sizes = (vq.shape[0], eq.shape[0], p.shape[0])
+
+
+def ba_rig_solve(g: RigHandle) -> dict:
+    r = Report()
+    _rig_check(lib().ba_rig_solve(g.ptr, ctypes.byref(r)), g.ptr)
+    return r.as_dict()
+
+
+def ba_rig_get_state(g: RigHandle):
+    F, R, P = g.sizes
+    vq, eq, p = np.empty((F, 7)), np.empty((R, 7)), np.empty((P, 3))
+    _rig_check(lib().ba_rig_get_state(g.ptr, vq.ctypes.data, eq.ctypes.data, p.ctypes.data),
+               g.ptr)
+    return vq, eq, p
 
 
 # --------------------------------------------------------------------------- batch / serve

@@ -77,6 +77,19 @@ void launch_lm_begin(const DevProblem& d, const SolveConfig& cfg, cudaStream_t s
 void launch_lm_iteration(const DevProblem& d, const SolveConfig& cfg, cudaStream_t s);
 void launch_lm_end(const DevProblem& d, const SolveConfig& cfg, cudaStream_t s);
 
+// Single steps of the LM iteration (lm_kernels.cu) for solvers that form
+// their own reduced system from the BA Schur complement.  step 0: k_lin_cam
+// and k_lin_pt (they return early unless the state is new); 1: k_damp_pt; 2:
+// k_schur (camera blocks damped by the scalars d.lm points to); 3: k_backsub
+// (point part of the model decrease); 4: k_cost with arg = trial | mode << 1.
+void launch_step(const DevProblem& d, const SolveConfig& cfg, int step, int arg, cudaStream_t s);
+void launch_lm_init_step(const DevProblem& d, const SolveConfig& cfg, cudaStream_t s);
+// gain ratio with the camera part of the model decrease in ndl_cam partial
+// sums at part[kPartDl + kDlParts / 2]
+void launch_gain_step(const DevProblem& d, int ndl_cam, cudaStream_t s);
+void launch_commit_step(const DevProblem& d, cudaStream_t s);
+void launch_rmse_step(const DevProblem& d, cudaStream_t s);
+
 // solvers.cu
 void launch_linear_solve(const DevProblem& d, const SolveConfig& cfg, cudaStream_t s);
 // Per-CTA column lists of the PCG kernel's shared-memory variant (host copy).

@@ -851,6 +851,57 @@ void set_schur_smem_attr(int precision, size_t bytes) {
                          (int)bytes);
 }
 
+// Single steps of the iteration, for solvers that form their own reduced
+// system from the BA Schur complement (the rig solver, rig.cu).
+template <typename T>
+static void steps_t(const DevProblem& d, const SolveConfig& cfg, int step, int arg,
+                    cudaStream_t s) {
+  const T delta = (T)cfg.huber_delta;
+  const unsigned gp = grid_cap(d.P, 256, 148 * 8);
+  switch (step) {
+    case 0:  // linearisation (a new state only)
+      k_lin_cam<T, 256><<<d.C, 256, 0, s>>>(d, delta);
+      k_lin_pt<T><<<gp, 256, 0, s>>>(d, delta);
+      break;
+    case 1:
+      k_damp_pt<T><<<gp, 256, 0, s>>>(d);
+      break;
+    case 2:
+      k_schur<T, 256><<<d.C, 256, schur_smem_bytes<T>(cfg.schur_colcap, d.max_chunk_subs), s>>>(
+          d, cfg.schur_colcap);
+      break;
+    case 3:
+      k_backsub<T><<<backsub_blocks(d), 256, 0, s>>>(d);
+      break;
+    case 4:  // arg: trial (bit 0), mode (bit 1)
+      k_cost<T><<<cost_blocks(d), 256, 0, s>>>(d, arg & 1, delta, (arg >> 1) & 1);
+      break;
+    default:
+      break;
+  }
+}
+
+void launch_step(const DevProblem& d, const SolveConfig& cfg, int step, int arg, cudaStream_t s) {
+  if (d.precision == BA_FP32) steps_t<float>(d, cfg, step, arg, s);
+  else steps_t<double>(d, cfg, step, arg, s);
+}
+
+void launch_lm_init_step(const DevProblem& d, const SolveConfig& cfg, cudaStream_t s) {
+  k_lm_init<<<1, 256, 0, s>>>(d, cost_blocks(d), 0, cfg.mu0, cfg.iters);
+}
+
+void launch_gain_step(const DevProblem& d, int ndl_cam, cudaStream_t s) {
+  k_gain<<<1, 256, 0, s>>>(d, cost_blocks(d), 0, backsub_blocks(d), ndl_cam);
+}
+
+void launch_commit_step(const DevProblem& d, cudaStream_t s) {
+  k_commit<<<grid_cap(d.C > d.P ? d.C : d.P, 256, 148 * 8), 256, 0, s>>>(d);
+}
+
+void launch_rmse_step(const DevProblem& d, cudaStream_t s) {
+  k_rmse_final<<<1, 256, 0, s>>>(d, cost_blocks(d));
+}
+
 void launch_lm_begin(const DevProblem& d, const SolveConfig& cfg, cudaStream_t s) {
   if (d.precision == BA_FP32) lm_begin_t<float>(d, cfg, s);
   else lm_begin_t<double>(d, cfg, s);

@@ -12,7 +12,7 @@ import pytest
 from paper_2510_15271_b300 import ba
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADERS = [os.path.join(ROOT, "include", h) for h in ("ba.h", "ba_pose_graph.h")]
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("ba.h", "ba_pose_graph.h", "ba_rig.h")]
 
 
 @pytest.fixture(scope="module")
@@ -33,7 +33,8 @@ def test_header_declares_the_boundary_calls():
     names = _declared_functions()
     for required in ("ba_create", "ba_set_problem", "ba_solve", "ba_get_state", "ba_submit",
                      "ba_poll", "ba_destroy", "ba_solve_batch", "ba_last_error",
-                     "ba_pg_create", "ba_pg_set_graph", "ba_pg_solve", "ba_pg_get_state"):
+                     "ba_pg_create", "ba_pg_set_graph", "ba_pg_solve", "ba_pg_get_state",
+                     "ba_rig_create", "ba_rig_set_problem", "ba_rig_solve", "ba_rig_get_state"):
         assert required in names
 
 
