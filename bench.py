@@ -719,6 +719,62 @@ def run_pose_graph(args, local_rank):
     return out
 
 
+def run_rig(args, local_rank):
+    """Rig BA with extrinsic refinement (Sec. 4.4) on a 3-camera rig window:
+    100 frames, 20 000 points, 10 LM iterations, FP32 and FP64 (the reduced
+    rig system is dense: 6 x 103 unknowns); obs*iters/s from the same start
+    each step.  With the CPU legs on, the FP64 oracle (full normal equations)
+    on a 40-frame, 800-point sample of the same recipe, one iteration."""
+    from paper_2510_15271_b300 import ba, rig_scenes
+    from scipy.spatial.transform import Rotation
+
+    def qt(R, t):
+        q = Rotation.from_matrix(R).as_quat()
+        q = np.concatenate([q[:, 3:], q[:, :3]], axis=1)
+        q *= np.where(q[:, :1] < 0, -1.0, 1.0)
+        return np.concatenate([q, t], axis=1)
+
+    s = rig_scenes.make_rig_scene(seed=5, n_frames=100, rig=3, n_pts=20000)
+    iters = 10
+    out = {"workload": f"rig BA: {s.n_frames} frames x {s.n_rc} cameras, {s.n_pts} points, "
+                       f"{s.n_obs} observations, {iters} LM iterations, dense rig system",
+           "unit": UNIT}
+    for prec in ("fp32", "fp64"):
+        o = ba.ba_options_default(precision=ba.BA_FP32 if prec == "fp32" else ba.BA_FP64,
+                                  max_lm_iters=iters, device=local_rank)
+        ms, reps = [], []
+        with ba.ba_rig_create(o) as g:
+            for k in range(max(3, args.warmup) + args.steps):
+                ba.ba_rig_set_problem(g, qt(s.Rv, s.tv), qt(s.Re, s.te), s.X, s.obs_frame,
+                                      s.obs_rc, s.obs_pt, s.obs_uv, s.intrinsics[0],
+                                      s.frame_fixed, s.rc_fixed)
+                rep = ba.ba_rig_solve(g)
+                if k >= max(3, args.warmup):
+                    ms.append(rep["solve_ms"])
+                    reps.append(rep)
+        mean_ms = float(np.mean(ms))
+        out[prec] = {"value": s.n_obs * iters / (mean_ms * 1e-3), "ms_per_step": round(mean_ms, 3),
+                     "initial_cost": float(reps[-1]["costs"][0]),
+                     "final_cost": float(reps[-1]["costs"][-1]),
+                     "accepted": int(reps[-1]["n_accepted"]),
+                     "gpu_launches_per_step": int(reps[-1]["n_kernels"])}
+    out["value"] = out["fp32"]["value"]
+    if not args.no_cpu:
+        from oracle import rig_ba as RB   # the CPU comparison only
+        c = rig_scenes.make_rig_scene(seed=5, n_frames=40, rig=3, n_pts=800)
+        prob = RB.RigProblem(c.intrinsics, c.obs_frame, c.obs_rc, c.obs_pt, c.obs_uv,
+                             c.frame_fixed.astype(bool), c.rc_fixed.astype(bool), c.n_frames,
+                             c.n_rc, c.n_pts)
+        t0 = time.perf_counter()
+        RB.rig_lm_solve(prob, RB.RigState(c.Rv, c.tv, c.Re, c.te, c.X), RB.RigOptions(lm_iters=1))
+        dt = time.perf_counter() - t0
+        out["cpu_oracle"] = {"value": c.n_obs / dt, "unit": UNIT,
+                             "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                             "sample": f"one LM iteration, 40 frames x 3 cameras, {c.n_obs} "
+                                       "observations (full normal equations)"}
+    return out
+
+
 # --------------------------------------------------------------------------- reference arm
 
 def run_reference(args):
@@ -787,6 +843,7 @@ def main():
                     help="skip the reprojection-error / triangulation leg")
     ap.add_argument("--no-priors", action="store_true", help="skip the pose-prior leg")
     ap.add_argument("--no-pgo", action="store_true", help="skip the pose-graph leg")
+    ap.add_argument("--no-rig", action="store_true", help="skip the rig BA leg")
     ap.add_argument("--windows", type=int, default=512)
     ap.add_argument("--batch-schedule", default="",
                     help="threads,ctas_per_sm for the batched solver instead of the autotuner")
@@ -854,6 +911,8 @@ def main():
         line["pose_priors"] = run_priors(args, s, 0)
     if not args.no_pgo:
         line["pose_graph"] = run_pose_graph(args, 0)
+    if not args.no_rig:
+        line["rig"] = run_rig(args, 0)
     if not args.no_served:
         line["served"] = run_served(args, 0)
         line["local_ba_p50_ms"] = line["served"]["p50_ms"]

@@ -12,8 +12,9 @@
  * Ad(E) xi_V + xi_E).  Points are eliminated with the BA Schur complement
  * over one "virtual camera" per observed (frame, rig camera) pair; the
  * reduced system over the rig parameters is P^T S P + mu D_rig (P the linear
- * map above, D_rig = diag of P^T U P, Marquardt scaling), solved by the
- * one-CTA dense Cholesky kernel (6 (frames + rig cameras) <= 4096).
+ * map above, D_rig = diag of P^T U P, Marquardt scaling), held dense
+ * (6 (frames + rig cameras) <= 4096) and solved by the one-CTA Cholesky
+ * kernel while it fits in shared memory, else by block-Jacobi PCG.
  *
  * Conventions as in ba.h: poses as (qw, qx, qy, qz, tx, ty, tz) of the
  * world -> vehicle and vehicle -> camera maps; one pinhole K shared by all
@@ -32,9 +33,13 @@ extern "C" {
 typedef struct ba_rig ba_rig;
 
 /* Create a rig solver.  Options read: precision (BA_FP64, or BA_FP32 for
- * the per-observation work, reduced system and Cholesky, with FP64 cost,
- * gain and damping), max_lm_iters, huber_delta, mu0, mu_min, device,
- * cuda_stream, use_graph; the others are ignored.  Errors: INVALID_ARG, CUDA. */
+ * the per-observation work, reduced system and its solve, with FP64 cost,
+ * gain and damping), solver (BA_SOLVER_AUTO: dense Cholesky while the rig
+ * system fits in one CTA's shared memory, else PCG; BA_SOLVER_DENSE;
+ * BA_SOLVER_PCG), pcg_tol, pcg_max_iters (the pipelined PCG when its plan
+ * keeps the system in shared memory and pcg_tol >= 1e-10), max_lm_iters,
+ * huber_delta, mu0, mu_min, device, cuda_stream, use_graph; the others are
+ * ignored.  Errors: INVALID_ARG, CUDA. */
 ba_status ba_rig_create(const ba_options* opts, ba_rig** out);
 
 /* Load a problem from host arrays (replaces any earlier one):

@@ -16,7 +16,9 @@
 //     summation order in the library: the sums differ in the last bits
 //     between runs),
 //   - k_rig_system: the damped system in the path's precision, identity rows
-//     for fixed parameters, solved by the BA dense Cholesky kernel,
+//     for fixed parameters, solved by the BA dense Cholesky kernel (while it
+//     fits in shared memory) or the BA PCG on its full block pattern
+//     (k_rig_minv: block-Jacobi inverses),
 //   - k_rig_expand: xi_cam = P xi for the BA back-substitution (points),
 //   - k_rig_retract / k_rig_compose: trial vehicle poses and extrinsics,
 //     the rig part of the model decrease, the trial virtual cameras,
@@ -57,7 +59,7 @@ struct RigDev {
 __device__ __forceinline__ void adjoint6(const double* R, const double* t, double A[36]) {
 #pragma unroll
   for (int a = 0; a < 36; ++a) A[a] = 0.0;
-  // [t]x R: row r = t x (column of R)... computed entrywise
+  // the upper-right block [t]x R, entrywise
   const double H[9] = {0.0, -t[2], t[1], t[2], 0.0, -t[0], -t[1], t[0], 0.0};
 #pragma unroll
   for (int r = 0; r < 3; ++r)
@@ -193,6 +195,22 @@ __global__ void k_rig_system(DevProblem dr, RigDev g, const LmScalars* lm, doubl
     // full BSR pattern: block (rb, cb) at rb * nb + cb
     S[36 * ((int64_t)rb * g.nb + cb) + 6 * (r % 6) + (c % 6)] = (T)v;
     if (c == 0) ((T*)dr.b)[r] = g.fix[rb] ? T(0) : (T)g.bd[r];
+  }
+}
+
+// Thread per rig block row: the inverse diagonal block (block-Jacobi
+// preconditioner of the PCG path).
+template <typename T>
+__global__ void k_rig_minv(DevProblem dr, RigDev g) {
+  for (int rb = blockIdx.x * blockDim.x + threadIdx.x; rb < g.nb; rb += gridDim.x * blockDim.x) {
+    const T* Sd = (const T*)dr.S + 36 * ((int64_t)rb * g.nb + rb);
+    T blk[36], inv[36];
+#pragma unroll
+    for (int a = 0; a < 36; ++a) blk[a] = Sd[a];
+    spd6_inverse<T>(blk, inv);
+    T* M = (T*)dr.Minv + 36 * (int64_t)rb;
+#pragma unroll
+    for (int a = 0; a < 36; ++a) M[a] = inv[a];
   }
 }
 
@@ -409,6 +427,7 @@ int rig_iteration(ba_rig* r, cudaStream_t s) {
   k_rig_scatter<T><<<grid_n(d.nnzb, 128), 128, 0, s>>>(d, g);
   k_rig_vectors<T><<<grid_n(g.nvc, 128), 128, 0, s>>>(d, g);
   k_rig_system<T><<<grid_n((int64_t)g.n * g.n, 256), 256, 0, s>>>(r->dr, g, d.lm, r->mu_min);
+  if (r->cfg_dense.solver == BA_SOLVER_PCG) k_rig_minv<T><<<grid_n(g.nb, 64), 64, 0, s>>>(r->dr, g);
   launch_linear_solve(r->dr, r->cfg_dense, s);
   k_rig_expand<T><<<grid_n(g.nvc, 128), 128, 0, s>>>(d, r->dr, g);
   launch_step(d, cfg, 3, 0, s);  // back-substitution: trial points, point model decrease
@@ -460,6 +479,7 @@ ba_status ba_rig_create(const ba_options* opts, ba_rig** out) {
   }
   *out = nullptr;
   ba_options o = *opts;
+  const int rig_solver = o.solver;
   o.solver = BA_SOLVER_PCG;  // the virtual-camera system itself is never solved
   o.prior_seq_weight = 0.0;
   o.prior_abs_weight = 0.0;
@@ -471,6 +491,7 @@ ba_status ba_rig_create(const ba_options* opts, ba_rig** out) {
   if (st != BA_OK) return st;
   ba_rig* r = new ba_rig();
   r->opts = o;
+  r->opts.solver = rig_solver;
   r->h = h;
   *out = r;
   return BA_OK;
@@ -634,20 +655,53 @@ ba_status ba_rig_set_problem(ba_rig* r, int32_t F, int32_t R, int32_t P, int64_t
   r->dz.lm = r->zero_lm;
   r->dz.mu_min = 0.0;
   r->mu_min = d.mu_min;
-  // dense Cholesky of the rig system
+  // the rig system: one-CTA dense Cholesky while it fits in shared memory
+  // (auto) or when asked for; otherwise block-Jacobi PCG on its full block
+  // pattern (the one-CTA Cholesky from global memory took 25 ms for 618
+  // unknowns)
   SolveConfig& cd = r->cfg_dense;
   cd = SolveConfig();
-  cd.solver = BA_SOLVER_DENSE;
   int smax = 0;
   cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, r->h->device);
   const size_t need = dense_smem_bytes(prec, g.n);
-  if (need + 1024 <= (size_t)smax) {
-    cd.dense_smem = need;
-    set_dense_smem_attr(prec, need);
-  } else if (!rkeep(r, dr.dense, need)) {
-    r->err = "ba_rig_set_problem: out of device memory (dense workspace)";
-    rig_free(r);
-    return BA_ERR_OOM;
+  int solver = r->opts.solver;
+  if (solver == BA_SOLVER_AUTO) solver = need + 1024 <= (size_t)smax ? BA_SOLVER_DENSE : BA_SOLVER_PCG;
+  cd.solver = solver;
+  cd.pcg_tol = r->opts.pcg_tol;
+  cd.pcg_max = r->opts.pcg_max_iters;
+  if (solver == BA_SOLVER_DENSE) {
+    if (need + 1024 <= (size_t)smax) {
+      cd.dense_smem = need;
+      set_dense_smem_attr(prec, need);
+    } else if (!rkeep(r, dr.dense, need)) {
+      r->err = "ba_rig_set_problem: out of device memory (dense workspace)";
+      rig_free(r);
+      return BA_ERR_OOM;
+    }
+  } else {
+    ok = rkeep(r, dr.Minv, (size_t)g.nb * 36 * Tsz) && rkeep(r, dr.rv, (size_t)g.n * Tsz) &&
+         rkeep(r, dr.z, (size_t)g.n * Tsz) && rkeep(r, dr.qv, (size_t)g.n * Tsz) &&
+         rkeep(r, dr.p0, (size_t)g.n * Tsz) && rkeep(r, dr.p1, (size_t)g.n * Tsz);
+    cd.pcg_pipelined = cd.pcg_tol >= 1e-10 ? 1 : 0;
+    PcgPlan plan;
+    bool planned = ok && plan_pcg(prec, r->h->device, rrow, rcol, (size_t)smax - 4096, cd, plan);
+    if (planned && cd.pcg_pipelined && cd.pcg_smem == 0) {
+      cd.pcg_pipelined = 0;
+      planned = plan_pcg(prec, r->h->device, rrow, rcol, (size_t)smax - 4096, cd, plan);
+    }
+    ok = planned && rkeep(r, dr.pcg_ucol, std::max<size_t>(plan.ucol.size(), 1) * sizeof(int32_t)) &&
+         rkeep(r, dr.pcg_uptr, plan.uptr.size() * sizeof(int32_t)) &&
+         rkeep(r, dr.pcg_lcol, std::max<size_t>(plan.lcol.size(), 1) * sizeof(int32_t)) &&
+         rkeep(r, dr.pcg_lown, plan.lown.size() * sizeof(int32_t));
+    if (!ok) {
+      r->err = "ba_rig_set_problem: PCG plan or its buffers failed";
+      rig_free(r);
+      return BA_ERR_OOM;
+    }
+    RG_CK(cudaMemcpy(dr.pcg_ucol, plan.ucol.data(), plan.ucol.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    RG_CK(cudaMemcpy(dr.pcg_uptr, plan.uptr.data(), plan.uptr.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    RG_CK(cudaMemcpy(dr.pcg_lcol, plan.lcol.data(), plan.lcol.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    RG_CK(cudaMemcpy(dr.pcg_lown, plan.lown.data(), plan.lown.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   }
   RG_CK(cudaStreamSynchronize(s));
   r->loaded = true;
@@ -716,7 +770,7 @@ ba_status ba_rig_solve(ba_rig* r, ba_report* out) {
     RG_CK(cudaMemcpy(rp, d.rep.rmse_parts, sizeof(rp), cudaMemcpyDeviceToHost));
     out->n_iters = iters;
     out->n_accepted = lm.n_accepted;
-    out->solver = BA_SOLVER_DENSE;
+    out->solver = r->cfg_dense.solver;
     out->rmse_px = rp[1] > 0 ? std::sqrt(rp[0] / rp[1]) : 0.0;
     out->n_valid_obs = (int64_t)rp[1];
     out->solve_ms = ms;

@@ -35,9 +35,11 @@ def _oracle(s, iters, rc_fixed=None):
     return RB.rig_lm_solve(prob, st, RB.RigOptions(lm_iters=iters))
 
 
-def _gpu(s, precision, iters, rc_fixed=None):
+def _gpu(s, precision, iters, rc_fixed=None, **kw):
     o = ba.ba_options_default(precision=ba.BA_FP32 if precision == "fp32" else ba.BA_FP64,
                               max_lm_iters=iters)
+    for k, v in kw.items():
+        setattr(o, k, v)
     with ba.ba_rig_create(o) as g:
         ba.ba_rig_set_problem(g, _qt(s.Rv, s.tv), _qt(s.Re, s.te), s.X, s.obs_frame, s.obs_rc,
                               s.obs_pt, s.obs_uv, s.intrinsics[0], s.frame_fixed,
@@ -68,6 +70,19 @@ def test_fp64_matches_oracle_per_iteration(seed):
     np.testing.assert_allclose(X, ref.state.X, atol=1e-6)
     np.testing.assert_allclose(eq[:, 4:], ref.state.te, atol=1e-7)
     np.testing.assert_allclose(O.quat_to_rot(eq[:, :4]), ref.state.Re, atol=1e-8)
+
+
+def test_fp64_pcg_rig_system_matches_oracle():
+    """The PCG path of the rig system (taken when the dense system does not
+    fit in shared memory), forced on a small problem with a tight tolerance."""
+    s = rig_scenes.make_rig_scene(seed=12, n_frames=30, rig=3, n_pts=400)
+    n = 6 * (s.n_frames + s.n_rc)
+    rep, _ = _gpu(s, "fp64", 6, solver=ba.BA_SOLVER_PCG, pcg_tol=1e-13, pcg_max_iters=8 * n)
+    assert rep["solver"] == ba.BA_SOLVER_PCG
+    ref = _oracle(s, 6)
+    rel = np.abs(rep["costs"] - ref.costs) / ref.costs
+    assert rel.max() <= COST_RTOL, (rel, rep["costs"], ref.costs)
+    _accept_flips_only_at_convergence(rep, ref)
 
 
 def test_fixed_extrinsic_and_frames_keep_their_poses():
