@@ -38,8 +38,12 @@ typedef struct ba_rig ba_rig;
  * system fits in one CTA's shared memory, else PCG; BA_SOLVER_DENSE;
  * BA_SOLVER_PCG), pcg_tol, pcg_max_iters (the pipelined PCG when its plan
  * keeps the system in shared memory and pcg_tol >= 1e-10), max_lm_iters,
- * huber_delta, mu0, mu_min, device, cuda_stream, use_graph; the others are
- * ignored.  Errors: INVALID_ARG, CUDA. */
+ * huber_delta, mu0, mu_min, device, cuda_stream, use_graph, and
+ * prior_abs_weight as lambda_e of the extrinsic prior (Sec. 4.4, the absolute
+ * constraint on T_c^v: 1/2 lambda_e ||T_vc - T_vc^init||^2 over the top 3 x 4
+ * blocks of the camera-to-vehicle transforms, measured on the extrinsics
+ * given to ba_rig_set_problem; 0: off); the others are ignored.  Errors:
+ * INVALID_ARG, CUDA. */
 ba_status ba_rig_create(const ba_options* opts, ba_rig** out);
 
 /* Load a problem from host arrays (replaces any earlier one):

@@ -83,10 +83,11 @@ void launch_lm_end(const DevProblem& d, const SolveConfig& cfg, cudaStream_t s);
 // k_schur (camera blocks damped by the scalars d.lm points to); 3: k_backsub
 // (point part of the model decrease); 4: k_cost with arg = trial | mode << 1.
 void launch_step(const DevProblem& d, const SolveConfig& cfg, int step, int arg, cudaStream_t s);
-void launch_lm_init_step(const DevProblem& d, const SolveConfig& cfg, cudaStream_t s);
+// nmisc: further cost partial sums at part[kPartMisc] (a prior's), added to F
+void launch_lm_init_step(const DevProblem& d, const SolveConfig& cfg, int nmisc, cudaStream_t s);
 // gain ratio with the camera part of the model decrease in ndl_cam partial
-// sums at part[kPartDl + kDlParts / 2]
-void launch_gain_step(const DevProblem& d, int ndl_cam, cudaStream_t s);
+// sums at part[kPartDl + kDlParts / 2] and nmisc cost partials at kPartMisc
+void launch_gain_step(const DevProblem& d, int ndl_cam, int nmisc, cudaStream_t s);
 void launch_commit_step(const DevProblem& d, cudaStream_t s);
 void launch_rmse_step(const DevProblem& d, cudaStream_t s);
 

@@ -886,12 +886,12 @@ void launch_step(const DevProblem& d, const SolveConfig& cfg, int step, int arg,
   else steps_t<double>(d, cfg, step, arg, s);
 }
 
-void launch_lm_init_step(const DevProblem& d, const SolveConfig& cfg, cudaStream_t s) {
-  k_lm_init<<<1, 256, 0, s>>>(d, cost_blocks(d), 0, cfg.mu0, cfg.iters);
+void launch_lm_init_step(const DevProblem& d, const SolveConfig& cfg, int nmisc, cudaStream_t s) {
+  k_lm_init<<<1, 256, 0, s>>>(d, cost_blocks(d), nmisc, cfg.mu0, cfg.iters);
 }
 
-void launch_gain_step(const DevProblem& d, int ndl_cam, cudaStream_t s) {
-  k_gain<<<1, 256, 0, s>>>(d, cost_blocks(d), 0, backsub_blocks(d), ndl_cam);
+void launch_gain_step(const DevProblem& d, int ndl_cam, int nmisc, cudaStream_t s) {
+  k_gain<<<1, 256, 0, s>>>(d, cost_blocks(d), nmisc, backsub_blocks(d), ndl_cam);
 }
 
 void launch_commit_step(const DevProblem& d, cudaStream_t s) {

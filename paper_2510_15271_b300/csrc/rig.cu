@@ -34,6 +34,7 @@
 #include "../../include/ba_rig.h"
 #include "handle.h"
 #include "lm.h"
+#include "pose_terms.cuh"
 
 namespace ba {
 extern thread_local std::string g_create_error;
@@ -53,6 +54,8 @@ struct RigDev {
   double* Ud = nullptr;               // [nb][6] diagonal of P^T U P
   double* bd = nullptr;               // [n] P^T b
   double* gd = nullptr;               // [n] P^T g
+  double lam_e = 0.0;                 // extrinsic prior weight
+  double* anchor = nullptr;           // [R][12] initial camera-to-vehicle transforms
 };
 
 // Ad(E) of E = (R, t) for xi = (v, omega): [[R, [t]x R], [0, R]] (row-major 6 x 6).
@@ -172,6 +175,75 @@ __global__ void k_rig_vectors(DevProblem d, RigDev g) {
       atomicAdd(g.bd + 6 * re + e, bv[e]);
       atomicAdd(g.gd + 6 * re + e, gv[e]);
     }
+  }
+}
+
+// Thread per free rig camera: the extrinsic prior (Sec. 4.4, the absolute
+// constraint on T_c^v): 1/2 lambda_e ||T_vc - T_vc^init||^2 over the top
+// 3 x 4 blocks of the camera-to-vehicle transform, whose Jacobian for the
+// left perturbation of E is -(T_vc X_k) (pose_terms.cuh).  J^T J into the
+// diagonal block and the Marquardt scaling, J^T r into g and b (after the
+// scatter kernels, in stream order).
+__global__ void k_rig_prior(RigDev g) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.R; c += gridDim.x * blockDim.x) {
+    const int rb = g.F + c;
+    if (g.fix[rb]) continue;
+    double C[3], M[12], r[12], dU[36], dg[6];
+    camera_centre(g.Re + 9 * c, g.te + 3 * c, C);
+    pose::twc_rows(g.Re + 9 * c, C, M);
+#pragma unroll
+    for (int e = 0; e < 12; ++e) r[e] = M[e] - g.anchor[12 * c + e];
+#pragma unroll
+    for (int e = 0; e < 36; ++e) dU[e] = 0.0;
+#pragma unroll
+    for (int e = 0; e < 6; ++e) dg[e] = 0.0;
+    pose::accumulate(M, false, -1.0, r, g.lam_e, dU, dg);
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+#pragma unroll
+      for (int b = 0; b < 6; ++b) g.Sd[(size_t)(6 * rb + a) * g.n + 6 * rb + b] += dU[6 * a + b];
+      g.Ud[6 * rb + a] += dU[7 * a];
+      g.gd[6 * rb + a] += dg[a];
+      g.bd[6 * rb + a] -= dg[a];
+    }
+  }
+}
+
+// One CTA: the extrinsic prior's cost at the current or trial extrinsics
+// into part[kPartMisc] (added to F by the LM init and gain kernels).
+__global__ void k_rig_prior_cost(DevProblem d, RigDev g, int trial) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int c = threadIdx.x; c < g.R; c += blockDim.x) {
+    const double* R = trial ? g.Re2 + 9 * c : g.Re + 9 * c;
+    const double* t = trial ? g.te2 + 3 * c : g.te + 3 * c;
+    double C[3], M[12];
+    camera_centre(R, t, C);
+    pose::twc_rows(R, C, M);
+    double e2 = 0.0;
+#pragma unroll
+    for (int e = 0; e < 12; ++e) {
+      const double r = M[e] - g.anchor[12 * c + e];
+      e2 += r * r;
+    }
+    acc += 0.5 * g.lam_e * e2;
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    d.part[kPartMisc] = s;
+  }
+}
+
+// Thread per rig camera: the anchor of the extrinsic prior.
+__global__ void k_rig_anchor(RigDev g) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.R; c += gridDim.x * blockDim.x) {
+    double C[3];
+    camera_centre(g.Re + 9 * c, g.te + 3 * c, C);
+    pose::twc_rows(g.Re + 9 * c, C, g.anchor + 12 * c);
   }
 }
 
@@ -426,6 +498,7 @@ int rig_iteration(ba_rig* r, cudaStream_t s) {
   cudaMemsetAsync(g.gd, 0, (size_t)g.n * sizeof(double), s);
   k_rig_scatter<T><<<grid_n(d.nnzb, 128), 128, 0, s>>>(d, g);
   k_rig_vectors<T><<<grid_n(g.nvc, 128), 128, 0, s>>>(d, g);
+  if (g.lam_e > 0.0) k_rig_prior<<<1, 64, 0, s>>>(g);
   k_rig_system<T><<<grid_n((int64_t)g.n * g.n, 256), 256, 0, s>>>(r->dr, g, d.lm, r->mu_min);
   if (r->cfg_dense.solver == BA_SOLVER_PCG) k_rig_minv<T><<<grid_n(g.nb, 64), 64, 0, s>>>(r->dr, g);
   launch_linear_solve(r->dr, r->cfg_dense, s);
@@ -436,7 +509,9 @@ int rig_iteration(ba_rig* r, cudaStream_t s) {
   k_rig_compose<<<grid_n(g.nvc, 128), 128, 0, s>>>(g.Rv2, g.tv2, g.Re2, g.te2, g, d.R2, d.t2,
                                                    d.Cc2, d.cam32b);
   launch_step(d, cfg, 4, 1, s);  // trial cost
-  launch_gain_step(d, nret, s);
+  const int nmisc = g.lam_e > 0.0 ? 1 : 0;
+  if (nmisc) k_rig_prior_cost<<<1, 64, 0, s>>>(d, g, 1);
+  launch_gain_step(d, nret, nmisc, s);
   launch_commit_step(d, s);
   k_rig_commit<<<grid_n(g.nb, 128), 128, 0, s>>>(d, g);
   return n + 12;
@@ -449,7 +524,9 @@ int rig_loop(ba_rig* r, int iters, cudaStream_t s) {
   r->h->cfg.iters = iters;
   int n = 0;
   launch_step(d, cfg, 4, 0, s);
-  launch_lm_init_step(d, cfg, s);
+  const int nmisc = r->g.lam_e > 0.0 ? 1 : 0;
+  if (nmisc) k_rig_prior_cost<<<1, 64, 0, s>>>(d, r->g, 0);
+  launch_lm_init_step(d, cfg, nmisc, s);
   n += 2;
   for (int it = 0; it < iters; ++it)
     n += d.precision == BA_FP32 ? rig_iteration<float>(r, s) : rig_iteration<double>(r, s);
@@ -480,6 +557,11 @@ ba_status ba_rig_create(const ba_options* opts, ba_rig** out) {
   *out = nullptr;
   ba_options o = *opts;
   const int rig_solver = o.solver;
+  const double lam_e = o.prior_abs_weight;  // the extrinsic prior's weight
+  if (!(lam_e >= 0.0) || !std::isfinite(lam_e)) {
+    g_create_error = "ba_rig_create: prior_abs_weight (lambda_e) must be finite and >= 0";
+    return BA_ERR_INVALID_ARG;
+  }
   o.solver = BA_SOLVER_PCG;  // the virtual-camera system itself is never solved
   o.prior_seq_weight = 0.0;
   o.prior_abs_weight = 0.0;
@@ -492,6 +574,7 @@ ba_status ba_rig_create(const ba_options* opts, ba_rig** out) {
   ba_rig* r = new ba_rig();
   r->opts = o;
   r->opts.solver = rig_solver;
+  r->opts.prior_abs_weight = lam_e;
   r->h = h;
   *out = r;
   return BA_OK;
@@ -626,7 +709,8 @@ ba_status ba_rig_set_problem(ba_rig* r, int32_t F, int32_t R, int32_t P, int64_t
             rkeep(r, g.gd, (size_t)g.n * 8) && rkeep(r, r->zero_lm, sizeof(LmScalars)) &&
             rkeep(r, dr.S, (size_t)dr.nnzb * 36 * Tsz) && rkeep(r, dr.b, (size_t)g.n * Tsz) &&
             rkeep(r, dr.dc, (size_t)g.n * Tsz) && rkeep(r, dr.s_rowptr, (g.nb + 1) * sizeof(int32_t)) &&
-            rkeep(r, dr.s_col, rcol.size() * sizeof(int32_t)) && rkeep(r, dr.s_diag, g.nb * sizeof(int32_t));
+            rkeep(r, dr.s_col, rcol.size() * sizeof(int32_t)) && rkeep(r, dr.s_diag, g.nb * sizeof(int32_t)) &&
+            rkeep(r, g.anchor, 12 * (size_t)R * 8);
   if (!ok) {
     r->err = "ba_rig_set_problem: out of device memory";
     rig_free(r);
@@ -648,6 +732,8 @@ ba_status ba_rig_set_problem(ba_rig* r, int32_t F, int32_t R, int32_t P, int64_t
   RG_CK(cudaMemcpy(dr.s_col, rcol.data(), rcol.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   RG_CK(cudaMemcpy(dr.s_diag, rdiag.data(), rdiag.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   RG_CK(cudaMemset(r->zero_lm, 0, sizeof(LmScalars)));
+  g.lam_e = r->opts.prior_abs_weight;
+  k_rig_anchor<<<1, 64, 0, s>>>(g);  // on the given extrinsics
   dr.lm = d.lm;
   dr.part = d.part;
   dr.barrier = d.barrier;

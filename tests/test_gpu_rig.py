@@ -26,13 +26,13 @@ def _qt(R, t):
     return np.concatenate([O.rot_to_quat(R), t], axis=1)
 
 
-def _oracle(s, iters, rc_fixed=None):
+def _oracle(s, iters, rc_fixed=None, lam_e=0.0):
     prob = RB.RigProblem(s.intrinsics, s.obs_frame, s.obs_rc, s.obs_pt, s.obs_uv,
                          s.frame_fixed.astype(bool),
                          (s.rc_fixed if rc_fixed is None else rc_fixed).astype(bool),
                          s.n_frames, s.n_rc, s.n_pts)
     st = RB.RigState(s.Rv, s.tv, s.Re, s.te, s.X)
-    return RB.rig_lm_solve(prob, st, RB.RigOptions(lm_iters=iters))
+    return RB.rig_lm_solve(prob, st, RB.RigOptions(lm_iters=iters, lam_e=lam_e))
 
 
 def _gpu(s, precision, iters, rc_fixed=None, **kw):
@@ -83,6 +83,19 @@ def test_fp64_pcg_rig_system_matches_oracle():
     rel = np.abs(rep["costs"] - ref.costs) / ref.costs
     assert rel.max() <= COST_RTOL, (rel, rep["costs"], ref.costs)
     _accept_flips_only_at_convergence(rep, ref)
+
+
+@pytest.mark.parametrize("lam_e", [3e3, 1e7])
+def test_fp64_extrinsic_prior_matches_oracle(lam_e):
+    """The absolute constraint on the extrinsics (Sec. 4.4), measured on the
+    given extrinsics: per-iteration cost to 1e-9; a large weight holds them."""
+    s = rig_scenes.make_rig_scene(seed=13, n_frames=8, rig=3, n_pts=150)
+    rep, (vq, eq, X) = _gpu(s, "fp64", 8, prior_abs_weight=lam_e)
+    ref = _oracle(s, 8, lam_e=lam_e)
+    rel = np.abs(rep["costs"] - ref.costs) / ref.costs
+    assert rel.max() <= COST_RTOL, (rel, rep["costs"], ref.costs)
+    _accept_flips_only_at_convergence(rep, ref)
+    np.testing.assert_allclose(eq[:, 4:], ref.state.te, atol=1e-7)
 
 
 def test_fixed_extrinsic_and_frames_keep_their_poses():
