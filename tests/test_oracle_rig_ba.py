@@ -154,3 +154,20 @@ def test_extrinsic_prior_is_zero_at_the_start_and_holds_the_extrinsics(small):
     d_free = np.abs(free.state.te - st.te).max() + np.abs(free.state.Re - st.Re).max()
     d_held = np.abs(held.state.te - st.te).max() + np.abs(held.state.Re - st.Re).max()
     assert d_held < 1e-2 * d_free
+
+
+def test_generator_scene_is_consistent():
+    """The seeded rig scene: indices in range, every point seen at least
+    twice, the composite true cameras see their observations in front, and
+    the noise-free reprojection of the true state is at the noise level."""
+    s = RS.make_rig_scene(seed=2, n_frames=10, rig=3, n_pts=200)
+    assert s.obs_frame.max() < s.n_frames and s.obs_rc.max() < s.n_rc and s.obs_pt.max() < s.n_pts
+    assert np.bincount(s.obs_pt, minlength=s.n_pts).min() >= 2
+    prob = _problem(s)
+    gt = RB.RigState(s.Rv_gt, s.tv_gt, s.Re_gt, s.te_gt, s.X_gt)
+    r, _, _, _, valid = RB._linearize_obs(prob, gt, 0.0)
+    assert valid.all()
+    rms = np.sqrt(np.mean(np.sum(r * r, axis=1)))
+    assert 0.3 < rms < 1.0          # 0.5 px per axis of noise
+    again = RS.make_rig_scene(seed=2, n_frames=10, rig=3, n_pts=200)
+    np.testing.assert_array_equal(again.obs_uv, s.obs_uv)
