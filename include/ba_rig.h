@@ -54,8 +54,9 @@ ba_status ba_rig_create(const ba_options* opts, ba_rig** out);
  *                             observation; obs_uv [n_obs][2] pixels
  *   frame_fixed [n_frames], rc_fixed [n_rig] or NULL
  * Errors: INVALID_ARG (sizes < 1, 6 (n_frames + n_rig) > 4096, an index out
- * of range, a non-finite value, a zero quaternion, or the BA layout's own
- * checks on the observations: a point with fewer than 2 of them), OOM, CUDA. */
+ * of range, a non-finite value, a zero quaternion, a free frame or rig camera
+ * without observations, or the BA layout's own checks on the observations: a
+ * point with fewer than 2 of them), OOM, CUDA. */
 ba_status ba_rig_set_problem(ba_rig* g, int32_t n_frames, int32_t n_rig, int32_t n_pts,
                              int64_t n_obs, const double* vehicle_qt, const double* extr_qt,
                              const double* pts, const int32_t* obs_frame, const int32_t* obs_rc,

@@ -628,6 +628,25 @@ ba_status ba_rig_set_problem(ba_rig* r, int32_t F, int32_t R, int32_t P, int64_t
     }
     key[k] = (int64_t)obs_frame[k] * R + obs_rc[k];
   }
+  // a free frame or rig camera without observations would leave its block of
+  // the rig system singular
+  {
+    std::vector<uint8_t> seen_f(F, 0), seen_c(R, 0);
+    for (int64_t k = 0; k < N; ++k) {
+      seen_f[obs_frame[k]] = 1;
+      seen_c[obs_rc[k]] = 1;
+    }
+    for (int f = 0; f < F; ++f)
+      if (!seen_f[f] && !(frame_fixed && frame_fixed[f])) {
+        r->err = "ba_rig_set_problem: a free frame has no observation";
+        return BA_ERR_INVALID_ARG;
+      }
+    for (int c = 0; c < R; ++c)
+      if (!seen_c[c] && !(rc_fixed && rc_fixed[c])) {
+        r->err = "ba_rig_set_problem: a free rig camera has no observation";
+        return BA_ERR_INVALID_ARG;
+      }
+  }
   std::vector<int64_t> vk(key);
   std::sort(vk.begin(), vk.end());
   vk.erase(std::unique(vk.begin(), vk.end()), vk.end());

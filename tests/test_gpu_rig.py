@@ -129,3 +129,9 @@ def test_invalid_rig_problems_are_refused():
                                   s.rc_fixed)
         with pytest.raises(ba.BAError, match="no problem"):
             ba.ba_rig_solve(g)
+        # a free frame without observations
+        vq = np.concatenate([_qt(s.Rv, s.tv), _qt(s.Rv[:1], s.tv[:1])])
+        with pytest.raises(ba.BAError, match="free frame has no observation"):
+            ba.ba_rig_set_problem(g, vq, _qt(s.Re, s.te), s.X, s.obs_frame, s.obs_rc, s.obs_pt,
+                                  s.obs_uv, s.intrinsics[0],
+                                  np.concatenate([s.frame_fixed, [0]]), s.rc_fixed)
