@@ -1104,12 +1104,38 @@ bool plan_pcg(int precision, int device, const std::vector<int32_t>& rowptr,
     G = occ * sms;
   }
   pcg_lists(G, R, rowptr, col, plan, maxnnz, maxu);
-  const size_t need = pcg_smem_need(precision, maxnnz, R, maxu);
+  size_t need = pcg_smem_need(precision, maxnnz, R, maxu);
   bool smem = false;
   const void* fs = pcg_fn_prec(precision, true, rw, pipe);
   if (fs && need + static_smem(fs) <= smem_limit) {
     cudaFuncSetAttribute(fs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
     smem = pcg_occupancy(fs, need) * sms >= G;
+  }
+  // Long rows that do not fit: fewer rows per CTA (more CTAs, still within
+  // the co-resident grid) can keep S in shared memory (the dense 103-block-row
+  // rig system in FP64: 8 rows per CTA need 244 KB, 4 rows 122 KB)
+  for (int R2 = R / 2; !smem && R2 >= 1; R2 /= 2) {
+    const int G2 = (C + R2 - 1) / R2;
+    if (G2 > gmax) break;
+    int rw2 = 1;
+    while (rw2 * kPcgWarps < R2) rw2 *= 2;
+    const void* f2 = pcg_fn_prec(precision, true, rw2, pipe);
+    if (!f2) continue;
+    PcgPlan p2;
+    int mn2 = 0, mu2 = 0;
+    pcg_lists(G2, R2, rowptr, col, p2, mn2, mu2);
+    const size_t need2 = pcg_smem_need(precision, mn2, R2, mu2);
+    if (need2 + static_smem(f2) > smem_limit) continue;
+    cudaFuncSetAttribute(f2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need2);
+    if (pcg_occupancy(f2, need2) * sms < G2) continue;
+    plan = std::move(p2);
+    G = G2;
+    R = R2;
+    rw = rw2;
+    maxnnz = mn2;
+    maxu = mu2;
+    need = need2;
+    smem = true;
   }
   cfg.pcg_blocks = G;
   cfg.pcg_rows = R;
