@@ -134,6 +134,12 @@ typedef struct {
                                camera-to-world pose given to ba_set_problem.
                                ba_solve only (ba_solve_batch and
                                ba_create_server refuse it)                    */
+  int pcg_resident_cap;     /* bytes of shared memory per CTA in which the PCG
+                               kernels may keep their rows of S resident
+                               (0: the device's limit).  A small cap makes
+                               them read S from global memory every product,
+                               as on systems too large to stay resident; for
+                               tests and tuning                               */
 } ba_options;
 
 typedef struct {
@@ -218,6 +224,22 @@ ba_status ba_get_state(const ba_handle* h, double* cam_qt_out, double* pts_out, 
  * layout; the damping restarts from mu0.  Errors: STATE, INVALID_ARG, CUDA. */
 ba_status ba_set_state(ba_handle* h, const double* cam_qt, const double* pts, int mem_kind);
 
+/* Diagnostic: the reduced camera system of the last linear solve of the
+ * last ba_solve, as the device holds it, for checking the solve on the host
+ * (host memory, FP64).  Rows and columns of fixed cameras are identity rows
+ * with a zero right-hand side.
+ *   dim    6 n_cams
+ *   S_out  [dim][dim] or NULL: S = U* - W V*^-1 W^T as stored (in the path's
+ *          precision, promoted), zero outside its block pattern
+ *   b_out  [dim] or NULL: its right-hand side before rounding to the path's
+ *          precision (-g_c + W V*^-1 g_p in FP64)
+ *   x_out  [dim] or NULL: the solution the step used: the FP64 iterate of the
+ *          refinement loop when refinement is on, else the solver's output
+ *          in the path's precision, promoted
+ * Errors: STATE (no finished solve), INVALID_ARG (dim), CUDA. */
+ba_status ba_get_reduced_system(const ba_handle* h, int32_t dim, double* S_out, double* b_out,
+                                double* x_out);
+
 /* Kernel timings of the last solve, one entry per kernel kind: out[max]
  * receives up to max entries, *n the number written.  A serving handle adds
  * serve_tick (ticks, their summed milliseconds), serve_completed (requests),
@@ -234,22 +256,30 @@ ba_status ba_kernel_stats(const ba_handle* h, ba_kernel_stat* out, int32_t max, 
  * start-up, or a host library that owns every allocation of its context
  * through its own pool).  It calls no cudaMalloc, cudaFree or allocating
  * library routine; its scratch is one file-scope device array of about
- * 1.5 MB, held by every GPU that loads the library until the process exits.
+ * 1.5 MB.  The library's device code is loaded lazily, so the first call on
+ * a device is where the driver loads the array and takes its memory; the
+ * array is then held until the process exits.  Make that first call at
+ * start-up (a one-camera problem will do), before any stream capture on the
+ * device begins: it also looks up the array's device address, with that
+ * device current, and later calls take no device memory at all.  The address
+ * is kept per device and does not survive cudaDeviceReset: do not call this
+ * entry point on a device after resetting it.
  *   device       CUDA device ordinal; the caller's current device is restored
  *   cuda_stream  cudaStream_t to run on (NULL: the legacy default stream)
  *   cam_qt, pts, obs_cam, obs_pt, obs_uv   device pointers, layouts as in
  *                ba_set_problem; observations in any order
  *   K            host pointer; huber_delta as in ba_options (<= 0: none)
- *   cost_out     device pointer to one double that receives F
+ *   cost_out     device pointer to one double that receives F (unspecified
+ *                when the call fails)
  * Observations with depth below 1e-3 leave the sum, as in ba_solve.  The call
  * blocks until cost_out is written.  Limits: n_cams <= 16384.  Every call on
  * a device shares the scratch array and keeps the last call's contents (the
  * call clears what must start at zero); calls whose work overlaps on the GPU
- * race.  The first call on a device looks up the array's device address,
- * with that device current; make that first call before any stream capture
- * on the device begins.  Errors (message in ba_last_error(NULL)):
- * INVALID_ARG (NULL pointer, size < 1, n_cams above the limit, an index out
- * of range), CUDA. */
+ * race.  Errors (message in ba_last_error(NULL)): INVALID_ARG (NULL pointer,
+ * size < 1, n_cams above the limit, and, naming the first offender, an index
+ * out of range, a non-finite pose, point or pixel, or a zero quaternion, as
+ * ba_set_problem refuses them), CUDA (including a kernel that fails to
+ * launch). */
 ba_status ba_cost_noalloc(int device, void* cuda_stream, int32_t n_cams, int32_t n_pts,
                           int64_t n_obs, const double* cam_qt, const double* pts,
                           const int32_t* obs_cam, const int32_t* obs_pt, const double* obs_uv,

@@ -56,7 +56,7 @@ __all__ = [
     "state_from_qt", "state_to_qt", "se3_retract", "retract",
     "huber_rho", "huber_weight", "residuals", "cost", "linearize", "block_sums",
     "damped_blocks", "schur_system", "back_substitute", "full_normal_equations",
-    "pcg_block_jacobi", "solve_step", "model_decrease", "lm_solve",
+    "pcg_block_jacobi", "solve_step", "model_decrease", "damping_update", "lm_solve",
     "rmse", "pose_errors", "umeyama_sim3",
 ]
 
@@ -526,6 +526,19 @@ def model_decrease(h, D, g, mu):
     return 0.5 * float(h @ (mu * D * h - g))
 
 
+def damping_update(mu, nu, gain, accepted):
+    """Nielsen's damping update (Madsen, Nielsen & Tingleff 2004, Sec. 3.2,
+    eq. 3.16 with Nielsen's nu rule), returning the new (mu, nu).  After an
+    accepted step mu shrinks by max(1/3, 1 - (2 gain - 1)^3): a third for a
+    step the model predicted exactly (gain 1), unchanged at gain 1/2, doubled
+    as gain tends to 0; nu restarts at 2.  After a rejected step mu grows by
+    nu and nu doubles, so repeated rejections raise the damping
+    geometrically faster."""
+    if accepted:
+        return mu * max(1.0 / 3.0, 1.0 - (2.0 * gain - 1.0) ** 3), 2.0
+    return mu * nu, 2.0 * nu
+
+
 def _linearization(prob, st, opts, pri=None):
     dU = dg = cpl = None
     if pri is not None:
@@ -587,16 +600,12 @@ def lm_solve(prob: Problem, st0: State, opts: LMOptions) -> LMResult:
         cg.append(iters)
         gains.append(gain)
         dLs.append(dL)
-        if dL > 0 and gain > 0:
+        accept = bool(dL > 0 and gain > 0)
+        mu, nu = damping_update(mu, nu, gain, accept)
+        if accept:
             st, F = cand, F_new
-            mu = mu * max(1.0 / 3.0, 1.0 - (2.0 * gain - 1.0) ** 3)
-            nu = 2.0
             lin = None
-            acc.append(True)
-        else:
-            mu = mu * nu
-            nu = 2.0 * nu
-            acc.append(False)
+        acc.append(accept)
         costs.append(F)
     return LMResult(np.array(costs), np.array(acc, dtype=bool), np.array(mus),
                     np.array(cg, dtype=np.int64), np.array(gains), np.array(dLs), st)

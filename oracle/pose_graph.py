@@ -39,7 +39,8 @@ import scipy.linalg
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from .ba_oracle import DIAG_MIN, hat, quat_to_rot, rot_to_quat, se3_retract
+from .ba_oracle import (DIAG_MIN, damping_update, hat, quat_to_rot, rot_to_quat,
+                        se3_retract)
 
 __all__ = ["PoseGraph", "PGOptions", "PGResult", "pose_graph_from_arrays", "relative_poses",
            "pg_residuals", "pg_cost", "pg_jacobians", "pg_normal_equations", "pg_lm_solve"]
@@ -218,16 +219,12 @@ def pg_lm_solve(pg: PoseGraph, R0, t0, opts: PGOptions) -> PGResult:
         gain = (F - F_new) / dL if dL > 0 else -np.inf
         mus.append(mu)
         gains.append(gain)
-        if dL > 0 and gain > 0:
+        accept = bool(dL > 0 and gain > 0)
+        mu, nu = damping_update(mu, nu, gain, accept)
+        if accept:
             R, t, F = R2, t2, F_new
-            mu = mu * max(1.0 / 3.0, 1.0 - (2.0 * gain - 1.0) ** 3)
-            nu = 2.0
             lin = None
-            acc.append(True)
-        else:
-            mu = mu * nu
-            nu = 2.0 * nu
-            acc.append(False)
+        acc.append(accept)
         costs.append(F)
     return PGResult(np.array(costs), np.array(acc, dtype=bool), np.array(mus), np.array(gains),
                     R, t)

@@ -249,16 +249,12 @@ def rig_lm_solve(prob: RigProblem, st0: RigState, opts: RigOptions) -> RigResult
         gain = (F - F_new) / dL if dL > 0 else -np.inf
         mus.append(mu)
         gains.append(gain)
-        if dL > 0 and gain > 0:
+        accept = bool(dL > 0 and gain > 0)
+        mu, nu = B.damping_update(mu, nu, gain, accept)
+        if accept:
             st, F = cand, F_new
-            mu = mu * max(1.0 / 3.0, 1.0 - (2.0 * gain - 1.0) ** 3)
-            nu = 2.0
             lin = None
-            acc.append(True)
-        else:
-            mu = mu * nu
-            nu = 2.0 * nu
-            acc.append(False)
+        acc.append(accept)
         costs.append(F)
     return RigResult(np.array(costs), np.array(acc, dtype=bool), np.array(mus),
                      np.array(gains), st)

@@ -49,7 +49,8 @@ class Options(Structure):
                 ("serve_tick_ms", c_double),
                 ("serve_split_ms", c_double),
                 ("prior_seq_weight", c_double),
-                ("prior_abs_weight", c_double)]
+                ("prior_abs_weight", c_double),
+                ("pcg_resident_cap", c_int)]
 
 
 class Intrinsics(Structure):
@@ -116,6 +117,7 @@ _SIGNATURES = {
     "ba_solve": (c_int, [c_void_p, POINTER(Report)]),
     "ba_get_state": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
     "ba_set_state": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
+    "ba_get_reduced_system": (c_int, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
     "ba_destroy": (None, [c_void_p]),
     "ba_kernel_stats": (c_int, [c_void_p, c_void_p, c_int32, POINTER(c_int32)]),
     "ba_last_error": (c_char_p, [c_void_p]),
@@ -325,6 +327,18 @@ def ba_set_state(h: Handle, cam_qt, pts):
     q = _host(cam_qt, np.float64)
     p = _host(pts, np.float64)
     _check(lib().ba_set_state(h.ptr, q.ctypes.data, p.ctypes.data, BA_MEM_HOST), h.ptr)
+
+
+def ba_get_reduced_system(h: Handle, n_cams: int):
+    """(S, b, x) of the last linear solve as the device holds them (dense
+    FP64 copies; see ba.h)."""
+    n = 6 * n_cams
+    S = np.empty((n, n))
+    b = np.empty(n)
+    x = np.empty(n)
+    _check(lib().ba_get_reduced_system(h.ptr, n, S.ctypes.data, b.ctypes.data, x.ctypes.data),
+           h.ptr)
+    return S, b, x
 
 
 def ba_destroy(h: Handle):

@@ -155,6 +155,10 @@ static ba_status check_options(const ba_options* o, std::string& err) {
     err = "serve_tick_ms and serve_split_ms must be finite";
     return BA_ERR_INVALID_ARG;
   }
+  if (o->pcg_resident_cap < 0) {
+    err = "pcg_resident_cap must be >= 0";
+    return BA_ERR_INVALID_ARG;
+  }
   if (o->pcg_variant < 0 || o->pcg_variant > 3) {
     err = "pcg_variant must be 0 (auto), 1 (standard), 2 (pipelined) or 3 (cluster)";
     return BA_ERR_INVALID_ARG;
@@ -648,13 +652,15 @@ ba_status ba_set_problem(ba_handle* h, int32_t n_cams, int32_t n_pts, int64_t n_
     std::vector<int32_t> hcol(d.nnzb);
     CK(cudaMemcpy(hcol.data(), d.s_col, d.nnzb * sizeof(int32_t), cudaMemcpyDeviceToHost));
     PcgPlan plan;
-    bool planned = plan_pcg(prec, h->device, hrp, hcol, smax - 4096, cfg, plan);
+    size_t resident = smax - 4096;
+    if (h->opts.pcg_resident_cap > 0) resident = std::min(resident, (size_t)h->opts.pcg_resident_cap);
+    bool planned = plan_pcg(prec, h->device, hrp, hcol, resident, cfg, plan);
     if (h->opts.pcg_variant == 0 && (!planned || cfg.pcg_smem == 0 || cfg.refine)) {
       // S streamed from memory, or refinement: the standard recurrence keeps
       // more CTAs per SM and needed far fewer iterations with refinement
       // (city workload: 2 777 instead of 4 588 per solve, 322 instead of 570 ms)
       cfg.pcg_pipelined = 0;
-      planned = plan_pcg(prec, h->device, hrp, hcol, smax - 4096, cfg, plan);
+      planned = plan_pcg(prec, h->device, hrp, hcol, resident, cfg, plan);
     }
     if (!planned) {
       h->err = "ba_set_problem: too many cameras for the PCG kernel";
@@ -887,6 +893,53 @@ ba_status ba_get_state(const ba_handle* hc, double* cam_qt_out, double* pts_out,
   if (pts_out) {
     CK(cudaMemcpyAsync(pts_out, d.X, (size_t)d.P * 3 * sizeof(double), kind, s));
     CK(cudaStreamSynchronize(s));
+  }
+  return BA_OK;
+}
+
+ba_status ba_get_reduced_system(const ba_handle* hc, int32_t dim, double* S_out, double* b_out,
+                                double* x_out) {
+  ba_handle* h = const_cast<ba_handle*>(hc);
+  if (!h) return BA_ERR_INVALID_ARG;
+  if (!h->loaded || !h->solved) {
+    h->err = "ba_get_reduced_system: needs a finished ba_solve";
+    return BA_ERR_STATE;
+  }
+  const DevProblem& d = h->d;
+  if (dim != 6 * d.C) {
+    h->err = "ba_get_reduced_system: dim must be 6 n_cams";
+    return BA_ERR_INVALID_ARG;
+  }
+  CK(cudaSetDevice(h->device));
+  cudaStream_t s = h->stream;
+  CK(cudaStreamSynchronize(s));
+  const bool f32 = d.precision == BA_FP32;
+  const size_t tsz = f32 ? sizeof(float) : sizeof(double);
+  auto promote = [&](const std::vector<unsigned char>& raw, size_t i) {
+    return f32 ? (double)reinterpret_cast<const float*>(raw.data())[i]
+               : reinterpret_cast<const double*>(raw.data())[i];
+  };
+  if (S_out) {
+    std::vector<int32_t> rp(d.C + 1), col(d.nnzb);
+    std::vector<unsigned char> raw((size_t)d.nnzb * 36 * tsz);
+    CK(cudaMemcpy(rp.data(), d.s_rowptr, rp.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(col.data(), d.s_col, col.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(raw.data(), d.S, raw.size(), cudaMemcpyDeviceToHost));
+    std::fill(S_out, S_out + (size_t)dim * dim, 0.0);
+    for (int i = 0; i < d.C; ++i)
+      for (int b = rp[i]; b < rp[i + 1]; ++b)
+        for (int e = 0; e < 36; ++e)
+          S_out[(size_t)(6 * i + e / 6) * dim + 6 * col[b] + e % 6] = promote(raw, 36 * (size_t)b + e);
+  }
+  if (b_out) CK(cudaMemcpy(b_out, d.b64, (size_t)dim * sizeof(double), cudaMemcpyDeviceToHost));
+  if (x_out) {
+    if (h->cfg.refine) {
+      CK(cudaMemcpy(x_out, d.x64, (size_t)dim * sizeof(double), cudaMemcpyDeviceToHost));
+    } else {
+      std::vector<unsigned char> raw((size_t)dim * tsz);
+      CK(cudaMemcpy(raw.data(), d.dc, raw.size(), cudaMemcpyDeviceToHost));
+      for (int i = 0; i < dim; ++i) x_out[i] = promote(raw, i);
+    }
   }
   return BA_OK;
 }

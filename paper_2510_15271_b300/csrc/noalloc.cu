@@ -6,9 +6,11 @@
 // and forbids allocation afterwards, or a library that owns every buffer of
 // its CUDA context through its own pool.  This entry point takes the
 // problem in the caller's device buffers and keeps its scratch (camera
-// rotations and translations, per-block partial sums, an invalid-index
-// counter) in one file-scope device array of fixed size, so it calls no
-// cudaMalloc, cudaFree or allocating library routine.
+// rotations and translations, per-block partial sums, validation words) in
+// one file-scope device array of fixed size, so it calls no cudaMalloc,
+// cudaFree or allocating library routine.  It refuses what ba_set_problem
+// refuses about the values it reads: indices out of range, non-finite poses,
+// points or pixels, zero quaternions.
 //
 // Same arithmetic as the cost pass of the LM loop (k_cost, FP64 path): the
 // camera transform, residual and Huber rho of ba_device.cuh, an FP64 sum
@@ -16,6 +18,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 #include <string>
@@ -34,24 +37,58 @@ constexpr int kNoAllocBlocks = 512;     // CTAs of the cost pass (partial sums)
 constexpr int kNoAllocThreads = 256;
 constexpr int kCamOff = 0;                                  // [n_cams][12]: R (9), t (3)
 constexpr int kPartOff = 12 * kNoAllocMaxCams;              // [kNoAllocBlocks]
-constexpr int kCountOff = kPartOff + kNoAllocBlocks;        // invalid-index counter (u64)
-constexpr int kScratchDoubles = kCountOff + 8;
+constexpr int kFlagOff = kPartOff + kNoAllocBlocks;         // kNumFlags u64 words
+constexpr int kScratchDoubles = kFlagOff + 8;
 
-// The scratch of every call on this device (about 1.5 MB).  Held by each
-// GPU that loads the library until the process exits.  Calls share it: two
-// calls whose work overlaps on the GPU race on it.
+// Validation words at kFlagOff (u64): the number of observations with an
+// index out of range, then the lowest offending observation, camera, point
+// and pixel (observation) index, or ~0 when there is none.
+enum { kBadIndexCount = 0, kFirstBadObs, kFirstBadCam, kFirstBadPoint, kFirstBadPixel, kNumFlags };
+static_assert(kNumFlags <= 8, "validation words fit their slot");
+
+// The scratch of every call on this device (about 1.5 MB).  Calls share it:
+// two calls whose work overlaps on the GPU race on it.
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
-__global__ void k_na_cams(int C, const double* __restrict__ qt, double* __restrict__ scratch) {
-  if (blockIdx.x == 0 && threadIdx.x == 0)
-    *reinterpret_cast<unsigned long long*>(scratch + kCountOff) = 0ull;  // must start at zero
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < C; i += gridDim.x * blockDim.x) {
-    const double q[4] = {qt[7 * i], qt[7 * i + 1], qt[7 * i + 2], qt[7 * i + 3]};
-    double* out = scratch + kCamOff + 12 * i;
-    quat_to_rot(q, out);
-    out[9] = qt[7 * i + 4];
-    out[10] = qt[7 * i + 5];
-    out[11] = qt[7 * i + 6];
+__device__ __forceinline__ unsigned long long* flag_words(double* scratch) {
+  return reinterpret_cast<unsigned long long*>(scratch + kFlagOff);
+}
+
+// Resets the validation words; launched first, so every later kernel of the
+// call sees them reset (stream order).
+__global__ void k_na_init(double* __restrict__ scratch) {
+  unsigned long long* f = flag_words(scratch);
+  if (threadIdx.x < kNumFlags) f[threadIdx.x] = threadIdx.x == kBadIndexCount ? 0ull : ~0ull;
+}
+
+// Camera rotations and translations into the scratch, and the state checks
+// of ba_set_problem: every pose value finite and the quaternion nonzero,
+// every point finite.
+__global__ void k_na_state(int C, int P, const double* __restrict__ qt,
+                           const double* __restrict__ pts, double* __restrict__ scratch) {
+  unsigned long long* f = flag_words(scratch);
+  const int n = C > P ? C : P;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (i < C) {
+      double v[7];
+      bool fin = true;
+      for (int a = 0; a < 7; ++a) {
+        v[a] = qt[7 * i + a];
+        fin = fin && isfinite(v[a]);
+      }
+      const double q2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3];
+      if (!fin || !(q2 > 1e-30)) atomicMin(&f[kFirstBadCam], (unsigned long long)i);
+      double* out = scratch + kCamOff + 12 * i;
+      quat_to_rot(v, out);
+      out[9] = v[4];
+      out[10] = v[5];
+      out[11] = v[6];
+    }
+    if (i < P) {
+      const double x = pts[3 * i], y = pts[3 * i + 1], z = pts[3 * i + 2];
+      if (!isfinite(x) || !isfinite(y) || !isfinite(z))
+        atomicMin(&f[kFirstBadPoint], (unsigned long long)i);
+    }
   }
 }
 
@@ -61,13 +98,19 @@ __global__ void __launch_bounds__(kNoAllocThreads)
               const double* __restrict__ pts, Intrinsics K, double delta,
               double* __restrict__ scratch) {
   __shared__ double red[kNoAllocThreads / 32];
+  unsigned long long* f = flag_words(scratch);
   double acc = 0.0;
   unsigned long long bad = 0;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int c = obs_cam[k], j = obs_pt[k];
     if (c < 0 || c >= C || j < 0 || j >= P) {
-      ++bad;
+      if (bad++ == 0) atomicMin(&f[kFirstBadObs], (unsigned long long)k);
+      continue;
+    }
+    const double u = obs_uv[2 * k], v = obs_uv[2 * k + 1];
+    if (!isfinite(u) || !isfinite(v)) {
+      atomicMin(&f[kFirstBadPixel], (unsigned long long)k);
       continue;
     }
     const double* cam = scratch + kCamOff + 12 * c;
@@ -75,11 +118,11 @@ __global__ void __launch_bounds__(kNoAllocThreads)
     to_camera64(cam, cam + 9, pts[3 * (int64_t)j], pts[3 * (int64_t)j + 1],
                 pts[3 * (int64_t)j + 2], xc);
     double r0, r1;
-    if (!residual<double>(xc, obs_uv[2 * k], obs_uv[2 * k + 1], K, r0, r1)) continue;
+    if (!residual<double>(xc, u, v, K, r0, r1)) continue;
     const double s = __fma_rn(r0, r0, __dmul_rn(r1, r1));
     acc += 0.5 * huber_rho<double>(s, delta);
   }
-  if (bad) atomicAdd(reinterpret_cast<unsigned long long*>(scratch + kCountOff), bad);
+  if (bad) atomicAdd(&f[kBadIndexCount], bad);
   acc = warp_sum(acc);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
@@ -106,7 +149,12 @@ __global__ void k_na_reduce(const double* __restrict__ scratch, double* __restri
 
 // Device address of the scratch array, looked up by the first call on each
 // device with that device current (so that first call belongs before any
-// stream capture on the device).
+// stream capture on the device).  The library's code is loaded lazily, one
+// module per source file, so this lookup is also where the driver loads this
+// file's module and takes the array's device memory.  The cached address
+// does not survive cudaDeviceReset (the module is then loaded again, possibly
+// elsewhere): a process that resets a device must not call this entry point
+// on it afterwards.
 constexpr int kMaxDevices = 64;
 std::mutex g_na_mutex;
 double* g_na_addr[kMaxDevices] = {};
@@ -173,20 +221,39 @@ extern "C" ba_status ba_cost_noalloc(int device, void* cuda_stream, int32_t n_ca
   } else {
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const Intrinsics Ki{K->fx, K->fy, K->cx, K->cy};
-    k_na_cams<<<(n_cams + 127) / 128, 128, 0, s>>>(n_cams, cam_qt, scratch);
+    cudaGetLastError();  // a stale error of an earlier call is not this call's
+    const int nst = n_cams > n_pts ? n_cams : n_pts;
+    k_na_init<<<1, 32, 0, s>>>(scratch);
+    k_na_state<<<(int)std::min<int64_t>((nst + 255) / 256, 1024), 256, 0, s>>>(n_cams, n_pts,
+                                                                               cam_qt, pts, scratch);
     k_na_cost<<<kNoAllocBlocks, kNoAllocThreads, 0, s>>>(n_obs, n_cams, n_pts, obs_cam, obs_pt,
                                                         obs_uv, pts, Ki, huber_delta, scratch);
     k_na_reduce<<<1, 256, 0, s>>>(scratch, cost_out);
-    unsigned long long bad = 0;
-    cudaError_t e = cudaMemcpyAsync(&bad, scratch + kCountOff, sizeof(bad),
-                                    cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaGetLastError();  // launch failures (no image, bad configuration)
+    unsigned long long f[kNumFlags] = {};
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(f, scratch + kFlagOff, sizeof(f), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    const unsigned long long none = ~0ull;
     if (e != cudaSuccess) {
       g_create_error = std::string("ba_cost_noalloc: ") + cudaGetErrorString(e);
       st = BA_ERR_CUDA;
-    } else if (bad) {
-      g_create_error = "ba_cost_noalloc: " + std::to_string(bad) +
-                       " observations have a camera or point index out of range";
+    } else if (f[kBadIndexCount]) {
+      g_create_error = "ba_cost_noalloc: " + std::to_string(f[kBadIndexCount]) +
+                       " observations have a camera or point index out of range (first: "
+                       "observation " + std::to_string(f[kFirstBadObs]) + ")";
+      st = BA_ERR_INVALID_ARG;
+    } else if (f[kFirstBadCam] != none) {
+      g_create_error = "ba_cost_noalloc: camera " + std::to_string(f[kFirstBadCam]) +
+                       " has a non-finite pose or a zero quaternion";
+      st = BA_ERR_INVALID_ARG;
+    } else if (f[kFirstBadPoint] != none) {
+      g_create_error = "ba_cost_noalloc: point " + std::to_string(f[kFirstBadPoint]) +
+                       " is not finite";
+      st = BA_ERR_INVALID_ARG;
+    } else if (f[kFirstBadPixel] != none) {
+      g_create_error = "ba_cost_noalloc: observation " + std::to_string(f[kFirstBadPixel]) +
+                       " has a non-finite pixel";
       st = BA_ERR_INVALID_ARG;
     }
   }

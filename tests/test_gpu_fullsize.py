@@ -64,8 +64,13 @@ def test_final_rmse_within_one_percent_of_oracle(scene, golden, prec):
     r = O.rmse(prob, st, scene.obs_inlier, golden["outlier_threshold_px"])
     r_ref = golden["rmse_inlier_trimmed_px"]
     assert abs(r - r_ref) <= 0.01 * r_ref, (prec, r, r_ref)
+    # the gate on every generator inlier, untrimmed
+    u = O.rmse(prob, st, scene.obs_inlier)
+    u_ref = golden["rmse_inlier_px"]
+    assert abs(u - u_ref) <= 0.01 * u_ref, (prec, u, u_ref)
     # the report's own RMSE is over every observation in front of the camera
     assert rep["rmse_px"] == pytest.approx(O.rmse(prob, st), rel=1e-6)
     assert rep["costs"][-1] <= 1.01 * golden["costs"][-1]
-    print(f"{prec}: trimmed inlier rmse {r:.5f} (oracle {r_ref:.5f}), final cost "
-          f"{rep['costs'][-1]:.7e} (oracle {golden['costs'][-1]:.7e})")
+    print(f"{prec}: inlier rmse trimmed {r:.5f} (oracle {r_ref:.5f}), untrimmed {u:.5f} "
+          f"(oracle {u_ref:.5f}), final cost {rep['costs'][-1]:.7e} "
+          f"(oracle {golden['costs'][-1]:.7e})")

@@ -372,3 +372,133 @@ def test_planted_mistakes_are_caught(monkeypatch):
     monkeypatch.setattr(OB, "damped_blocks", O.damped_blocks)
     _, _, _, _, h_bad, _ = OB.solve_step(prob, lin, 0.5, O.LMOptions(solver="dense"))
     assert np.linalg.norm(h_bad - h) > 1e-6 * np.linalg.norm(h)
+
+
+# --------------------------------------------------------------------------- gain ratio and damping
+#
+# Each pin below is a helper that raises AssertionError when the oracle is
+# wrong, so that the planted-slip test can run it against a broken oracle.
+
+def _check_model_decrease(O_):
+    """The predicted decrease of an LM step is L(0) - L(h) of the
+    Gauss-Newton model L(h) = F + g^T h + 1/2 h^T A h (Madsen, Nielsen &
+    Tingleff 2004, Sec. 3.2), evaluated here from its definition with the
+    full stacked normal equations (A, g pinned against finite differences
+    above) and numpy's solve of the damped system (A + mu D) h = -g.  The
+    oracle's closed form eliminates A through the damped system, so the two
+    agree only if neither the 1/2 nor a sign is lost."""
+    s, prob, st = _tiny(seed=21, n_cams=3, n_pts=15, sigma=1.5)
+    for delta in (0.0, 1.0):
+        A, g = O_.full_normal_equations(prob, st, delta)
+        D = np.maximum(np.diag(A), O_.DIAG_MIN)
+        for mu in (1e-4, 0.3, 20.0):
+            h = np.linalg.solve(A + mu * np.diag(D), -g)
+            ref = -(g @ h) - 0.5 * h @ A @ h
+            assert ref > 0
+            assert O_.model_decrease(h, D, g, mu) == pytest.approx(ref, rel=1e-9), (delta, mu)
+        # the LM loop reaches the same value through the Schur route
+        res = O_.lm_solve(prob, st, O_.LMOptions(huber_delta=delta, lm_iters=1, solver="dense",
+                                                 mu0=0.3))
+        h = np.linalg.solve(A + 0.3 * np.diag(D), -g)
+        assert res.dL[0] == pytest.approx(-(g @ h) - 0.5 * h @ A @ h, rel=1e-8), delta
+
+
+def _check_small_step_gain(O_):
+    """The Gauss-Newton model agrees with F to first order, so the gain ratio
+    (measured over predicted decrease) tends to 1 as heavy damping shrinks the
+    step, the gap shrinking like 1/mu.  With a dropped 1/2 in the predicted
+    decrease it would tend to 1/2, with a flipped sign to -1."""
+    s, prob, st = _tiny(seed=22, n_cams=4, n_pts=30, sigma=1.0)
+    for delta in (0.0, 1.0):
+        gaps = []
+        for mu0 in (1e2, 1e3, 1e4):
+            res = O_.lm_solve(prob, st, O_.LMOptions(huber_delta=delta, lm_iters=1,
+                                                     solver="dense", mu0=mu0))
+            gaps.append(abs(res.gain[0] - 1.0))
+        assert gaps[-1] < 2e-3, (delta, gaps)
+        assert gaps[0] > gaps[1] > gaps[2], (delta, gaps)
+        assert gaps[1] / gaps[2] > 5.0, (delta, gaps)   # about tenfold per decade of mu
+
+
+# (gain ratio, factor on mu) of an accepted step: max(1/3, 1 - (2 gain - 1)^3)
+_NIELSEN_ACCEPTED = [
+    (1.0, 1.0 / 3.0),     # the model predicted the decrease exactly
+    (0.95, 1.0 / 3.0),    # 1 - 0.9^3 = 0.271, held at the lower bound 1/3
+    (0.9, 0.488),         # 1 - 0.8^3
+    (0.75, 0.875),        # 1 - 0.5^3
+    (0.5, 1.0),           # halfway: damping unchanged
+    (0.25, 1.125),        # 1 + 0.5^3
+    (1e-12, 2.0),         # a barely useful step doubles the damping
+]
+
+
+def _check_damping_update(O_):
+    """Nielsen's update (Madsen, Nielsen & Tingleff 2004, eq. 3.16 and the nu
+    rule that follows it), as literal values of its published form."""
+    for gain, factor in _NIELSEN_ACCEPTED:
+        mu, nu = O_.damping_update(3.0, 8.0, gain, True)
+        assert mu == pytest.approx(3.0 * factor, rel=1e-9), (gain, mu / 3.0, factor)
+        assert nu == 2.0
+    # a rejected step multiplies mu by nu and doubles nu, whatever the gain
+    for gain in (-np.inf, -0.5, 0.7):
+        assert O_.damping_update(3.0, 8.0, gain, False) == (24.0, 16.0)
+    # reject, reject, accept exactly: 1e-4 -> 2e-4 -> 8e-4 -> 8e-4 / 3, nu 2 -> 4 -> 8 -> 2
+    mu, nu = 1e-4, 2.0
+    mu, nu = O_.damping_update(mu, nu, -1.0, False)
+    mu, nu = O_.damping_update(mu, nu, -1.0, False)
+    assert (mu, nu) == (pytest.approx(8e-4, rel=1e-15), 8.0)
+    mu, nu = O_.damping_update(mu, nu, 1.0, True)
+    assert (mu, nu) == (pytest.approx(8e-4 / 3.0, rel=1e-15), 2.0)
+
+
+def test_model_decrease_is_the_decrease_of_the_quadratic_model():
+    _check_model_decrease(O)
+
+
+def test_gain_ratio_tends_to_one_as_the_step_shrinks():
+    _check_small_step_gain(O)
+
+
+def test_damping_update_matches_its_published_form():
+    _check_damping_update(O)
+
+
+def test_lm_loop_applies_the_pinned_damping_update():
+    """The damping each iteration uses follows from the previous iteration's
+    damping, gain ratio and decision through the pinned update (nu tracked
+    alongside), over a run with accepted and rejected steps."""
+    s = scenes.make_scene("ring", seed=17, n_cams=8, n_pts=300)
+    prob = _problem(s)
+    res = O.lm_solve(prob, O.state_from_qt(s.cam_qt, s.pts), O.LMOptions(lm_iters=20,
+                                                                         solver="dense"))
+    assert res.accepted.any() and (~res.accepted).any()
+    assert res.mu[0] == O.LMOptions().mu0
+    nu = O.LMOptions().nu0
+    for k in range(len(res.mu) - 1):
+        mu_next, nu = O.damping_update(res.mu[k], nu, res.gain[k], bool(res.accepted[k]))
+        assert res.mu[k + 1] == mu_next, k
+
+
+def test_planted_slips_in_gain_ratio_and_damping_are_caught(monkeypatch):
+    """A dropped 1/2 or a flipped sign in the predicted decrease, and a wrong
+    exponent or bound in the damping update, each fail a pin above."""
+    import oracle.ba_oracle as OB
+    good_dl = OB.model_decrease
+    for bad in (lambda h, D, g, mu: 2.0 * good_dl(h, D, g, mu),      # 1/2 dropped
+                lambda h, D, g, mu: 0.5 * float(h @ (mu * D * h + g))):  # sign of g flipped
+        with monkeypatch.context() as m:
+            m.setattr(OB, "model_decrease", bad)
+            for pin in (_check_model_decrease, _check_small_step_gain):
+                with pytest.raises(AssertionError):
+                    pin(OB)
+    good_du = OB.damping_update
+    for bad in (lambda mu, nu, gain, acc: (mu * max(1 / 3, 1 - (2 * gain - 1) ** 2), 2.0)
+                if acc else (mu * nu, 2 * nu),                        # square, not cube
+                lambda mu, nu, gain, acc: (mu * max(1 / 2, 1 - (2 * gain - 1) ** 3), 2.0)
+                if acc else (mu * nu, 2 * nu),                        # bound 1/2, not 1/3
+                lambda mu, nu, gain, acc: good_du(mu, nu, gain, acc) if acc
+                else (mu * nu, nu)):                                  # nu not doubled
+        with monkeypatch.context() as m:
+            m.setattr(OB, "damping_update", bad)
+            with pytest.raises(AssertionError):
+                _check_damping_update(OB)
