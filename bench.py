@@ -177,13 +177,16 @@ def algorithmic_bytes(s, nnzb, kernel, fp32=True, pcg_iters=100):
 
 # --------------------------------------------------------------------------- our arm
 
-def run_ours(args, rank, world, local_rank):
+def run_ours(args, rank, world, local_rank, workload=None):
+    """One workload's solve in the timed configuration (FP32 path, inputs
+    resident, L2 flushed between steps), its FP64 path and its end-to-end
+    rate through the C ABI from host buffers."""
     import torch
     from paper_2510_15271_b300 import ba
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    s = make_workload(args.workload, replica_seed(args.seed, rank))
+    s = make_workload(workload or args.workload, replica_seed(args.seed, rank))
     iters = s.lm_iters
     work = s.n_obs * iters  # obs*iters per step
 
@@ -242,6 +245,7 @@ def run_ours(args, rank, world, local_rank):
     kstats = ba.ba_kernel_stats(h32)
     last = reps32[-1]
     launches_per_step = last["n_kernels"] + (2 if s.precision == "fp32" else 1)  # + state reset
+    q32, _ = ba.ba_get_state(h32, s.n_cams, s.n_pts)
     h32.close()
     # the same solve without the event nodes, to show what they cost
     hp = make_handle("fp32", profile=False)
@@ -254,11 +258,16 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_fp64:
         h64 = make_handle("fp64", profile=False)
         ms64, reps64 = timed(h64, args.fp64_steps, 1)
+        q64, _ = ba.ba_get_state(h64, s.n_cams, s.n_pts)
         h64.close()
+        rot, pos = pose_errors_qt(q32, q64)
         fp64 = {"value": work * args.fp64_steps * world / (ms64 / 1e3), "unit": UNIT,
                 "ms_per_step": ms64 / args.fp64_steps,
                 "final_cost": float(reps64[-1]["costs"][-1]),
-                "rmse_px": float(reps64[-1]["rmse_px"])}
+                "rmse_px": float(reps64[-1]["rmse_px"]),
+                "pcg_iters": int(np.sum(reps64[-1]["pcg_iters"])),
+                "pose_diff_fp32_vs_fp64": {"max_rad": float(rot.max()), "mean_rad": float(rot.mean()),
+                                           "max_m": float(pos.max()), "mean_m": float(pos.mean())}}
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
@@ -297,29 +306,68 @@ def run_ours(args, rank, world, local_rank):
         e2e = {"value": work * n_e2e * world / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": dt / n_e2e * 1e3}
 
+    pcg_kernel = {1: "k_pcg", 2: "k_pcg", 3: "k_pcg_cluster", 4: "k_pcg_stream"}.get(
+        int(last.get("pcg_variant", 0)), None)
     return dict(s=s, work=work, ms32=ms32, reps=reps32, kstats=kstats, clocks=clocks,
                 launches_per_step=launches_per_step, fp64=fp64, e2e=e2e,
-                ms_plain_per_step=ms_plain_per_step)
+                ms_plain_per_step=ms_plain_per_step, pcg_kernel=pcg_kernel)
+
+
+def leg_summary(res, args, peak, peak_kind):
+    """The fields of one workload's solve for the JSON line."""
+    top, per = roofline(res, peak, peak_kind)
+    steps = args.steps
+    rep = res["reps"][-1]
+    return {
+        "config": _config(args, res["s"]),
+        "value": res["work"] * steps / (res["ms32"] / 1e3), "unit": UNIT,
+        "ms_per_step": res["ms32"] / steps, "roofline": top, "kernel_rooflines": per,
+        "e2e": res["e2e"], "fp64_path": res["fp64"], "pcg_kernel": res["pcg_kernel"],
+        "kernels_ms_per_step": {k: round(v[1], 4) for k, v in res["kstats"].items()},
+        "ms_per_step_without_event_nodes": res["ms_plain_per_step"],
+        "solve": {"final_cost": float(rep["costs"][-1]), "rmse_px": float(rep["rmse_px"]),
+                  "pcg_iters": [int(v) for v in rep["pcg_iters"]],
+                  "accepted": int(rep["n_accepted"])},
+    }
 
 
 def cpu_baseline(s, iters, kind="oracle"):
-    """The FP64 oracle, as it stands, for `iters` LM iterations on scene s."""
+    """The FP64 oracle, as it stands, for `iters` LM iterations on scene s
+    (its PCG refined as the recipe refines it)."""
     import oracle as O
     prob = O.Problem.from_arrays(s.intrinsics(), s.obs_cam, s.obs_pt, s.obs_uv, s.cam_fixed,
                                  s.n_cams, s.n_pts)
     st = O.state_from_qt(s.cam_qt, s.pts)
     t0 = time.perf_counter()
     O.lm_solve(prob, st, O.LMOptions(huber_delta=s.huber_delta, lm_iters=iters, solver=s.solver,
-                                     pcg_tol=s.pcg_tol, pcg_max_iters=s.pcg_max_iters))
+                                     pcg_tol=s.pcg_tol, pcg_max_iters=s.pcg_max_iters,
+                                     refine_max=5 if s.refine else 0))
     dt = time.perf_counter() - t0
     return s.n_obs * iters / dt, dt
 
 
-def roofline(res, peak_gbs, peak_kind):
+def cpu_sample(name, seed):
+    """The bounded sample of a workload the CPU baseline times (about 10-30 s
+    of oracle work per LM iteration on the host cores)."""
+    from paper_2510_15271_b300 import scenes
+    kw = {"driving": {}, "city": dict(n_cams=1000, n_pts=200000)}.get(name, {})
+    return scenes.make_scene(name, seed=seed, **kw), kw
+
+
+def _working_launches(res, name):
+    """Launches of a kernel that did work: after a rejected step the
+    linearisation kernels return at once, so their per-launch time is taken
+    over the accepted steps plus the first (one linearisation each)."""
+    launches, total_ms = res["kstats"][name]
+    if name in ("lin_cam", "lin_pt"):
+        rep = res["reps"][-1]
+        launches = max(1, min(launches, 1 + int(rep["n_accepted"])))
+    return launches, total_ms
+
+
+def kernel_roofline(res, name, peak_gbs, peak_kind, nnzb):
     s = res["s"]
-    nnzb, sumL2 = camera_pairs(s)
-    ks = res["kstats"]
-    name, (launches, total_ms) = max(ks.items(), key=lambda kv: kv[1][1])
+    launches, total_ms = _working_launches(res, name)
     per_launch_ms = total_ms / launches
     mean_pcg = float(np.mean(res["reps"][-1]["pcg_iters"])) if name == "pcg" else 0
     nbytes = algorithmic_bytes(s, nnzb, name, True, pcg_iters=mean_pcg)
@@ -328,19 +376,44 @@ def roofline(res, peak_gbs, peak_kind):
            "unit": "GB/s", "frac": round(achieved / peak_gbs, 4),
            "traffic": measured_traffic(s, name),
            "peak_source": peak_kind, "bytes_per_launch": int(nbytes),
-           "launch_ms": round(per_launch_ms, 4), "nnzb": nnzb, "sum_track_len_sq": sumL2}
+           "launch_ms": round(per_launch_ms, 4), "launches": int(launches)}
     if name == "pcg" and mean_pcg > 0:
-        # S is staged in shared memory once per launch, so the per-iteration
-        # bytes above never reach DRAM: the fraction measures the iteration
-        # latency (two grid barriers per iteration), not bandwidth.
         out["per_iter_us"] = round(per_launch_ms * 1e3 / mean_pcg, 2)
-        out["limiter"] = "grid-barrier latency (S resident in shared memory)"
+        if res.get("pcg_kernel") == "k_pcg_stream":
+            out["limiter"] = ("S streamed from HBM through shared memory by bulk copies every "
+                              "product, one grid-wide reduction per half-iteration")
+        else:
+            # S is staged in shared memory once per launch, so the per-iteration
+            # bytes never reach DRAM: the fraction measures the iteration latency
+            out["limiter"] = "grid-barrier latency (S resident in shared memory)"
     return out
 
 
-PROFILE_KERNELS = os.path.join(ROOT, "profiles", "driving_fp32_kernels.md")
-_PROFILE_NAMES = {"pcg": "k_pcg", "schur": "k_schur", "backsub": "k_backsub",
-                  "lin_cam": "k_lin_cam", "lin_pt": "k_lin_pt", "cost_trial": "k_cost"}
+ROOFLINE_KERNELS = ("lin_cam", "lin_pt", "damp_pt", "schur", "pcg", "backsub", "cost_trial")
+
+
+def roofline(res, peak_gbs, peak_kind):
+    """The dominant kernel's roofline (the line's `roofline`) and every main
+    kernel's (`kernel_rooflines`)."""
+    s = res["s"]
+    nnzb, sumL2 = camera_pairs(s)
+    ks = res["kstats"]
+    name = max(ks.items(), key=lambda kv: kv[1][1])[0]
+    top = kernel_roofline(res, name, peak_gbs, peak_kind, nnzb)
+    top["nnzb"] = nnzb
+    top["sum_track_len_sq"] = sumL2
+    per = {k: kernel_roofline(res, k, peak_gbs, peak_kind, nnzb)
+           for k in ROOFLINE_KERNELS if k in ks}
+    return top, per
+
+
+def profile_path(workload):
+    return os.path.join(ROOT, "profiles", f"{workload}_fp32_kernels.md")
+
+
+_PROFILE_NAMES = {"pcg": ("k_pcg_stream", "k_pcg"), "schur": ("k_schur",),
+                  "backsub": ("k_backsub",), "lin_cam": ("k_lin_cam",), "lin_pt": ("k_lin_pt",),
+                  "cost_trial": ("k_cost",), "damp_pt": ("k_damp_pt",)}
 
 
 # The sources of the single-problem path the driving profile covers: its
@@ -348,7 +421,8 @@ _PROFILE_NAMES = {"pcg": "k_pcg", "schur": "k_schur", "backsub": "k_backsub",
 # host code that plans their launches (the multi-problem engine, the server
 # and the opt-in cluster PCG are not on this path).
 DRIVING_SOURCES = ("ba_api.cu", "ba_device.cuh", "ba_internal.h", "handle.h", "layout.cu",
-                   "layout.h", "lm.h", "lm_kernels.cu", "solvers.cu", "../../include/ba.h")
+                   "layout.h", "lm.h", "lm_kernels.cu", "solvers.cu", "pcg_stream.cu",
+                   "../../include/ba.h")
 
 
 def source_digest():
@@ -367,15 +441,16 @@ def measured_traffic(s, name):
     """DRAM bytes per launch of `name` from the committed ncu summary of the
     driving FP32 workload, or None when the workload differs or the kernel
     sources changed since the capture."""
-    if s.name != "driving" or name not in _PROFILE_NAMES or not os.path.exists(PROFILE_KERNELS):
+    path = profile_path(s.name)
+    if name not in _PROFILE_NAMES or not os.path.exists(path):
         return None
-    text = open(PROFILE_KERNELS).read()
+    text = open(path).read()
     m = re.search(r"Source digest.*?`([0-9a-f]{16})`", text, re.S)
     if not m or m.group(1) != source_digest():
         return None
     for line in text.splitlines():
         cells = [c.strip() for c in line.strip().strip("|").split("|")]
-        if len(cells) > 4 and cells[0] == _PROFILE_NAMES[name]:
+        if len(cells) > 4 and cells[0] in _PROFILE_NAMES[name]:
             return int(cells[4])
     return None
 
@@ -487,26 +562,65 @@ def run_batched(args, local_rank):
     }
 
 
-def run_served(args, local_rank):
-    """Served local BA: Poisson arrivals replaying a pool of seeded requests
-    (cameras log-uniform [10, 200], points log-uniform [1k, 40k], track length
-    2 + Geometric(mean 3)); p50 / p99 of submit-to-result latency."""
-    from paper_2510_15271_b300 import ba, scenes
-    pool = [scenes.make_request(5000 + i) for i in range(args.serve_pool)]
-    arrs = [ba._ProblemArrays.from_scene(r) for r in pool]
-    arrivals = scenes.poisson_arrivals(args.serve_rate, args.serve_seconds, seed=5)
-    o = ba.options_for_scene(pool[0], "fp32", device=local_rank)
-    o.serve_slots = args.serve_slots
-    o.serve_queue = 1 << 20
-    o.serve_arena_bytes = args.serve_arena_gb << 30
-    o.serve_split_ms = args.serve_split_ms
-    lat, cams, obs_done = [], [], 0
-    with ba.ba_create_server(o) as h:
-        for a in arrs[:8]:  # warm-up
+def _request_arrays(seed):
+    """One served request of the recipe (a worker-process task: no CUDA)."""
+    from paper_2510_15271_b300 import scenes
+    r = scenes.make_request(seed)
+    return (r.n_cams, r.lm_iters, r.cam_qt, r.pts, r.obs_cam, r.obs_pt, r.obs_uv, r.cam_fixed,
+            tuple(r.intrinsics()))
+
+
+def request_pool(n, first_seed=5000):
+    """n distinct seeded requests, generated in parallel on the host cores
+    (spawned workers: the parent may already hold a CUDA context) and cached
+    on local disk by seed range, outside any timed region."""
+    import multiprocessing
+    import pickle
+    from concurrent.futures import ProcessPoolExecutor
+    path = os.path.join(tempfile.gettempdir(), f"ba_request_pool_{first_seed}_{n}.pkl")
+    if os.path.exists(path):
+        try:
+            with open(path, "rb") as f:
+                return pickle.load(f), 0.0
+        except Exception:
+            pass
+    t0 = time.perf_counter()
+    workers = max(1, min(len(os.sched_getaffinity(0)), 32))
+    with ProcessPoolExecutor(max_workers=workers,
+                             mp_context=multiprocessing.get_context("spawn")) as ex:
+        pool = list(ex.map(_request_arrays, range(first_seed, first_seed + n), chunksize=8))
+    dt = time.perf_counter() - t0
+    try:
+        with open(path, "wb") as f:
+            pickle.dump(pool, f, protocol=pickle.HIGHEST_PROTOCOL)
+    except Exception:
+        pass
+    return pool, dt
+
+
+def _serve(ba, pool_arrs, pool, arrivals, opts, cams_split=96):
+    """Replay Poisson arrivals against one server; request i is pool item
+    i mod len(pool).  Returns latencies, camera counts, per-item RMSE, span."""
+    lat, cams, rmse, obs_done = [], [], {}, 0
+    with ba.ba_create_server(opts) as h:
+        for a in pool_arrs[:8]:  # warm-up
             rid = ba.ba_submit(h, a)
             while ba.ba_poll(h, rid) is None:
                 time.sleep(1e-4)
         pending = {}
+
+        def collect(rid):
+            nonlocal obs_done
+            r = ba.ba_poll(h, rid)
+            if r is None:
+                return False
+            j = pending.pop(rid)
+            lat.append(r.latency_ms)
+            cams.append(pool[j][0])
+            rmse[j] = r.rmse_px
+            obs_done += len(pool[j][4])
+            return True
+
         t0 = time.perf_counter()
         for i, ta in enumerate(arrivals):
             while True:
@@ -515,49 +629,101 @@ def run_served(args, local_rank):
                     break
                 if pending and len(pending) > 64:
                     for rid in list(pending)[:16]:
-                        r = ba.ba_poll(h, rid)
-                        if r is not None:
-                            lat.append(r.latency_ms)
-                            j = pending.pop(rid)
-                            cams.append(pool[j].n_cams)
-                            obs_done += len(pool[j].obs_cam)
+                        collect(rid)
                 else:
                     time.sleep(min(ta - now, 2e-4))
-            j = i % len(arrs)
-            pending[ba.ba_submit(h, arrs[j])] = j
+            j = i % len(pool_arrs)
+            pending[ba.ba_submit(h, pool_arrs[j])] = j
         while pending:
             for rid in list(pending):
-                r = ba.ba_poll(h, rid)
-                if r is not None:
-                    lat.append(r.latency_ms)
-                    j = pending.pop(rid)
-                    cams.append(pool[j].n_cams)
-                    obs_done += len(pool[j].obs_cam)
+                collect(rid)
             time.sleep(2e-4)
         span = time.perf_counter() - t0
         st = ba.ba_kernel_stats(h)
-    lat, cams = np.array(lat), np.array(cams)
-    big = cams > 96  # latency by window size
-    return {
+    return np.array(lat), np.array(cams), rmse, obs_done, span, st
+
+
+def _latency_summary(lat, cams, span, obs_done, iters, split=96):
+    big = cams > split
+    pct = lambda v, q: float(np.percentile(v, q)) if v.size else None
+    return {"requests": int(lat.size), "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
+            "max_ms": float(lat.max()), "throughput_req_s": lat.size / span,
+            "value": obs_done * iters / span, "unit": UNIT,
+            "p50_ms_small": pct(lat[~big], 50), "p99_ms_small": pct(lat[~big], 99),
+            "p50_ms_large": pct(lat[big], 50), "p99_ms_large": pct(lat[big], 99)}
+
+
+def run_served(args, local_rank):
+    """Served local BA (config 5): Poisson arrivals at the stated rate for the
+    stated time against one FP32 server, replaying a pool of distinct seeded
+    requests (cameras log-uniform [10, 200], points log-uniform [1k, 40k],
+    track length 2 + Geometric(mean 3)); p50 / p99 of submit-to-result
+    latency.  Beside it, at equal final RMSE: an FP64 server at the same
+    offered rate (a shorter run) and the plain FP64 path (one ba_solve per
+    request, one at a time) on a sample of the pool."""
+    from paper_2510_15271_b300 import ba, scenes
+    pool, gen_s = request_pool(args.serve_pool)
+    arrs = [ba._ProblemArrays(q, p, c, j, uv, K, fx) for (_, _, q, p, c, j, uv, fx, K) in pool]
+    iters = pool[0][1]
+    arrivals = scenes.poisson_arrivals(args.serve_rate, args.serve_seconds, seed=5)
+    o = ba.ba_options_default(precision=ba.BA_FP32, solver=ba.BA_SOLVER_DENSE, max_lm_iters=iters,
+                              device=local_rank)
+    o.serve_slots = args.serve_slots
+    o.serve_queue = 1 << 20
+    o.serve_arena_bytes = args.serve_arena_gb << 30
+    o.serve_split_ms = args.serve_split_ms
+    lat, cams, rmse32, obs_done, span, st = _serve(ba, arrs, pool, arrivals, o)
+    out = {
         "workload": f"Poisson arrivals at {args.serve_rate:g} req/s for {args.serve_seconds:g} s "
-                    f"({len(arrivals)} requests replaying {len(pool)} seeded requests: cameras "
-                    "log-uniform [10, 200], points log-uniform [1k, 40k], track 2 + Geometric(3)), "
-                    f"{pool[0].lm_iters} LM iterations, FP32 with FP64 gain / damping",
-        "requests": int(lat.size), "p50_ms": float(np.percentile(lat, 50)),
-        "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()),
-        "throughput_req_s": lat.size / span, "value": obs_done * pool[0].lm_iters / span,
-        "unit": UNIT, "ticks": int(st["serve_tick"][0]),
+                    f"({len(arrivals)} requests replaying {len(pool)} distinct seeded requests: "
+                    "cameras log-uniform [10, 200], points log-uniform [1k, 40k], track 2 + "
+                    f"Geometric(3)), {iters} LM iterations, FP32 with FP64 gain / damping",
+        **_latency_summary(lat, cams, span, obs_done, iters),
+        "ticks": int(st["serve_tick"][0]),
         "tick_busy_frac": st["serve_tick"][1] / 1e3 / span,
         "large_launches": int(st["serve_large"][0]),
         "tick_mean_ctas": int(st["serve_tick_ctas"][0]),
         "tick_mean_requests": round(float(st["serve_tick_ctas"][1]), 1),
         "tick_mean_ms": round(st["serve_tick"][1] / max(st["serve_tick"][0], 1), 2),
-        "p50_ms_small": float(np.percentile(lat[~big], 50)) if (~big).any() else None,
-        "p99_ms_small": float(np.percentile(lat[~big], 99)) if (~big).any() else None,
-        "p50_ms_large": float(np.percentile(lat[big], 50)) if big.any() else None,
-        "p99_ms_large": float(np.percentile(lat[big], 99)) if big.any() else None,
-        "mean_obs_per_request": float(np.mean([len(r.obs_cam) for r in pool])),
+        "mean_obs_per_request": float(np.mean([len(r[4]) for r in pool])),
+        "pool_generate_s": round(gen_s, 1),
     }
+    if args.serve_fp64_seconds > 0:
+        # the same offered load on an FP64 server (shorter: it does not keep up)
+        arr64 = scenes.poisson_arrivals(args.serve_rate, args.serve_fp64_seconds, seed=5)
+        o64 = ba.ba_options_default(precision=ba.BA_FP64, solver=ba.BA_SOLVER_DENSE,
+                                    max_lm_iters=iters, device=local_rank)
+        for k in ("serve_slots", "serve_queue", "serve_arena_bytes", "serve_split_ms"):
+            setattr(o64, k, getattr(o, k))
+        l64, c64, rmse64, od64, sp64, _ = _serve(ba, arrs, pool, arr64, o64)
+        both = [j for j in rmse64 if j in rmse32]
+        rel = [abs(rmse32[j] - rmse64[j]) / rmse64[j] for j in both]
+        out["fp64_server"] = {"offered": f"{args.serve_rate:g} req/s for "
+                                         f"{args.serve_fp64_seconds:g} s",
+                              **_latency_summary(l64, c64, sp64, od64, iters)}
+        out["rmse_fp32_vs_fp64_max_rel"] = float(max(rel)) if rel else None
+        out["rmse_compared_requests"] = len(both)
+    if args.serve_plain_sample > 0:
+        # the plain FP64 path: one request at a time through ba_solve
+        t_req, od = [], 0
+        for (nc, it, q, p, c, j, uv, fx, K) in pool[:args.serve_plain_sample]:
+            t0 = time.perf_counter()
+            op = ba.ba_options_default(precision=ba.BA_FP64, solver=ba.BA_SOLVER_DENSE,
+                                       max_lm_iters=it, device=local_rank)
+            with ba.ba_create(op) as h:
+                ba.ba_set_problem(h, q, p, c, j, uv, K, fx)
+                ba.ba_solve(h)
+                ba.ba_get_state(h, nc, p.shape[0])
+            t_req.append(1e3 * (time.perf_counter() - t0))
+            od += len(c)
+        t_req = np.array(t_req)
+        out["plain_fp64_path"] = {
+            "sample": f"the first {len(t_req)} pool requests, one at a time (ba_create, "
+                      "ba_set_problem, ba_solve, ba_get_state)",
+            "p50_ms": float(np.percentile(t_req, 50)), "p99_ms": float(np.percentile(t_req, 99)),
+            "throughput_req_s": len(t_req) / (t_req.sum() / 1e3),
+            "value": od * iters / (t_req.sum() / 1e3), "unit": UNIT}
+    return out
 
 
 def run_outer(args, s, local_rank, peak):
@@ -779,7 +945,7 @@ def run_rig(args, local_rank):
 
 def run_reference(args):
     """The FP64 CPU oracle, as it stands, on the host cores: each step is one
-    LM iteration on a 300-camera sample of the driving recipe."""
+    LM iteration on a 300-camera sample of the workload's recipe."""
     from paper_2510_15271_b300 import scenes
     full = scenes.make_scene(args.workload, seed=args.seed)
     s = scenes.make_scene(args.workload, seed=args.seed, **_reference_sample(args.workload))
@@ -812,17 +978,20 @@ def _reference_sample(name):
     if name == "driving":
         return dict(n_cams=300, n_pts=60000, length_m=600.0)
     if name == "city":
-        return dict(n_cams=1000, n_pts=200000)
+        return dict(n_cams=300, n_pts=60000)
     return {}
 
 
 def _config(args, s):
-    return {"workload": f"{args.workload} BA: {s.n_cams} cameras, {s.n_pts} points, "
+    refine = ", FP64 iterative refinement of the PCG residual (<= 5 outer steps, 1e-6)" \
+        if s.refine else ""
+    return {"workload": f"{s.name} BA: {s.n_cams} cameras, {s.n_pts} points, "
                         f"{s.n_obs} observations, {s.lm_iters} LM iterations, Huber "
                         f"{s.huber_delta} px, {s.solver} solver (tol {s.pcg_tol}, max "
-                        f"{s.pcg_max_iters}), FP32 with FP64 cost / gain / damping / 3x3 inverses",
+                        f"{s.pcg_max_iters}){refine}, FP32 with FP64 cost / gain / damping / "
+                        "3x3 inverses",
             "n_cams": s.n_cams, "n_pts": s.n_pts, "n_obs": s.n_obs, "lm_iters": s.lm_iters,
-            "seed": args.seed, "l2": "flushed between steps (256 MB write inside the timed region)",
+            "seed": s.seed, "l2": "flushed between steps (256 MB write inside the timed region)",
             "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
 
 
@@ -834,7 +1003,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="driving", choices=["driving", "city", "ring"])
+    ap.add_argument("--workload", default="city", choices=["driving", "city", "ring"])
+    ap.add_argument("--no-driving", action="store_true",
+                    help="skip the driving leg (run beside a city headline)")
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -854,8 +1025,13 @@ def main():
                     help="threads,ctas_per_sm for the batched solver instead of the autotuner")
     ap.add_argument("--plain-sample", type=int, default=16)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
-    ap.add_argument("--serve-seconds", type=float, default=5.0)
-    ap.add_argument("--serve-pool", type=int, default=96)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-pool", type=int, default=2048,
+                    help="distinct seeded requests the arrivals replay")
+    ap.add_argument("--serve-fp64-seconds", type=float, default=10.0,
+                    help="served leg: FP64 server at the same offered rate (0: off)")
+    ap.add_argument("--serve-plain-sample", type=int, default=64,
+                    help="served leg: requests solved one at a time by the plain FP64 path")
     ap.add_argument("--serve-slots", type=int, default=1024)
     ap.add_argument("--serve-arena-gb", type=int, default=32)
     ap.add_argument("--serve-split-ms", type=float, default=10.0,
@@ -892,28 +1068,33 @@ def main():
         return
     peak, peak_kind = _peaks()
     s = res["s"]
+    head = leg_summary(res, args, peak, peak_kind)
     value = whole_job_value(res["work"], args.steps, world, res["ms32"])
     line = {
         "impl": "ours", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms32"] / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic", "config": _config(args, s),
-        "roofline": roofline(res, peak, peak_kind),
+        "data": "synthetic", "config": head["config"],
+        "roofline": head["roofline"], "kernel_rooflines": head["kernel_rooflines"],
         "e2e": res["e2e"], "gpu_launches": res["launches_per_step"] * args.steps,
-        "clocks": res["clocks"], "fp64_path": res["fp64"],
-        "kernels_ms_per_step": {k: round(v[1] / 1.0, 4) for k, v in res["kstats"].items()},
-        "ms_per_step_without_event_nodes": res["ms_plain_per_step"],
-        "solve": {"final_cost": float(res["reps"][-1]["costs"][-1]),
-                  "rmse_px": float(res["reps"][-1]["rmse_px"]),
-                  "pcg_iters": [int(v) for v in res["reps"][-1]["pcg_iters"]],
-                  "accepted": int(res["reps"][-1]["n_accepted"])},
+        "clocks": res["clocks"], "fp64_path": res["fp64"], "pcg_kernel": head["pcg_kernel"],
+        "kernels_ms_per_step": head["kernels_ms_per_step"],
+        "ms_per_step_without_event_nodes": head["ms_per_step_without_event_nodes"],
+        "solve": head["solve"],
     }
+    sd = s if s.name == "driving" else None
+    if s.name != "driving" and not args.no_driving:
+        # the driving-sequence workload as a second leg, same timing rules
+        rd = run_ours(args, 0, 1, local_rank, workload="driving")
+        line["driving"] = leg_summary(rd, args, peak, peak_kind)
+        line["driving"]["clocks"] = rd["clocks"]
+        sd = rd["s"]
     if not args.no_batched:
         line["batched"] = run_batched(args, 0)
-    if not args.no_outer:
-        line["outer_loop"] = run_outer(args, s, 0, peak)
-    if not args.no_priors and args.workload == "driving":
-        line["pose_priors"] = run_priors(args, s, 0)
+    if not args.no_outer and sd is not None:
+        line["outer_loop"] = run_outer(args, sd, 0, peak)
+    if not args.no_priors and sd is not None:
+        line["pose_priors"] = run_priors(args, sd, 0)
     if not args.no_pgo:
         line["pose_graph"] = run_pose_graph(args, 0)
     if not args.no_rig:
@@ -923,11 +1104,15 @@ def main():
         line["local_ba_p50_ms"] = line["served"]["p50_ms"]
         line["local_ba_p99_ms"] = line["served"]["p99_ms"]
     if not args.no_cpu:
-        v, dt = cpu_baseline(s, args.cpu_iters)
+        # the oracle on a bounded sample of the headline workload
+        cs, kw = cpu_sample(s.name, s.seed)
+        iters = 1 if kw else args.cpu_iters
+        v, dt = cpu_baseline(cs, iters)
+        what = (f"{iters} LM iteration(s) of a {cs.n_cams}-camera / {cs.n_pts}-point / "
+                f"{cs.n_obs}-observation sample of the {s.name} recipe" if kw else
+                f"{iters} LM iterations of the full workload")
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": len(os.sched_getaffinity(0)),
-                                "kind": "oracle",
-                                "sample": f"{args.cpu_iters} LM iterations of the full workload "
-                                          f"({dt:.1f} s)"}
+                                "kind": "oracle", "sample": f"{what} ({dt:.1f} s)"}
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch

@@ -74,7 +74,9 @@ typedef struct {
   double huber_delta;   /* Huber threshold in px; <= 0: plain least squares   */
   double pcg_tol;       /* stop when ||r|| <= pcg_tol ||b||                    */
   int pcg_max_iters;    /* cap on products with S per solve (per inner solve) */
-  int refine;           /* BA_FP32 + PCG: FP64 iterative refinement           */
+  int refine;           /* PCG: iterative refinement on the FP64 residual
+                           b - S x (with BA_FP64 this is PCG restarted from
+                           the current iterate)                               */
   int refine_max;       /* outer refinement steps (default 5)                 */
   double refine_tol;    /* stop refinement at ||b - S x|| <= tol ||b||        */
   double mu0;           /* initial damping (default 1e-4)                     */
@@ -93,15 +95,19 @@ typedef struct {
                                between the kernels of the captured loop)      */
   int pcg_variant;          /* PCG kernel.  0: auto (2 when the reduced
                                system stays in shared memory and there is no
-                               refinement, else 1); 1: standard PCG on
-                               a cooperative grid
+                               refinement, 4 when it does not stay resident,
+                               else 1); 1: standard PCG on a cooperative grid
                                (two grid barriers per iteration); 2:
                                pipelined PCG (one grid barrier per iteration,
                                recurrence vectors in FP64); 3: standard
                                PCG in one thread-block cluster (hardware
                                cluster barriers, exchanges through
                                distributed shared memory; falls back to 1
-                               when S does not fit, or with refinement)      */
+                               when S does not fit, or with refinement); 4:
+                               standard PCG with S streamed through shared
+                               memory by bulk copies, one CTA per SM and the
+                               same number of blocks of S per CTA (falls back
+                               to 1 when its plan does not fit)              */
   double mu_min;            /* floor of the damping used in the linear system;
                                < 0: auto (1e-4 for BA_FP32, where rounding in
                                the FP32 Schur complement otherwise exceeds its
@@ -166,7 +172,8 @@ typedef struct {
   double solve_ms;                   /* device time of the LM loop           */
   double setup_ms;                   /* device time of ba_set_problem        */
   int32_t n_kernels;                 /* library kernels launched by the solve */
-  int32_t pad;
+  int32_t pcg_variant;               /* PCG kernel the solve ran (the values of
+                                        ba_options.pcg_variant; 0: dense)     */
 } ba_report;
 
 /* Per-kernel device time of the last ba_solve (opts.profile = 1 only). */

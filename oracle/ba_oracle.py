@@ -35,9 +35,13 @@ Readings where the paper is silent (listed with reasons in the design notes):
     means plain least squares;
   * observations with depth z < 1e-3 get weight 0 and leave the cost;
   * damping: (A + mu D) h = -g with D = diag(A) clamped to >= 1e-12,
-    mu_0 = 1e-4, nu_0 = 2; accept iff dL > 0 and gain ratio > 0;
+    mu_0 = 1e-4, nu_0 = 2; accept iff dL > 0 and gain ratio > 0; optionally
+    a floor mu >= mu_min after accepted steps (the reduced-precision path's
+    schedule, for comparisons at equal algorithm; 0 by default);
   * PCG starts at x = 0 and stops when ||r|| <= tol ||b|| or after max
-    iterations (or early, should p^T S p fail to be positive);
+    iterations (or early, should p^T S p fail to be positive); the
+    city-scale workload wraps it in iterative refinement (at most 5 outer
+    steps on the FP64 residual, stop at ||b - S x|| <= 1e-6 ||b||);
   * a Cholesky factorisation that fails (S not numerically positive
     definite) counts as a rejected step.
 """
@@ -56,7 +60,7 @@ __all__ = [
     "state_from_qt", "state_to_qt", "se3_retract", "retract",
     "huber_rho", "huber_weight", "residuals", "cost", "linearize", "block_sums",
     "damped_blocks", "schur_system", "back_substitute", "full_normal_equations",
-    "pcg_block_jacobi", "solve_step", "model_decrease", "damping_update", "lm_solve",
+    "pcg_block_jacobi", "pcg_refined", "solve_step", "model_decrease", "damping_update", "lm_solve",
     "rmse", "pose_errors", "umeyama_sim3",
 ]
 
@@ -448,6 +452,29 @@ def pcg_block_jacobi(S: np.ndarray, b: np.ndarray, tol: float, max_iters: int, b
     return x, k, rel
 
 
+def pcg_refined(S: np.ndarray, b: np.ndarray, tol: float, max_iters: int, refine_max: int,
+                refine_tol: float):
+    """Iterative refinement around the PCG above (Carson & Higham 2018), the
+    solver of the city-scale mapping workload (reading C11): from x = 0, at
+    most refine_max times compute the residual r = b - S x, stop once
+    ||r|| <= refine_tol ||b||, else solve S d = r by PCG (tol, max_iters) and
+    set x = x + d.  With the residual in the same FP64 as everything else
+    this is PCG restarted from the current iterate.  Returns (x, total
+    products with S, ||b - S x|| / ||b||)."""
+    x = np.zeros_like(b)
+    bnorm = float(np.linalg.norm(b))
+    total = 0
+    for _ in range(refine_max):
+        r = b - S @ x
+        if float(np.linalg.norm(r)) <= refine_tol * bnorm:
+            break
+        d, k, _ = pcg_block_jacobi(S, r, tol, max_iters)
+        x = x + d
+        total += k
+    rel = float(np.linalg.norm(b - S @ x)) / bnorm if bnorm > 0 else 0.0
+    return x, total, rel
+
+
 # ----------------------------------------------------------------------------- LM
 
 @dataclasses.dataclass
@@ -457,8 +484,11 @@ class LMOptions:
     solver: str = "dense"        # "dense" (Schur + Cholesky), "pcg" (Schur + PCG), "full"
     pcg_tol: float = 1e-6
     pcg_max_iters: int = 100
+    refine_max: int = 0          # > 0: PCG inside iterative refinement (pcg_refined)
+    refine_tol: float = 1e-6
     mu0: float = 1e-4
     nu0: float = 2.0
+    mu_min: float = 0.0          # damping floor after an accepted step (the FP32 path's, C15)
     prior_seq: float = 0.0       # lambda_c of the sequential pose prior (oracle/priors.py)
     prior_abs: float = 0.0       # lambda_a of the absolute pose prior
 
@@ -507,6 +537,9 @@ def solve_step(prob: Problem, lin, mu: float, opts: LMOptions):
             dcf = scipy.linalg.cho_solve(scipy.linalg.cho_factor(S, lower=True), b)
         except np.linalg.LinAlgError:
             return None       # S not numerically positive definite: no step
+    elif opts.solver == "pcg" and opts.refine_max > 0:
+        dcf, iters, _ = pcg_refined(S, b, opts.pcg_tol, opts.pcg_max_iters, opts.refine_max,
+                                    opts.refine_tol)
     elif opts.solver == "pcg":
         dcf, iters, _ = pcg_block_jacobi(S, b, opts.pcg_tol, opts.pcg_max_iters)
     else:
@@ -603,6 +636,7 @@ def lm_solve(prob: Problem, st0: State, opts: LMOptions) -> LMResult:
         accept = bool(dL > 0 and gain > 0)
         mu, nu = damping_update(mu, nu, gain, accept)
         if accept:
+            mu = max(mu, opts.mu_min)
             st, F = cand, F_new
             lin = None
         acc.append(accept)

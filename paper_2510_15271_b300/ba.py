@@ -65,7 +65,7 @@ class Report(Structure):
                 ("pcg_rel_residual", c_double * BA_MAX_ITERS),
                 ("gain", c_double * BA_MAX_ITERS), ("rmse_px", c_double),
                 ("n_valid_obs", c_int64), ("solve_ms", c_double), ("setup_ms", c_double),
-                ("n_kernels", c_int32), ("pad", c_int32)]
+                ("n_kernels", c_int32), ("pcg_variant", c_int32)]
 
     def as_dict(self):
         n = self.n_iters
@@ -76,7 +76,8 @@ class Report(Structure):
                     pcg_rel_residual=np.array(self.pcg_rel_residual[:n]),
                     gain=np.array(self.gain[:n]), rmse_px=self.rmse_px,
                     n_valid_obs=self.n_valid_obs, solve_ms=self.solve_ms,
-                    setup_ms=self.setup_ms, n_kernels=self.n_kernels)
+                    setup_ms=self.setup_ms, n_kernels=self.n_kernels,
+                    pcg_variant=self.pcg_variant)
 
 
 class KernelStat(Structure):
@@ -660,7 +661,7 @@ def options_for_scene(scene, precision: Optional[str] = None, **kw) -> Options:
     o.huber_delta = scene.huber_delta
     o.pcg_tol = scene.pcg_tol
     o.pcg_max_iters = scene.pcg_max_iters
-    o.refine = 1 if (scene.refine and prec == "fp32") else 0
+    o.refine = 1 if scene.refine else 0
     for k, v in kw.items():
         setattr(o, k, v)
     return o

@@ -159,8 +159,8 @@ static ba_status check_options(const ba_options* o, std::string& err) {
     err = "pcg_resident_cap must be >= 0";
     return BA_ERR_INVALID_ARG;
   }
-  if (o->pcg_variant < 0 || o->pcg_variant > 3) {
-    err = "pcg_variant must be 0 (auto), 1 (standard), 2 (pipelined) or 3 (cluster)";
+  if (o->pcg_variant < 0 || o->pcg_variant > 4) {
+    err = "pcg_variant must be 0 (auto), 1 (standard), 2 (pipelined), 3 (cluster) or 4 (streamed)";
     return BA_ERR_INVALID_ARG;
   }
   if (o->solver < BA_SOLVER_AUTO || o->solver > BA_SOLVER_PCG) {
@@ -617,7 +617,7 @@ ba_status ba_set_problem(ba_handle* h, int32_t n_cams, int32_t n_pts, int64_t n_
   cfg.mu0 = h->opts.mu0;
   cfg.pcg_tol = h->opts.pcg_tol;
   cfg.pcg_max = h->opts.pcg_max_iters;
-  cfg.refine = (h->opts.refine && prec == BA_FP32) ? 1 : 0;
+  cfg.refine = h->opts.refine ? 1 : 0;
   cfg.refine_max = h->opts.refine_max;
   cfg.refine_tol = h->opts.refine_tol;
   // auto (0) takes the pipelined recurrence (one grid barrier per iteration,
@@ -680,6 +680,30 @@ ba_status ba_set_problem(ba_handle* h, int32_t n_cams, int32_t n_pts, int64_t n_
     CK(cudaMemcpy(d.pcg_uptr, plan.uptr.data(), plan.uptr.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d.pcg_lcol, plan.lcol.data(), plan.lcol.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d.pcg_lown, plan.lown.data(), plan.lown.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    // S that does not stay resident in shared memory is streamed through it
+    // by bulk copies (auto), or always when asked for (variant 4)
+    const bool want_stream = h->opts.pcg_variant == 4 ||
+                             (h->opts.pcg_variant == 0 && cfg.pcg_smem == 0);
+    if (want_stream) {
+      PcsPlan ps;
+      if (plan_pcg_stream(prec, h->device, hrp, hcol, smax - 1024, cfg, ps)) {
+        auto up = [&](auto*& dst, const auto& v) {
+          using E = typename std::decay<decltype(v)>::type::value_type;
+          if (!keep(h, dst, std::max<size_t>(v.size(), 1) * sizeof(E))) return false;
+          return v.empty() || cudaMemcpy(dst, v.data(), v.size() * sizeof(E),
+                                         cudaMemcpyHostToDevice) == cudaSuccess;
+        };
+        if (!(up(d.pcs_rows, ps.rows) && up(d.pcs_uptr, ps.uptr) && up(d.pcs_ucol, ps.ucol) &&
+              up(d.pcs_ioff, ps.ioff) && up(d.pcs_wrow, ps.wrow) && up(d.pcs_idx, ps.idx))) {
+          h->err = "ba_set_problem: out of device memory (streamed PCG plan)";
+          free_problem(h);
+          return BA_ERR_OOM;
+        }
+        cfg.pcg_pipelined = 0;
+      } else {
+        cfg.pcs_smem = 0;
+      }
+    }
     // one thread-block cluster instead of the grid kernel, when asked for
     // (measured no faster than the grid kernel on this part: about 13 us per
     // iteration either way, so auto keeps the grid kernel)
@@ -811,6 +835,12 @@ ba_status ba_solve(ba_handle* h, ba_report* out) {
     out->solve_ms = ms;
     out->setup_ms = h->setup_ms;
     out->n_kernels = h->marks.launches;
+    const SolveConfig& c = h->cfg;
+    out->pcg_variant = c.solver != BA_SOLVER_PCG ? 0
+                       : c.pcs_smem > 0         ? 4
+                       : c.pcc_cs > 0           ? 3
+                       : c.pcg_pipelined        ? 2
+                                                : 1;
   }
   h->solved = true;
   h->last_solve_ms = ms;

@@ -125,6 +125,13 @@ struct DevProblem {
   int32_t* pcg_uptr = nullptr;  // [G + 1]
   int32_t* pcg_lcol = nullptr;  // [nnzb] list index of each block's column
   int32_t* pcg_lown = nullptr;  // [C] list index of each row's own column
+  // streamed PCG plan (PcsPlan)
+  int32_t* pcs_rows = nullptr;
+  int32_t* pcs_uptr = nullptr;
+  int32_t* pcs_ucol = nullptr;
+  int32_t* pcs_ioff = nullptr;
+  int32_t* pcs_wrow = nullptr;
+  uint32_t* pcs_idx = nullptr;
   // cluster PCG plan
   int32_t* pcc_rows = nullptr;  // [cs + 1] first block row of each CTA
   int32_t* pcc_nres = nullptr;  // [cs] blocks of S each CTA keeps in shared memory

@@ -53,6 +53,10 @@ struct SolveConfig {
   size_t pcc_smem = 0;     // cluster PCG: dynamic shared memory per CTA
   int pcc_rmax = 0, pcc_umax = 0, pcc_nnzmax = 0;  // cluster PCG: layout sizes
   size_t dense_smem = 0;   // dynamic shared memory of the dense solver (0: global workspace)
+  size_t pcs_smem = 0;     // streamed PCG (pcg_stream.cu): dynamic shared memory (0: not used)
+  int pcs_blocks = 0;      // streamed PCG: CTAs (one per SM)
+  int pcs_nd = 1;          // streamed PCG: own elements per consumer thread (kernel variant)
+  int pcs_maxu = 0, pcs_rmax = 0;  // streamed PCG: most listed columns / rows of one CTA
   Marks* marks = nullptr;
 };
 
@@ -108,6 +112,22 @@ struct PccPlan {
 bool plan_pcg_cluster(int precision, int device, const std::vector<int32_t>& rowptr,
                       const std::vector<int32_t>& col, SolveConfig& cfg, PccPlan& plan);
 void launch_pcg_cluster(const DevProblem& d, const SolveConfig& cfg, cudaStream_t s);
+
+// Plan of the streamed PCG kernel (pcg_stream.cu): rows with balanced block
+// counts per CTA, each CTA's referenced columns, and the packed (local row,
+// local column) index of every block, listed per consumer-warp range.
+struct PcsPlan {
+  std::vector<int32_t> rows;   // [G + 1] first block row of each CTA
+  std::vector<int32_t> uptr;   // [G + 1] first listed column of each CTA
+  std::vector<int32_t> ucol;   // concatenated sorted column lists
+  std::vector<int32_t> ioff;   // [G][8] offset of each warp range's indices
+  std::vector<int32_t> wrow;   // [G][8][2] first, last local row of each range (-1: empty)
+  std::vector<uint32_t> idx;   // packed indices, each range starting at a multiple of 4
+};
+bool plan_pcg_stream(int precision, int device, const std::vector<int32_t>& rowptr,
+                     const std::vector<int32_t>& col, size_t smem_limit, SolveConfig& cfg,
+                     PcsPlan& plan);
+void launch_pcg_stream(const DevProblem& d, const SolveConfig& cfg, cudaStream_t s);
 
 bool plan_pcg(int precision, int device, const std::vector<int32_t>& rowptr,
               const std::vector<int32_t>& col, size_t smem_limit, SolveConfig& cfg,

@@ -1156,6 +1156,10 @@ static void linear_solve_t(const DevProblem& d, const SolveConfig& cfg, cudaStre
     launch_pcg_cluster(d, cfg, s);
     return;
   }
+  if (cfg.pcs_smem > 0) {
+    launch_pcg_stream(d, cfg, s);
+    return;
+  }
   cudaMemsetAsync(d.barrier, 0, sizeof(unsigned), s);  // arrival counter only
   DevProblem dd = d;
   double tol = cfg.pcg_tol;

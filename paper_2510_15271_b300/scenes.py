@@ -34,6 +34,7 @@ Workloads (sizes are the defaults; every builder accepts smaller ones):
 from __future__ import annotations
 
 import dataclasses
+import itertools
 import math
 from typing import List, Optional
 
@@ -452,12 +453,16 @@ def _city_scene(name, seed, n_cams=5000, n_pts=1_000_000, *, extent=3000.0, bloc
         rows_sel = []
         for chunk in range(0, m, 65536):
             idx = np.arange(chunk, min(m, chunk + 65536))
-            maxc = max((len(nb[i]) for i in idx), default=0)
+            lens = np.fromiter((len(nb[i]) for i in idx), dtype=np.int64, count=idx.size)
+            maxc = int(lens.max()) if lens.size else 0
             if maxc == 0:
                 continue
+            # row r holds the neighbours of point idx[r] in the order the tree
+            # returned them, padded with -1
             cand = np.full((idx.size, maxc), -1, dtype=np.int64)
-            for r_, i in enumerate(idx):
-                cand[r_, :len(nb[i])] = nb[i]
+            cand[np.arange(maxc)[None, :] < lens[:, None]] = np.fromiter(
+                itertools.chain.from_iterable(nb[i] for i in idx), dtype=np.int64,
+                count=int(lens.sum()))
             valid = cand >= 0
             cc = np.where(valid, cand, 0)
             uv, w = _image(Pm[cc], Xi[idx][:, None, :])

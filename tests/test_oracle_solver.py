@@ -211,6 +211,49 @@ def test_pcg_counts_products_and_respects_the_cap():
     assert k == 7 and rel > 1e-14
 
 
+def test_refinement_with_one_step_is_plain_pcg():
+    rng = np.random.Generator(np.random.PCG64(11))
+    M = rng.normal(size=(90, 90))
+    S = M @ M.T + 1e-2 * np.eye(90)
+    b = rng.normal(size=90)
+    x1, k1, r1 = O.pcg_block_jacobi(S, b, 1e-3, 40)
+    x2, k2, r2 = O.pcg_refined(S, b, 1e-3, 40, 1, 1e-12)
+    np.testing.assert_array_equal(x1, x2)
+    assert k1 == k2 and r2 == pytest.approx(r1, rel=1e-12)
+
+
+def test_refinement_reaches_its_tolerance_and_the_direct_solution():
+    """Loose inner solves (tol 1e-2) refined until the residual, recomputed
+    here by numpy, is below 1e-10 relative; the solution is then within
+    kappa(S) times that of the Cholesky solution."""
+    rng = np.random.Generator(np.random.PCG64(12))
+    M = rng.normal(size=(120, 120))
+    S = M @ M.T + 0.5 * np.eye(120)
+    b = rng.normal(size=120)
+    x, k, rel = O.pcg_refined(S, b, 1e-2, 500, 20, 1e-10)
+    true_rel = np.linalg.norm(b - S @ x) / np.linalg.norm(b)
+    assert true_rel <= 1e-10 and rel == pytest.approx(true_rel, rel=1e-9)
+    x_ref = scipy.linalg.cho_solve(scipy.linalg.cho_factor(S), b)
+    assert np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref) <= np.linalg.cond(S) * true_rel
+    # each outer step cut the residual: more than one step was needed
+    _, _, rel1 = O.pcg_refined(S, b, 1e-2, 500, 1, 1e-10)
+    assert rel1 > 1e-4 and k > 0
+
+
+def test_refined_lm_step_on_a_tiny_scene_is_the_direct_step():
+    """In the LM loop, a refined PCG step with a tight outer tolerance is the
+    dense Cholesky step (same costs to 1e-10)."""
+    s = scenes.make_scene("city", seed=13, n_cams=12, n_pts=500)
+    prob = _problem(s)
+    st = O.state_from_qt(s.cam_qt, s.pts)
+    ref = O.lm_solve(prob, st, O.LMOptions(huber_delta=1.5, lm_iters=4, solver="dense"))
+    res = O.lm_solve(prob, st, O.LMOptions(huber_delta=1.5, lm_iters=4, solver="pcg",
+                                           pcg_tol=1e-3, pcg_max_iters=30, refine_max=30,
+                                           refine_tol=1e-13))
+    np.testing.assert_allclose(res.costs, ref.costs, rtol=1e-10)
+    assert np.all(res.pcg_iters > 30)
+
+
 # --------------------------------------------------------------------------- LM
 
 @pytest.mark.parametrize("name,kw,opts", [
@@ -477,6 +520,27 @@ def test_lm_loop_applies_the_pinned_damping_update():
     for k in range(len(res.mu) - 1):
         mu_next, nu = O.damping_update(res.mu[k], nu, res.gain[k], bool(res.accepted[k]))
         assert res.mu[k + 1] == mu_next, k
+
+
+def test_damping_floor_holds_mu_and_is_inert_when_zero():
+    """mu_min floors the damping after accepted steps only; with 0 (the
+    default) the run is the plain schedule bit for bit."""
+    s = scenes.make_scene("ring", seed=17, n_cams=8, n_pts=300)
+    prob = _problem(s)
+    st = O.state_from_qt(s.cam_qt, s.pts)
+    plain = O.lm_solve(prob, st, O.LMOptions(lm_iters=12, solver="dense"))
+    zero = O.lm_solve(prob, st, O.LMOptions(lm_iters=12, solver="dense", mu_min=0.0))
+    np.testing.assert_array_equal(plain.costs, zero.costs)
+    assert plain.mu.min() < 1e-4
+    floored = O.lm_solve(prob, st, O.LMOptions(lm_iters=12, solver="dense", mu_min=1e-4))
+    assert floored.mu.min() == pytest.approx(1e-4, rel=1e-15)
+    nu = 2.0
+    for k in range(len(floored.mu) - 1):
+        mu_next, nu = O.damping_update(floored.mu[k], nu, floored.gain[k],
+                                       bool(floored.accepted[k]))
+        if floored.accepted[k]:
+            mu_next = max(mu_next, 1e-4)
+        assert floored.mu[k + 1] == mu_next, k
 
 
 def test_planted_slips_in_gain_ratio_and_damping_are_caught(monkeypatch):
