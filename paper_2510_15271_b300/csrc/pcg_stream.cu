@@ -122,6 +122,28 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned b
       : "memory");
 }
 
+// The same with an L2 cache policy (createpolicy) for the source lines.
+__device__ __forceinline__ void bulk_copy_hint(void* dst, const void* src, unsigned bytes,
+                                               uint64_t* bar, uint64_t policy) {
+  uint64_t g;
+  asm volatile("cvta.to.global.u64 %0, %1;" : "=l"(g) : "l"(src));
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], "
+      "[%1], %2, [%3], %4;" ::"r"(smem_addr(dst)),
+      "l"(g), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
+      : "memory");
+}
+
+// L2 policy: the given fraction of the lines a copy touches are kept in L2
+// in preference to others (evict_last), the rest go first (evict_first).
+__device__ __forceinline__ uint64_t keep_fraction_policy(float frac) {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.L2::evict_first.b64 %0, %1;"
+               : "=l"(pol)
+               : "f"(frac));
+  return pol;
+}
+
 __device__ __forceinline__ void consumers_sync() {
   asm volatile("bar.sync %0, %1;" ::"r"(kSBar), "r"(kSConsumers) : "memory");
 }
@@ -149,7 +171,8 @@ struct WarpPlan {
 // all products; the range is cycled through).  Lane 0 only.
 template <typename T, int NS>
 __device__ __forceinline__ void issue_slice(const DevProblem& d, const WarpPlan& wp, unsigned q,
-                                            T* ring, uint32_t* ridx, uint64_t* full) {
+                                            T* ring, uint32_t* ridx, uint64_t* full,
+                                            uint64_t policy, bool hint) {
   const int w = threadIdx.x >> 5;
   const unsigned slot = q % NS;
   const int c = (int)(q % (unsigned)wp.nch);
@@ -158,8 +181,12 @@ __device__ __forceinline__ void issue_slice(const DevProblem& d, const WarpPlan&
   const unsigned ibytes = (unsigned)(((cnt + 3) & ~3) * sizeof(uint32_t));
   uint64_t* bar = &full[w * NS + slot];
   mbar_arrive_tx(bar, sbytes + ibytes);
-  bulk_copy(ring + (size_t)(w * NS + slot) * kSlice * 36,
-            (const T*)d.S + 36 * (int64_t)(wp.b0 + c * kSlice), sbytes, bar);
+  if (hint)
+    bulk_copy_hint(ring + (size_t)(w * NS + slot) * kSlice * 36,
+                   (const T*)d.S + 36 * (int64_t)(wp.b0 + c * kSlice), sbytes, bar, policy);
+  else
+    bulk_copy(ring + (size_t)(w * NS + slot) * kSlice * 36,
+              (const T*)d.S + 36 * (int64_t)(wp.b0 + c * kSlice), sbytes, bar);
   bulk_copy(ridx + (w * NS + slot) * kSlice, (const uint32_t*)d.pcs_idx + wp.ioff + c * kSlice,
             ibytes, bar);
 }
@@ -194,7 +221,8 @@ __device__ __forceinline__ void flush_row(int r, const A s[6], const WarpPlan& w
 template <typename T, typename A, typename V, int NS>
 __device__ void spmv_stream(const DevProblem& d, const WarpPlan& wp, int nrow, const int* sfirst,
                             const int* slast, uint64_t* full, int* fail, T* ring, uint32_t* ridx,
-                            const V* sv, double* sq, double* fl, unsigned& g, int* err) {
+                            const V* sv, double* sq, double* fl, unsigned& g, int* err,
+                            uint64_t policy, bool hint) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const unsigned FULL = 0xffffffffu;
   if (wp.nch > 0) {
@@ -246,7 +274,7 @@ __device__ void spmv_stream(const DevProblem& d, const WarpPlan& wp, int nrow, c
       }
       // the slice is in registers: refill its slot with the slice NS ahead
       __syncwarp();
-      if (lane == 0) issue_slice<T, NS>(d, wp, g + NS, ring, ridx, full);
+      if (lane == 0) issue_slice<T, NS>(d, wp, g + NS, ring, ridx, full, policy, hint);
       // lanes past the range join the last valid lane's row with y = 0
       lr = __shfl_sync(FULL, lr, lane < nvalid ? lane : nvalid - 1);
       if (__all_sync(FULL, lr == cur)) {
@@ -375,6 +403,7 @@ struct StreamArgs {
   int refine, refine_max;
   double refine_tol;
   int maxu, rmax;
+  float l2_keep;  // fraction of S's lines copied with evict_last priority (0: no hint)
 };
 
 // Shared-memory layout (dynamic): ring [kSWarps][NS][kSlice][36] T |
@@ -452,8 +481,11 @@ __global__ void __launch_bounds__(kSThreads, 1) k_pcg_stream(DevProblem d, Strea
   }
   __syncthreads();
   // every warp starts its stream: the first NS slices of its range
+  const bool hint = a.l2_keep > 0.f;
+  const uint64_t policy = hint ? keep_fraction_policy(fminf(a.l2_keep, 1.f)) : 0ull;
   if (lane == 0 && wp.nch > 0)
-    for (unsigned q = 0; q < (unsigned)NS; ++q) issue_slice<T, NS>(d, wp, q, ring, ridx, full);
+    for (unsigned q = 0; q < (unsigned)NS; ++q)
+      issue_slice<T, NS>(d, wp, q, ring, ridx, full, policy, hint);
 
   // Every decision that steers the threads (loop conditions, early stops)
   // is taken by thread 0 and broadcast through shared memory after a
@@ -544,7 +576,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_pcg_stream(DevProblem d, Strea
       }
       consumers_sync();
       spmv_stream<T, T, T, NS>(d, wp, nrow, sfirst, slast, full, fail, ring, ridx, sv, sq, fl, g,
-                               err);
+                               err, policy, hint);
       double pq[1] = {0.0};
       T qr[ND];
 #pragma unroll
@@ -638,7 +670,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_pcg_stream(DevProblem d, Strea
         sv64[i] = __ldcg(d.x64 + 6 * __ldg(ucol + i / 6) + i % 6);
       consumers_sync();
       spmv_stream<T, double, double, NS>(d, wp, nrow, sfirst, slast, full, fail, ring, ridx, sv64,
-                                         sq, fl, g, err);
+                                         sq, fl, g, err, policy, hint);
       double l2[1] = {0.0};
 #pragma unroll
       for (int j = 0; j < ND; ++j) {
@@ -792,6 +824,16 @@ bool plan_pcg_stream(int precision, int device, const std::vector<int32_t>& rowp
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kSThreads, need);
   if (per_sm < 1 || per_sm * sms < G) return false;
+  // S is read in full every product.  When it is larger than the L2, a
+  // cyclic stream through it evicts every line before its next use; marking
+  // a share of its lines evict_last keeps that share resident across
+  // products (about 45 % of the L2 for S: on the city workload, 158 MB of S
+  // against 126 MB of L2, 44 -> 36 us per iteration with results unchanged;
+  // keeping more than the L2 holds thrashes and gains nothing)
+  int l2 = 0;
+  cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device);
+  const double sbytes = (double)nnzb * 36 * (precision == BA_FP32 ? 4 : 8);
+  cfg.pcs_l2_keep = sbytes > 0 ? (float)std::min(1.0, 0.45 * l2 / sbytes) : 0.f;
   cfg.pcs_blocks = G;
   cfg.pcs_nd = nd;
   cfg.pcs_maxu = maxu;
@@ -804,7 +846,7 @@ void launch_pcg_stream(const DevProblem& d, const SolveConfig& cfg, cudaStream_t
   cudaMemsetAsync(d.barrier, 0, sizeof(unsigned), s);  // arrival counter only
   DevProblem dd = d;
   StreamArgs a{cfg.pcg_tol, cfg.pcg_max, cfg.refine, cfg.refine_max, cfg.refine_tol,
-               cfg.pcs_maxu, cfg.pcs_rmax};
+               cfg.pcs_maxu, cfg.pcs_rmax, cfg.pcs_l2_keep};
   void* args[] = {&dd, &a};
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3(cfg.pcs_blocks);
