@@ -506,41 +506,81 @@ ba_status ba_set_problem(ba_handle* h, int32_t n_cams, int32_t n_pts, int64_t n_
     std::vector<int32_t> hsb(nseg + 1), hcs(nchunks + 1);
     CK(cudaMemcpy(hsb.data(), d.seg_begin, (nseg + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(hcs.data(), d.chunk_seg, (nchunks + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
-    const size_t smax_sub = max_dyn_smem(h->device) - 4096;
-    const int colcap_guess = std::min<int>(*std::max_element(hrow.begin(), hrow.end()), 64);
-    int sub_len = 8, max_subs = 0;
-    for (;; sub_len *= 2) {
-      max_subs = 0;
+    // blocks on and right of the diagonal per row: the Schur kernel's accumulators
+    {
+      std::vector<int32_t> hdiag(C), hrp(C + 1);
+      CK(cudaMemcpy(hdiag.data(), d.s_diag, C * sizeof(int32_t), cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(hrp.data(), d.s_rowptr, (C + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+      d.max_row_upper = 1;
+      for (int i = 0; i < C; ++i) d.max_row_upper = std::max(d.max_row_upper, hrp[i + 1] - hdiag[i]);
+    }
+    // The Schur kernel stages only the sub-segments of split segments; the
+    // shortest sub_len (best balance) whose staging, with the accumulators of
+    // the longest row (or at least 64 of them), leaves room for two CTAs per
+    // SM.
+    int smem_sm = 0;
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device);
+    const size_t two_per_sm = std::min<size_t>(max_dyn_smem(h->device) - 2048,
+                                               (size_t)smem_sm / 2 - 4096);
+    int sub_len = 8, max_rs = 0;
+    auto staged = [&](int len) {
+      int most = 0;
       for (int ch = 0; ch < nchunks; ++ch) {
         int n = 0;
-        for (int sg = hcs[ch]; sg < hcs[ch + 1]; ++sg)
-          n += (hsb[sg + 1] - hsb[sg] + sub_len - 1) / sub_len;
-        max_subs = std::max(max_subs, n);
+        for (int sg = hcs[ch]; sg < hcs[ch + 1]; ++sg) {
+          const int ns = (hsb[sg + 1] - hsb[sg] + len - 1) / len;
+          if (ns > 1) n += ns;
+        }
+        most = std::max(most, n);
       }
-      if (schur_smem(prec, colcap_guess, max_subs) <= smax_sub || sub_len >= 4096) break;
+      return most;
+    };
+    for (;; sub_len *= 2) {
+      max_rs = staged(sub_len);
+      if (schur_smem(prec, std::min(d.max_row_upper, 64), max_rs) <= two_per_sm || sub_len >= 4096)
+        break;
     }
     // the table itself is built on the device: counts, scan, fill
     int64_t nsub64 = 0;
     for (int sg = 0; sg < nseg; ++sg) nsub64 += (hsb[sg + 1] - hsb[sg] + sub_len - 1) / sub_len;
     const int nsub = (int)nsub64;
+    // staging index of every sub-segment (sub-segments are numbered in
+    // segment order, as the device fill numbers them)
+    std::vector<int32_t> hrs;
+    hrs.reserve(std::max(nsub, 1));
+    for (int ch = 0; ch < nchunks; ++ch) {
+      int r = 0;
+      for (int sg = hcs[ch]; sg < hcs[ch + 1]; ++sg) {
+        const int ns = (hsb[sg + 1] - hsb[sg] + sub_len - 1) / sub_len;
+        for (int q = 0; q < ns; ++q) hrs.push_back(ns > 1 ? r++ : -1);
+      }
+    }
+    if ((int)hrs.size() != nsub) {
+      h->err = "ba_set_problem: inconsistent Schur segment table";
+      free_problem(h);
+      return BA_ERR_CUDA;
+    }
     int32_t* scnt = (int32_t*)tmp.get((size_t)(nseg + 1) * sizeof(int32_t));
     ok = scnt && keep(h, d.sub_begin, (nsub + 1) * sizeof(int32_t)) &&
          keep(h, d.sub_slot, std::max(nsub, 1) * sizeof(int32_t)) &&
-         keep(h, d.seg_sub, (nseg + 1) * sizeof(int32_t));
+         keep(h, d.seg_sub, (nseg + 1) * sizeof(int32_t)) &&
+         keep(h, d.sub_rs, std::max(nsub, 1) * sizeof(int32_t));
     if (!ok) {
       h->err = "ba_set_problem: out of device memory (sub-segments)";
       free_problem(h);
       return BA_ERR_OOM;
     }
+    if (nsub) CK(cudaMemcpy(d.sub_rs, hrs.data(), nsub * sizeof(int32_t), cudaMemcpyHostToDevice));
     launch_sub_counts(nseg, d.seg_begin, sub_len, scnt, s);
     launch_scan_i32(scnt, d.seg_sub, nseg, stmp2, d.seg_sub + nseg, s);
     launch_sub_fill(nseg, d.seg_begin, d.seg_slot, d.seg_sub, sub_len, d.sub_begin, d.sub_slot, s);
     const int32_t npi = (int32_t)np;
     CK(cudaMemcpyAsync(d.sub_begin + nsub, &npi, sizeof(int32_t), cudaMemcpyHostToDevice, s));
     CK(cudaGetLastError());
+    d.schur_smem_cap = two_per_sm;
     d.nsub = nsub;
     d.sub_len = sub_len;
-    d.max_chunk_subs = max_subs;
+    d.max_chunk_rs = max_rs;
   }
 
   // ---- solver buffers and state
@@ -727,8 +767,10 @@ ba_status ba_set_problem(ba_handle* h, int32_t n_cams, int32_t n_pts, int64_t n_
       cfg.pcc_cs = 0;
     }
   }
-  cfg.schur_colcap = schur_colcap(prec, d.max_row_nnz, d.max_chunk_subs, smax - 2048);
-  set_schur_smem_attr(prec, schur_smem(prec, cfg.schur_colcap, d.max_chunk_subs));
+  // the accumulators of the longest row in one pass where two CTAs per SM
+  // still fit, else in passes
+  cfg.schur_colcap = schur_colcap(prec, d.max_row_upper, d.max_chunk_rs, d.schur_smem_cap);
+  set_schur_smem_attr(prec, schur_smem(prec, cfg.schur_colcap, d.max_chunk_rs));
   CK(cudaEventRecord(h->ev1, s));
   CK(cudaEventSynchronize(h->ev1));
   float ms = 0.f;

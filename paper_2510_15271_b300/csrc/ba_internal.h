@@ -119,7 +119,13 @@ struct DevProblem {
   int32_t* sub_begin = nullptr;  // [nsub + 1] first pair of each sub-segment
   int32_t* sub_slot = nullptr;   // [nsub] output block slot
   int32_t* seg_sub = nullptr;    // [nseg + 1] first sub-segment of each segment
-  int nsub = 0, sub_len = 16, max_chunk_subs = 0;
+  // [nsub] staging index (within its chunk) of a sub-segment whose segment
+  // is split into several, -1 for a segment's only sub-segment
+  int32_t* sub_rs = nullptr;
+  int nsub = 0, sub_len = 16;
+  int max_chunk_rs = 0;   // most staged sub-segments of one chunk
+  int max_row_upper = 0;  // most blocks on and right of the diagonal in one row
+  size_t schur_smem_cap = 0;  // shared memory per Schur CTA that leaves room for two per SM
   // PCG shared-memory variant: per-CTA lists of referenced columns
   int32_t* pcg_ucol = nullptr;  // concatenated lists
   int32_t* pcg_uptr = nullptr;  // [G + 1]

@@ -74,8 +74,8 @@ void launch_prior_coupling(const DevProblem& d, cudaStream_t s);
 void launch_prior_cost(const DevProblem& d, int trial, cudaStream_t s);
 int backsub_blocks(const DevProblem& d);
 int retract_blocks(const DevProblem& d);
-size_t schur_smem(int precision, int colcap, int max_subs);
-int schur_colcap(int precision, int max_row_nnz, int max_subs, size_t smem_limit);
+size_t schur_smem(int precision, int colcap, int max_rs);
+int schur_colcap(int precision, int max_row_upper, int max_rs, size_t smem_limit);
 void set_schur_smem_attr(int precision, size_t bytes);
 
 void launch_lm_begin(const DevProblem& d, const SolveConfig& cfg, cudaStream_t s);

@@ -317,19 +317,25 @@ __global__ void k_damp_pt(DevProblem d) {
 constexpr int kResStride = 37;
 
 // Shared-memory layout of k_schur: acc [colcap][36] T | Y [kSchurChunk][18] T |
-// sub-segment results [max_subs][kResStride] T.
+// staged sub-segment results [max_rs][kResStride] T.
 template <typename T>
-__host__ __device__ inline size_t schur_smem_bytes(int colcap, int max_subs) {
+__host__ __device__ inline size_t schur_smem_bytes(int colcap, int max_rs) {
   return (size_t)colcap * 36 * sizeof(T) + (size_t)kSchurChunk * 18 * sizeof(T) +
-         (size_t)max_subs * kResStride * sizeof(T) + 64;
+         (size_t)max_rs * kResStride * sizeof(T) + 64;
 }
 
-// One CTA per camera row i1.  For each chunk of the row's observations:
-// threads compute Y_k1 = W_k1 V*_j^-1 into shared memory; each thread then
-// takes whole sub-segments of the pair list (at most sub_len consecutive
-// pairs of the chunk that land in one output block S_i1,i2) and accumulates
-// sum Y_k1 W_k2^T over them in registers; finally the sub-segment results of
-// each block are added in order.  No atomics; the summation order is fixed
+// One CTA per camera row i1.  Only the blocks on and right of the diagonal
+// are summed here (each off-diagonal one is also written transposed), so the
+// accumulators cover the row's upper slots [ub, nnz), in passes of colcap
+// blocks when they do not all fit.  For each chunk of the row's
+// observations: threads compute Y_k1 = W_k1 V*_j^-1 into shared memory; each
+// thread pair then takes whole sub-segments of the pair list (at most
+// sub_len consecutive pairs of the chunk that land in one output block
+// S_i1,i2) and accumulates sum Y_k1 W_k2^T over them in registers.  A
+// sub-segment that is its segment's only one adds its sum into the block's
+// accumulator at once (no other thread touches that block in this chunk);
+// the sub-segments of a split segment are staged in shared memory and added
+// in order afterwards.  No atomics; the summation order is fixed
 // (bit-reproducible).
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT, 2) k_schur(DevProblem d, int colcap) {
@@ -339,6 +345,8 @@ __global__ void __launch_bounds__(NT, 2) k_schur(DevProblem d, int colcap) {
   const int i = blockIdx.x;
   const int rb = d.s_rowptr[i];
   const int nnz = d.s_rowptr[i + 1] - rb;
+  const int ub = d.s_diag[i] - rb;  // first slot on or right of the diagonal
+  const int nup = nnz - ub;
   T* acc = reinterpret_cast<T*>(smem);
   T* Ys = acc + (size_t)colcap * 36;
   T* Rs = Ys + (size_t)kSchurChunk * 18;
@@ -352,8 +360,9 @@ __global__ void __launch_bounds__(NT, 2) k_schur(DevProblem d, int colcap) {
   double bacc[6] = {0, 0, 0, 0, 0, 0};
   T* Sg = (T*)d.S;
 
-  for (int cb = 0; cb < nnz; cb += colcap) {
-    const int ncol = min(colcap, nnz - cb);
+  for (int cb = 0; cb < nup; cb += colcap) {
+    const int ncol = min(colcap, nup - cb);
+    const int lo = ub + cb, hi = lo + ncol;  // slots of this pass
     for (int e = threadIdx.x; e < ncol * 36; e += NT) acc[e] = T(0);
     __syncthreads();
     if (!fixed_i) {
@@ -392,7 +401,7 @@ __global__ void __launch_bounds__(NT, 2) k_schur(DevProblem d, int colcap) {
         const int h = threadIdx.x & 1;
         for (int u = u0 + (int)(threadIdx.x >> 1); u < u1; u += NT / 2) {
           const int slot = d.sub_slot[u];
-          if (slot < cb || slot >= cb + ncol) continue;
+          if (slot < lo || slot >= hi) continue;
           const int pb = d.sub_begin[u], pe = d.sub_begin[u + 1];
           T sum[18];
 #pragma unroll
@@ -427,30 +436,39 @@ __global__ void __launch_bounds__(NT, 2) k_schur(DevProblem d, int colcap) {
               }
             }
           }
-          T* res = Rs + (size_t)(u - u0) * kResStride + 18 * h;
+          const int rs = d.sub_rs[u];
+          if (rs < 0) {
+            // the segment's only sub-segment: straight into its block
+            T* A = acc + 36 * (slot - lo) + 18 * h;
 #pragma unroll
-          for (int e = 0; e < 18; ++e) res[e] = sum[e];
+            for (int e = 0; e < 18; ++e) A[e] += sum[e];
+          } else {
+            T* res = Rs + (size_t)rs * kResStride + 18 * h;
+#pragma unroll
+            for (int e = 0; e < 18; ++e) res[e] = sum[e];
+          }
         }
         __syncthreads();
-        // combine the sub-segments of each segment in order
+        // the split segments: their sub-segments added in order
         for (int it = threadIdx.x; it < (sg1 - sg0) * 36; it += NT) {
           const int sg = sg0 + it / 36, e = it % 36;
+          const int v0 = d.seg_sub[sg], v1 = d.seg_sub[sg + 1];
+          if (v1 - v0 < 2) continue;
           const int slot = d.seg_slot[sg];
-          if (slot < cb || slot >= cb + ncol) continue;
+          if (slot < lo || slot >= hi) continue;
           T s = T(0);
-          for (int u = d.seg_sub[sg]; u < d.seg_sub[sg + 1]; ++u) s += Rs[(size_t)(u - u0) * kResStride + e];
-          acc[36 * (slot - cb) + e] += s;
+          for (int u = v0; u < v1; ++u) s += Rs[(size_t)d.sub_rs[u] * kResStride + e];
+          acc[36 * (slot - lo) + e] += s;
         }
         __syncthreads();
       }
     }
-    // write this column chunk of the row
+    // write this pass's blocks of the row (all on or right of the diagonal)
     const T* U = (const T*)d.U + 36 * (int64_t)i;
     for (int e = threadIdx.x; e < ncol * 36; e += NT) {
       const int s = e / 36, el = e % 36;
       const int a = el / 6, bb = el % 6;
-      const int col = d.s_col[rb + cb + s];
-      if (col < i) continue;  // written, transposed, by row col
+      const int col = d.s_col[rb + lo + s];
       T val;
       if (fixed_i) {
         val = (col == i && a == bb) ? T(1) : T(0);
@@ -462,8 +480,8 @@ __global__ void __launch_bounds__(NT, 2) k_schur(DevProblem d, int colcap) {
           val += u;
         }
       }
-      Sg[36 * (int64_t)(rb + cb + s) + el] = val;
-      if (col > i) Sg[36 * (int64_t)d.s_mirror[rb + cb + s] + 6 * bb + a] = val;
+      Sg[36 * (int64_t)(rb + lo + s) + el] = val;
+      if (col > i) Sg[36 * (int64_t)d.s_mirror[rb + lo + s] + 6 * bb + a] = val;
     }
     __syncthreads();
   }
@@ -763,14 +781,14 @@ int cost_blocks(const DevProblem& d) { return (int)grid_cap(d.N, 256, kCostParts
 int backsub_blocks(const DevProblem& d) { return (int)grid_cap(d.P, 256, kDlParts / 2); }
 int retract_blocks(const DevProblem& d) { return (int)grid_cap(d.C, 128, kDlParts / 2); }
 
-size_t schur_smem(int precision, int colcap, int max_subs) {
-  return precision == BA_FP32 ? schur_smem_bytes<float>(colcap, max_subs)
-                              : schur_smem_bytes<double>(colcap, max_subs);
+size_t schur_smem(int precision, int colcap, int max_rs) {
+  return precision == BA_FP32 ? schur_smem_bytes<float>(colcap, max_rs)
+                              : schur_smem_bytes<double>(colcap, max_rs);
 }
 
-int schur_colcap(int precision, int max_row_nnz, int max_subs, size_t smem_limit) {
-  int cap = max_row_nnz < 1 ? 1 : max_row_nnz;
-  while (cap > 1 && schur_smem(precision, cap, max_subs) > smem_limit) cap = (cap + 1) / 2;
+int schur_colcap(int precision, int max_row_upper, int max_rs, size_t smem_limit) {
+  int cap = max_row_upper < 1 ? 1 : max_row_upper;
+  while (cap > 1 && schur_smem(precision, cap, max_rs) > smem_limit) cap = (cap + 1) / 2;
   return cap;
 }
 
@@ -805,7 +823,7 @@ static void lm_iteration_t(const DevProblem& d, const SolveConfig& cfg, cudaStre
   mark(cfg, kKLinPt, s);
   k_damp_pt<T><<<gp, 256, 0, s>>>(d);
   mark(cfg, kKDampPt, s);
-  const size_t sm = schur_smem_bytes<T>(cfg.schur_colcap, d.max_chunk_subs);
+  const size_t sm = schur_smem_bytes<T>(cfg.schur_colcap, d.max_chunk_rs);
   k_schur<T, 256><<<d.C, 256, sm, s>>>(d, cfg.schur_colcap);
   launch_prior_coupling(d, s);  // adjacent cameras' prior blocks into S
   mark(cfg, kKSchur, s);
@@ -867,7 +885,7 @@ static void steps_t(const DevProblem& d, const SolveConfig& cfg, int step, int a
       k_damp_pt<T><<<gp, 256, 0, s>>>(d);
       break;
     case 2:
-      k_schur<T, 256><<<d.C, 256, schur_smem_bytes<T>(cfg.schur_colcap, d.max_chunk_subs), s>>>(
+      k_schur<T, 256><<<d.C, 256, schur_smem_bytes<T>(cfg.schur_colcap, d.max_chunk_rs), s>>>(
           d, cfg.schur_colcap);
       break;
     case 3:

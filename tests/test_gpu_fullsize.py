@@ -48,12 +48,22 @@ def test_initial_cost_matches_oracle(scene, golden):
         assert rep["costs"][0] == pytest.approx(golden["costs"][0], rel=rtol), prec
 
 
+# Two PCG solves that both stop at a relative residual of 1e-6 (rounded
+# differently) take steps that differ by up to kappa(S) times that (reading
+# C9); the step's cost agrees to about the tolerance on the driving system and
+# to a few times it on the far worse conditioned city system (measured 1.8e-6
+# between two valid summation orders of S), hence 1e-5 there.
+FIRST_STEP_RTOL = {"driving": 1e-6, "city": 1e-5}
+
+
 def test_fp64_first_step_matches_oracle(scene, golden):
     """Same PCG settings on both sides: the first step's cost agrees to about
     the solve tolerance."""
     rep, _, _ = ba.solve_scene(scene, "fp64", max_lm_iters=2, use_torch=True)
-    np.testing.assert_allclose(rep["costs"][:2], golden["costs"][:2], rtol=1e-6)
-    assert rep["pcg_iters"][0] == golden["pcg_iters"][0]
+    np.testing.assert_allclose(rep["costs"][:2], golden["costs"][:2],
+                               rtol=FIRST_STEP_RTOL[golden["workload"]])
+    if not golden.get("refine_max"):
+        assert rep["pcg_iters"][0] == golden["pcg_iters"][0]
 
 
 _SOLVES = {}
