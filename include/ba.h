@@ -107,7 +107,12 @@ typedef struct {
                                standard PCG with S streamed through shared
                                memory by bulk copies, one CTA per SM and the
                                same number of blocks of S per CTA (falls back
-                               to 1 when its plan does not fit)              */
+                               to 1 when its plan does not fit); 5: the same
+                               with one fused reduction per iteration (the
+                               same iterates in exact arithmetic; measured
+                               slower on this part: seven FP64 dot products
+                               per iteration cost more than the grid barrier
+                               they save)                                    */
   double mu_min;            /* floor of the damping used in the linear system;
                                < 0: auto (1e-4 for BA_FP32, where rounding in
                                the FP32 Schur complement otherwise exceeds its

@@ -159,8 +159,9 @@ static ba_status check_options(const ba_options* o, std::string& err) {
     err = "pcg_resident_cap must be >= 0";
     return BA_ERR_INVALID_ARG;
   }
-  if (o->pcg_variant < 0 || o->pcg_variant > 4) {
-    err = "pcg_variant must be 0 (auto), 1 (standard), 2 (pipelined), 3 (cluster) or 4 (streamed)";
+  if (o->pcg_variant < 0 || o->pcg_variant > 5) {
+    err = "pcg_variant must be 0 (auto), 1 (standard), 2 (pipelined), 3 (cluster), 4 (streamed) "
+          "or 5 (streamed, one reduction per iteration)";
     return BA_ERR_INVALID_ARG;
   }
   if (o->solver < BA_SOLVER_AUTO || o->solver > BA_SOLVER_PCG) {
@@ -722,7 +723,7 @@ ba_status ba_set_problem(ba_handle* h, int32_t n_cams, int32_t n_pts, int64_t n_
     CK(cudaMemcpy(d.pcg_lown, plan.lown.data(), plan.lown.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     // S that does not stay resident in shared memory is streamed through it
     // by bulk copies (auto), or always when asked for (variant 4)
-    const bool want_stream = h->opts.pcg_variant == 4 ||
+    const bool want_stream = h->opts.pcg_variant == 4 || h->opts.pcg_variant == 5 ||
                              (h->opts.pcg_variant == 0 && cfg.pcg_smem == 0);
     if (want_stream) {
       PcsPlan ps;
@@ -734,12 +735,14 @@ ba_status ba_set_problem(ba_handle* h, int32_t n_cams, int32_t n_pts, int64_t n_
                                          cudaMemcpyHostToDevice) == cudaSuccess;
         };
         if (!(up(d.pcs_rows, ps.rows) && up(d.pcs_uptr, ps.uptr) && up(d.pcs_ucol, ps.ucol) &&
-              up(d.pcs_ioff, ps.ioff) && up(d.pcs_wrow, ps.wrow) && up(d.pcs_idx, ps.idx))) {
+              up(d.pcs_ioff, ps.ioff) && up(d.pcs_wrow, ps.wrow) && up(d.pcs_idx, ps.idx) &&
+              keep(h, d.pcs_w, (size_t)2 * 6 * C * Tsz))) {
           h->err = "ba_set_problem: out of device memory (streamed PCG plan)";
           free_problem(h);
           return BA_ERR_OOM;
         }
         cfg.pcg_pipelined = 0;
+        cfg.pcs_one_sync = h->opts.pcg_variant == 5 ? 1 : 0;
       } else {
         cfg.pcs_smem = 0;
       }
@@ -879,7 +882,7 @@ ba_status ba_solve(ba_handle* h, ba_report* out) {
     out->n_kernels = h->marks.launches;
     const SolveConfig& c = h->cfg;
     out->pcg_variant = c.solver != BA_SOLVER_PCG ? 0
-                       : c.pcs_smem > 0         ? 4
+                       : c.pcs_smem > 0         ? (c.pcs_one_sync ? 5 : 4)
                        : c.pcc_cs > 0           ? 3
                        : c.pcg_pipelined        ? 2
                                                 : 1;

@@ -138,6 +138,7 @@ struct DevProblem {
   int32_t* pcs_ioff = nullptr;
   int32_t* pcs_wrow = nullptr;
   uint32_t* pcs_idx = nullptr;
+  void* pcs_w = nullptr;  // [2][6C] T: M q of the last two iterations (single-reduction PCG)
   // cluster PCG plan
   int32_t* pcc_rows = nullptr;  // [cs + 1] first block row of each CTA
   int32_t* pcc_nres = nullptr;  // [cs] blocks of S each CTA keeps in shared memory

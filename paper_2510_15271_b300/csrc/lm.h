@@ -58,6 +58,7 @@ struct SolveConfig {
   int pcs_nd = 1;          // streamed PCG: own elements per consumer thread (kernel variant)
   int pcs_maxu = 0, pcs_rmax = 0;  // streamed PCG: most listed columns / rows of one CTA
   float pcs_l2_keep = 0.f;  // streamed PCG: share of S's lines copied with evict_last priority
+  int pcs_one_sync = 0;     // streamed PCG: one fused reduction per iteration (else two)
   Marks* marks = nullptr;
 };
 

@@ -404,6 +404,7 @@ struct StreamArgs {
   double refine_tol;
   int maxu, rmax;
   float l2_keep;  // fraction of S's lines copied with evict_last priority (0: no hint)
+  int one_sync;   // 1: one fused reduction per iteration (variant 5); 0: the standard two
 };
 
 // Shared-memory layout (dynamic): ring [kSWarps][NS][kSlice][36] T |
@@ -419,7 +420,7 @@ __host__ __device__ inline size_t stream_smem_bytes(int maxu, int rmax) {
   o += (size_t)rmax * 6 * sizeof(double) * 2;
   o += (size_t)kSWarps * 12 * sizeof(double);
   o += (size_t)kSWarps * NS * sizeof(uint64_t);
-  o += 64 * sizeof(double) + 32 * sizeof(int);
+  o += 96 * sizeof(double) + 32 * sizeof(int);
   return o;
 }
 
@@ -445,9 +446,9 @@ __global__ void __launch_bounds__(kSThreads, 1) k_pcg_stream(DevProblem d, Strea
   p += (size_t)kSWarps * 12 * sizeof(double);
   uint64_t* full = reinterpret_cast<uint64_t*>(p);
   p += (size_t)kSWarps * NS * sizeof(uint64_t);
-  double* red = reinterpret_cast<double*>(p);  // [kSWarps * 4] + broadcast [8]
-  double* bcast = red + kSWarps * 4;
-  p += 64 * sizeof(double);
+  double* red = reinterpret_cast<double*>(p);  // [kSWarps * 8] + broadcast [8]
+  double* bcast = red + kSWarps * 8;
+  p += 96 * sizeof(double);
   int* misc = reinterpret_cast<int*>(p);  // fail | first[kSWarps] | last[kSWarps]
   int* fail = misc;
   int* sfirst = misc + 1;
@@ -628,10 +629,153 @@ __global__ void __launch_bounds__(kSThreads, 1) k_pcg_stream(DevProblem d, Strea
     return k;
   };
 
+  // The same Krylov iterates with one fused reduction per iteration (the
+  // rearrangement of D'Azevedo, Eijkhout & Romine 1993): z is carried by
+  // the recurrence z_k+1 = z_k - alpha_k M q_k, so with M symmetric
+  //   rho_k+1  = rho_k - 2 alpha_k (z_k . q_k) + alpha_k^2 (q_k . M q_k)
+  //   |r_k+1|^2 = |r_k|^2 - 2 alpha_k (r_k . q_k) + alpha_k^2 (q_k . q_k)
+  // and every scalar of the next iteration follows from seven dot products
+  // known right after the product with S; rho_k and |r_k|^2 themselves are
+  // summed directly each iteration, so the expansions extrapolate one step.
+  // After the one grid barrier every CTA stages the next search direction
+  //   p_k+1 = (z_k - alpha_k w_k) + beta_k+1 p_k,  w_k = M q_k,
+  // for its referenced columns from the owners' z_k, w_k, p_k (two buffers
+  // each, by parity), exactly as the owners form their own rows.
+  T* zb[2] = {(T*)d.z, (T*)d.rv};
+  T* wb[2] = {(T*)d.pcs_w, (T*)d.pcs_w + 6 * (int64_t)d.C};
+  __shared__ T s_alp;  // alpha of the previous iteration
+  auto pcg_one = [&](const T* rhs, T* xout, double tol, int max_iters, double& rel) -> int {
+    T xr[ND], rr[ND], zr[ND], pr[ND], wr[ND];
+    double l2[2] = {0.0, 0.0};
+#pragma unroll
+    for (int j = 0; j < ND; ++j) {
+      const int t = tid + j * kSConsumers;
+      xr[j] = rr[j] = pr[j] = wr[j] = T(0);
+      if (t < nel) rr[j] = rhs[e0 + t];
+    }
+    precondition(rr, zr, l2[0], l2[1]);  // z_0 = M r_0 (also into d.z = zb[0])
+    // "previous" buffers for the first staging: z_-1 = z_0, w_-1 = p_-1 = 0
+#pragma unroll
+    for (int j = 0; j < ND; ++j) {
+      const int t = tid + j * kSConsumers;
+      if (t < nel) {
+        zb[1][e0 + t] = zr[j];
+        wb[1][e0 + t] = T(0);
+        pb[1][e0 + t] = T(0);
+      }
+    }
+    cta_sum<2>(l2, red, partB);
+    grid_sync(d.barrier, epoch, err);
+    double tot[7];
+    {
+      double t2[2];
+      grid_total<2>(partB, bcast, t2);
+      tot[0] = t2[0];
+      tot[1] = t2[1];
+    }
+    double r2 = tot[1];
+    const double bnorm = sqrt(r2);
+    const double thr2 = (tol * bnorm) * (tol * bnorm);
+    int k = 0;
+    if (tid == 0) {
+      s_bt = T(0);
+      s_alp = T(0);
+      s_go = (max_iters > 0 && r2 > thr2 && !bad()) ? 1 : 0;
+    }
+    consumers_sync();
+    while (s_go) {
+      const T bt = s_bt, alp = s_alp;
+      const int cur = k & 1, prv = cur ^ 1;
+      // z_k = z_k-1 - alpha_k-1 w_k-1, p_k = z_k + beta_k p_k-1: own rows in
+      // registers and in this parity's buffers, referenced columns into sv
+#pragma unroll
+      for (int j = 0; j < ND; ++j) {
+        const int t = tid + j * kSConsumers;
+        zr[j] = zr[j] - alp * wr[j];
+        pr[j] = zr[j] + bt * pr[j];
+        if (t < nel) {
+          zb[cur][e0 + t] = zr[j];
+          pb[cur][e0 + t] = pr[j];
+        }
+      }
+      for (int i = tid; i < 6 * nu; i += kSConsumers) {
+        const int gi = 6 * __ldg(ucol + i / 6) + i % 6;
+        const T zk = __ldcg(zb[prv] + gi) - alp * __ldcg(wb[prv] + gi);
+        sv[i] = zk + bt * __ldcg(pb[prv] + gi);
+      }
+      consumers_sync();
+      spmv_stream<T, T, T, NS>(d, wp, nrow, sfirst, slast, full, fail, ring, ridx, sv, sq, fl, g,
+                               err, policy, hint);
+      // q = S p (own rows, in sq), w = M q; the seven dot products
+      double dl[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int j = 0; j < ND; ++j) {
+        const int t = tid + j * kSConsumers;
+        wr[j] = T(0);
+        if (t >= nel) continue;
+        const int lr = t / 6, e = t - 6 * lr;
+        const T* M = Minv + 36 * (int64_t)(r0 + lr) + 6 * e;
+        T wi = T(0);
+#pragma unroll
+        for (int f = 0; f < 6; ++f) wi += __ldg(M + f) * (T)sq[6 * lr + f];
+        wr[j] = wi;
+        wb[cur][e0 + t] = wi;
+        const double q = (double)(T)sq[t], p = (double)pr[j], z = (double)zr[j],
+                     r = (double)rr[j], w = (double)wi;
+        dl[0] += p * q;
+        dl[1] += z * q;
+        dl[2] += q * w;
+        dl[3] += r * z;
+        dl[4] += r * r;
+        dl[5] += r * q;
+        dl[6] += q * q;
+      }
+      cta_sum<7>(dl, red, partB);
+      grid_sync(d.barrier, epoch, err);
+      const bool e_now = tid == 0 ? bad() : false;
+      grid_total<7>(partB, bcast, tot);
+      if (tid == 0) {
+        const double pq = tot[0], zq = tot[1], qw = tot[2], rz = tot[3], rrk = tot[4],
+                     rq = tot[5], qq = tot[6];
+        int go = pq > 0.0 ? 1 : 0;  // S positive definite along p
+        if (go) {
+          const double al = rz / pq;
+          const double rz1 = rz - 2.0 * al * zq + al * al * qw;
+          const double rr1 = rrk - 2.0 * al * rq + al * al * qq;
+          s_al = (T)al;
+          s_alp = (T)al;
+          s_bt = (T)(rz1 / rz);
+          r2 = rr1;
+          go = (k + 1 < max_iters && rr1 > thr2 && rz1 > 0.0 && !e_now) ? 2 : 1;
+        }
+        s_go = go;  // 0: stop before the step, 1: take the step and stop, 2: go on
+      }
+      consumers_sync();
+      if (s_go == 0) break;
+      const T al = s_al;
+#pragma unroll
+      for (int j = 0; j < ND; ++j) {
+        const int t = tid + j * kSConsumers;
+        xr[j] += al * pr[j];
+        if (t < nel) rr[j] -= al * (T)sq[t];
+      }
+      ++k;
+      if (s_go == 1) break;
+    }
+#pragma unroll
+    for (int j = 0; j < ND; ++j) {
+      const int t = tid + j * kSConsumers;
+      if (t < nel) xout[e0 + t] = xr[j];
+    }
+    rel = bnorm > 0.0 ? sqrt(fmax(r2, 0.0)) / bnorm : 0.0;  // current in thread 0 only
+    return k;
+  };
+
   double rel = 0.0;
   int iters = 0;
   if (!a.refine) {
-    iters = pcg((const T*)d.b, (T*)d.dc, a.tol, a.max_iters, rel);
+    iters = a.one_sync ? pcg_one((const T*)d.b, (T*)d.dc, a.tol, a.max_iters, rel)
+                       : pcg((const T*)d.b, (T*)d.dc, a.tol, a.max_iters, rel);
   } else {
     // FP64 iterative refinement: solve S d = r in T, x += d, r = b - S x in
     // FP64 (S as stored, promoted), until ||r|| <= refine_tol ||b||
@@ -659,7 +803,8 @@ __global__ void __launch_bounds__(kSThreads, 1) k_pcg_stream(DevProblem d, Strea
       consumers_sync();
       if (!s_more) break;
       double rel_in;
-      iters += pcg(rhs, dx, a.tol, a.max_iters, rel_in);
+      iters += a.one_sync ? pcg_one(rhs, dx, a.tol, a.max_iters, rel_in)
+                          : pcg(rhs, dx, a.tol, a.max_iters, rel_in);
 #pragma unroll
       for (int j = 0; j < ND; ++j) {
         const int t = tid + j * kSConsumers;
@@ -846,7 +991,7 @@ void launch_pcg_stream(const DevProblem& d, const SolveConfig& cfg, cudaStream_t
   cudaMemsetAsync(d.barrier, 0, sizeof(unsigned), s);  // arrival counter only
   DevProblem dd = d;
   StreamArgs a{cfg.pcg_tol, cfg.pcg_max, cfg.refine, cfg.refine_max, cfg.refine_tol,
-               cfg.pcs_maxu, cfg.pcs_rmax, cfg.pcs_l2_keep};
+               cfg.pcs_maxu, cfg.pcs_rmax, cfg.pcs_l2_keep, cfg.pcs_one_sync};
   void* args[] = {&dd, &a};
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3(cfg.pcs_blocks);

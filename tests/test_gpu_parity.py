@@ -157,19 +157,22 @@ def test_cluster_pcg_with_streamed_blocks(prec):
         assert rel.max() <= COST_RTOL, (rel, rt["costs"], ref.costs)
 
 
+@pytest.mark.parametrize("variant", [4, 5])
 @pytest.mark.parametrize("seed,kw", [
     (4, {}),                                                   # 60 cameras
     (8, dict(n_cams=7, n_pts=700, length_m=14.0)),             # fewer cameras than warps' ranges
 ])
-def test_streamed_pcg_tight_matches_oracle_cholesky(seed, kw):
-    """The streamed kernel (variant 4: S copied through shared memory in
-    slices, one CTA per SM, rows split over the CTA's warps by block count):
+def test_streamed_pcg_tight_matches_oracle_cholesky(seed, kw, variant):
+    """The streamed kernel (S copied through shared memory in slices, one CTA
+    per SM, rows split over the CTA's warps by block count), with the
+    standard recurrence (4) and with one fused reduction per iteration (5):
     exact-enough solves reproduce the oracle's direct-solve LM path to 1e-9
     per iteration."""
     s = _driving_small(seed=seed, **kw)
     n = 6 * s.n_cams
     rep, q, p = ba.solve_scene(s, "fp64", max_lm_iters=6, solver=ba.BA_SOLVER_PCG,
-                               pcg_tol=1e-13, pcg_max_iters=4 * n, pcg_variant=4)
+                               pcg_tol=1e-13, pcg_max_iters=4 * n, pcg_variant=variant)
+    assert rep["pcg_variant"] == variant
     _, ref = _oracle(s, 6, "dense")
     rel = np.abs(rep["costs"] - ref.costs) / ref.costs
     assert rel.max() <= COST_RTOL, (rel, rep["costs"], ref.costs)
@@ -178,9 +181,11 @@ def test_streamed_pcg_tight_matches_oracle_cholesky(seed, kw):
     assert rot < 1e-7 and pos < 1e-7, (rot, pos)
 
 
-def test_streamed_pcg_production_tolerance_matches_oracle_pcg():
+@pytest.mark.parametrize("variant", [4, 5])
+def test_streamed_pcg_production_tolerance_matches_oracle_pcg(variant):
     s = _driving_small(seed=3)
-    rep, _, _ = ba.solve_scene(s, "fp64", max_lm_iters=8, solver=ba.BA_SOLVER_PCG, pcg_variant=4)
+    rep, _, _ = ba.solve_scene(s, "fp64", max_lm_iters=8, solver=ba.BA_SOLVER_PCG,
+                               pcg_variant=variant)
     _, ref = _oracle(s, 8, "pcg")
     rel = np.abs(rep["costs"] - ref.costs) / ref.costs
     assert rel.max() <= PCG_COST_RTOL, (rel, rep["costs"], ref.costs)
@@ -206,6 +211,7 @@ def test_streamed_pcg_is_auto_on_a_system_that_does_not_stay_resident(prec):
     without refinement."""
     s = scenes.make_scene("city", seed=9, n_cams=3000, n_pts=300000)
     ra, _, _ = ba.solve_scene(s, prec, max_lm_iters=3, solver=ba.BA_SOLVER_PCG, refine=1)
+    assert ra["pcg_variant"] == 4
     rg, _, _ = ba.solve_scene(s, prec, max_lm_iters=3, solver=ba.BA_SOLVER_PCG, refine=1,
                               pcg_variant=1)
     tol = 1e-6 if prec == "fp64" else 1e-4
