@@ -503,10 +503,7 @@ ba_status ba_set_problem(ba_handle* h, int32_t n_cams, int32_t n_pts, int64_t n_
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s));
 
-    // sub-segments of at most sub_len pairs (host side, from the segment table)
-    std::vector<int32_t> hsb(nseg + 1), hcs(nchunks + 1);
-    CK(cudaMemcpy(hsb.data(), d.seg_begin, (nseg + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(hcs.data(), d.chunk_seg, (nchunks + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    // sub-segments of at most sub_len pairs
     // blocks on and right of the diagonal per row: the Schur kernel's accumulators
     {
       std::vector<int32_t> hdiag(C), hrp(C + 1);
@@ -518,63 +515,51 @@ ba_status ba_set_problem(ba_handle* h, int32_t n_cams, int32_t n_pts, int64_t n_
     // The Schur kernel stages only the sub-segments of split segments; the
     // shortest sub_len (best balance) whose staging, with the accumulators of
     // the longest row (or at least 64 of them), leaves room for two CTAs per
-    // SM.
+    // SM.  The staged counts of every candidate length come from one pass on
+    // the device.
     int smem_sm = 0;
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device);
     const size_t two_per_sm = std::min<size_t>(max_dyn_smem(h->device) - 2048,
                                                (size_t)smem_sm / 2 - 4096);
-    int sub_len = 8, max_rs = 0;
-    auto staged = [&](int len) {
-      int most = 0;
-      for (int ch = 0; ch < nchunks; ++ch) {
-        int n = 0;
-        for (int sg = hcs[ch]; sg < hcs[ch + 1]; ++sg) {
-          const int ns = (hsb[sg + 1] - hsb[sg] + len - 1) / len;
-          if (ns > 1) n += ns;
-        }
-        most = std::max(most, n);
-      }
-      return most;
-    };
-    for (;; sub_len *= 2) {
-      max_rs = staged(sub_len);
-      if (schur_smem(prec, std::min(d.max_row_upper, 64), max_rs) <= two_per_sm || sub_len >= 4096)
-        break;
-    }
-    // the table itself is built on the device: counts, scan, fill
-    int64_t nsub64 = 0;
-    for (int sg = 0; sg < nseg; ++sg) nsub64 += (hsb[sg + 1] - hsb[sg] + sub_len - 1) / sub_len;
-    const int nsub = (int)nsub64;
-    // staging index of every sub-segment (sub-segments are numbered in
-    // segment order, as the device fill numbers them)
-    std::vector<int32_t> hrs;
-    hrs.reserve(std::max(nsub, 1));
-    for (int ch = 0; ch < nchunks; ++ch) {
-      int r = 0;
-      for (int sg = hcs[ch]; sg < hcs[ch + 1]; ++sg) {
-        const int ns = (hsb[sg + 1] - hsb[sg] + sub_len - 1) / sub_len;
-        for (int q = 0; q < ns; ++q) hrs.push_back(ns > 1 ? r++ : -1);
-      }
-    }
-    if ((int)hrs.size() != nsub) {
-      h->err = "ba_set_problem: inconsistent Schur segment table";
-      free_problem(h);
-      return BA_ERR_CUDA;
-    }
+    int32_t* stc = (int32_t*)tmp.get((size_t)nchunks * kSubLens * sizeof(int32_t) + 4);
     int32_t* scnt = (int32_t*)tmp.get((size_t)(nseg + 1) * sizeof(int32_t));
-    ok = scnt && keep(h, d.sub_begin, (nsub + 1) * sizeof(int32_t)) &&
+    int32_t* sbase = (int32_t*)tmp.get((size_t)(nseg + 1) * sizeof(int32_t));
+    ok = stc && scnt && sbase && keep(h, d.seg_sub, (nseg + 1) * sizeof(int32_t));
+    if (!ok) {
+      h->err = "ba_set_problem: out of device memory (sub-segments)";
+      free_problem(h);
+      return BA_ERR_OOM;
+    }
+    launch_stage_counts(nchunks, d.chunk_seg, d.seg_begin, stc, s);
+    CK(cudaGetLastError());
+    std::vector<int32_t> hstc((size_t)nchunks * kSubLens);
+    CK(cudaMemcpyAsync(hstc.data(), stc, hstc.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int sub_len = kSubLen0, max_rs = 0;
+    for (int j = 0; j < kSubLens; ++j) {
+      sub_len = kSubLen0 << j;
+      max_rs = 0;
+      for (int ch = 0; ch < nchunks; ++ch) max_rs = std::max(max_rs, hstc[(size_t)ch * kSubLens + j]);
+      if (schur_smem(prec, std::min(d.max_row_upper, 64), max_rs) <= two_per_sm) break;
+    }
+    // the table: counts, scan, staging bases, fill
+    launch_sub_counts(nseg, d.seg_begin, sub_len, scnt, s);
+    launch_scan_i32(scnt, d.seg_sub, nseg, stmp2, d.seg_sub + nseg, s);
+    launch_stage_base(nchunks, d.chunk_seg, d.seg_begin, sub_len, sbase, s);
+    CK(cudaGetLastError());
+    int32_t nsub = 0;
+    CK(cudaMemcpyAsync(&nsub, d.seg_sub + nseg, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    ok = keep(h, d.sub_begin, (nsub + 1) * sizeof(int32_t)) &&
          keep(h, d.sub_slot, std::max(nsub, 1) * sizeof(int32_t)) &&
-         keep(h, d.seg_sub, (nseg + 1) * sizeof(int32_t)) &&
          keep(h, d.sub_rs, std::max(nsub, 1) * sizeof(int32_t));
     if (!ok) {
       h->err = "ba_set_problem: out of device memory (sub-segments)";
       free_problem(h);
       return BA_ERR_OOM;
     }
-    if (nsub) CK(cudaMemcpy(d.sub_rs, hrs.data(), nsub * sizeof(int32_t), cudaMemcpyHostToDevice));
-    launch_sub_counts(nseg, d.seg_begin, sub_len, scnt, s);
-    launch_scan_i32(scnt, d.seg_sub, nseg, stmp2, d.seg_sub + nseg, s);
-    launch_sub_fill(nseg, d.seg_begin, d.seg_slot, d.seg_sub, sub_len, d.sub_begin, d.sub_slot, s);
+    launch_sub_fill(nseg, d.seg_begin, d.seg_slot, d.seg_sub, sbase, sub_len, d.sub_begin,
+                    d.sub_slot, d.sub_rs, s);
     const int32_t npi = (int32_t)np;
     CK(cudaMemcpyAsync(d.sub_begin + nsub, &npi, sizeof(int32_t), cudaMemcpyHostToDevice, s));
     CK(cudaGetLastError());
@@ -711,16 +696,19 @@ ba_status ba_set_problem(ba_handle* h, int32_t n_cams, int32_t n_pts, int64_t n_
     ok = keep(h, d.pcg_ucol, std::max<size_t>(plan.ucol.size(), 1) * sizeof(int32_t)) &&
          keep(h, d.pcg_uptr, plan.uptr.size() * sizeof(int32_t)) &&
          keep(h, d.pcg_lcol, std::max<size_t>(plan.lcol.size(), 1) * sizeof(int32_t)) &&
-         keep(h, d.pcg_lown, plan.lown.size() * sizeof(int32_t));
+         keep(h, d.pcg_lown, std::max<size_t>(plan.lown.size(), 1) * sizeof(int32_t));
     if (!ok) {
       h->err = "ba_set_problem: out of device memory (PCG plan)";
       free_problem(h);
       return BA_ERR_OOM;
     }
-    CK(cudaMemcpy(d.pcg_ucol, plan.ucol.data(), plan.ucol.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    if (!plan.ucol.empty())
+      CK(cudaMemcpy(d.pcg_ucol, plan.ucol.data(), plan.ucol.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d.pcg_uptr, plan.uptr.data(), plan.uptr.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d.pcg_lcol, plan.lcol.data(), plan.lcol.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d.pcg_lown, plan.lown.data(), plan.lown.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    if (!plan.lcol.empty())
+      CK(cudaMemcpy(d.pcg_lcol, plan.lcol.data(), plan.lcol.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    if (!plan.lown.empty())
+      CK(cudaMemcpy(d.pcg_lown, plan.lown.data(), plan.lown.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     // S that does not stay resident in shared memory is streamed through it
     // by bulk copies (auto), or always when asked for (variant 4)
     const bool want_stream = h->opts.pcg_variant == 4 || h->opts.pcg_variant == 5 ||

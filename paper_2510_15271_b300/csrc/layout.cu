@@ -600,14 +600,73 @@ __global__ void k_sub_counts(int nseg, const int32_t* __restrict__ seg_begin, in
 
 __global__ void k_sub_fill(int nseg, const int32_t* __restrict__ seg_begin,
                            const int32_t* __restrict__ seg_slot, const int32_t* __restrict__ seg_sub,
-                           int sub_len, int32_t* __restrict__ sub_begin,
-                           int32_t* __restrict__ sub_slot) {
+                           const int32_t* __restrict__ stage_base, int sub_len,
+                           int32_t* __restrict__ sub_begin, int32_t* __restrict__ sub_slot,
+                           int32_t* __restrict__ sub_rs) {
   for (int sg = blockIdx.x * blockDim.x + threadIdx.x; sg < nseg; sg += gridDim.x * blockDim.x) {
     int u = seg_sub[sg];
+    const bool split = seg_begin[sg + 1] - seg_begin[sg] > sub_len;
+    int r = split ? stage_base[sg] : -1;
     for (int q = seg_begin[sg]; q < seg_begin[sg + 1]; q += sub_len, ++u) {
       sub_begin[u] = q;
       sub_slot[u] = seg_slot[sg];
+      sub_rs[u] = r;
+      if (split) ++r;
     }
+  }
+}
+
+// One warp per chunk: the staged sub-segments of the chunk for every
+// candidate length at once.
+__global__ void k_stage_counts(int nchunks, const int32_t* __restrict__ chunk_seg,
+                               const int32_t* __restrict__ seg_begin, int32_t* __restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  const int ch = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  if (ch >= nchunks) return;
+  int acc[kSubLens];
+#pragma unroll
+  for (int j = 0; j < kSubLens; ++j) acc[j] = 0;
+  for (int sg = chunk_seg[ch] + lane; sg < chunk_seg[ch + 1]; sg += 32) {
+    const int len = seg_begin[sg + 1] - seg_begin[sg];
+#pragma unroll
+    for (int j = 0; j < kSubLens; ++j) {
+      const int sl = kSubLen0 << j;
+      const int ns = (len + sl - 1) / sl;
+      if (ns > 1) acc[j] += ns;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kSubLens; ++j) {
+    int v = acc[j];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) cnt[(size_t)ch * kSubLens + j] = v;
+  }
+}
+
+// One warp per chunk: exclusive prefix, in segment order, of the staged
+// sub-segments of each segment.
+__global__ void k_stage_base(int nchunks, const int32_t* __restrict__ chunk_seg,
+                             const int32_t* __restrict__ seg_begin, int sub_len,
+                             int32_t* __restrict__ base) {
+  const int lane = threadIdx.x & 31;
+  const int ch = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  if (ch >= nchunks) return;
+  const int end = chunk_seg[ch + 1];
+  int run = 0;
+  for (int s0 = chunk_seg[ch]; s0 < end; s0 += 32) {
+    const int sg = s0 + lane;
+    int v = 0;
+    if (sg < end) {
+      const int ns = (seg_begin[sg + 1] - seg_begin[sg] + sub_len - 1) / sub_len;
+      v = ns > 1 ? ns : 0;
+    }
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (sg < end) base[sg] = run + x - v;
+    run += __shfl_sync(0xffffffffu, x, 31);
   }
 }
 
@@ -617,10 +676,26 @@ void launch_sub_counts(int nseg, const int32_t* seg_begin, int sub_len, int32_t*
 }
 
 void launch_sub_fill(int nseg, const int32_t* seg_begin, const int32_t* seg_slot,
-                     const int32_t* seg_sub, int sub_len, int32_t* sub_begin, int32_t* sub_slot,
-                     cudaStream_t s) {
-  k_sub_fill<<<grid_for(nseg, 256), 256, 0, s>>>(nseg, seg_begin, seg_slot, seg_sub, sub_len,
-                                                  sub_begin, sub_slot);
+                     const int32_t* seg_sub, const int32_t* stage_base, int sub_len,
+                     int32_t* sub_begin, int32_t* sub_slot, int32_t* sub_rs, cudaStream_t s) {
+  k_sub_fill<<<grid_for(nseg, 256), 256, 0, s>>>(nseg, seg_begin, seg_slot, seg_sub, stage_base,
+                                                  sub_len, sub_begin, sub_slot, sub_rs);
+}
+
+void launch_stage_counts(int nchunks, const int32_t* chunk_seg, const int32_t* seg_begin,
+                         int32_t* cnt, cudaStream_t s) {
+  if (nchunks <= 0) return;
+  const int64_t threads = (int64_t)nchunks * 32;
+  k_stage_counts<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(nchunks, chunk_seg, seg_begin,
+                                                                   cnt);
+}
+
+void launch_stage_base(int nchunks, const int32_t* chunk_seg, const int32_t* seg_begin,
+                       int sub_len, int32_t* base, cudaStream_t s) {
+  if (nchunks <= 0) return;
+  const int64_t threads = (int64_t)nchunks * 32;
+  k_stage_base<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(nchunks, chunk_seg, seg_begin,
+                                                                 sub_len, base);
 }
 
 void launch_pair_counts(const DevProblem& d, int32_t* cnt, int32_t* nch, cudaStream_t s) {

@@ -38,9 +38,21 @@ void launch_pair_counts(const DevProblem& d, int32_t* cnt, int32_t* nch, cudaStr
 // Sub-segments of the Schur pair list (at most sub_len pairs each)
 void launch_sub_counts(int nseg, const int32_t* seg_begin, int sub_len, int32_t* cnt,
                        cudaStream_t s);
+// ... the first pair, slot and staging index (-1: not staged) of each
 void launch_sub_fill(int nseg, const int32_t* seg_begin, const int32_t* seg_slot,
-                     const int32_t* seg_sub, int sub_len, int32_t* sub_begin, int32_t* sub_slot,
-                     cudaStream_t s);
+                     const int32_t* seg_sub, const int32_t* stage_base, int sub_len,
+                     int32_t* sub_begin, int32_t* sub_slot, int32_t* sub_rs, cudaStream_t s);
+// Candidate sub-segment lengths kSubLen0 << j, j < kSubLens
+constexpr int kSubLen0 = 8, kSubLens = 10;
+// Per chunk and candidate length: how many sub-segments of split segments
+// (more than one sub-segment) the chunk holds, the ones the Schur kernel
+// stages in shared memory.  cnt is [nchunks][kSubLens].
+void launch_stage_counts(int nchunks, const int32_t* chunk_seg, const int32_t* seg_begin,
+                         int32_t* cnt, cudaStream_t s);
+// Per segment: the staging index of its first sub-segment within its chunk
+// (split segments numbered in segment order) for the given length.
+void launch_stage_base(int nchunks, const int32_t* chunk_seg, const int32_t* seg_begin,
+                       int sub_len, int32_t* base, cudaStream_t s);
 // d.s_mirror from the pattern (d.s_rowptr, d.s_col)
 void launch_mirror(const DevProblem& d, cudaStream_t s);
 void launch_gen_pairs(const DevProblem& d, const int32_t* chunk_ptr, const int32_t* pair_ptr,

@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "ba_internal.h"
@@ -99,6 +101,33 @@ void launch_rmse_step(const DevProblem& d, cudaStream_t s);
 
 // solvers.cu
 void launch_linear_solve(const DevProblem& d, const SolveConfig& cfg, cudaStream_t s);
+// The sorted distinct columns among col[0, n) (the blocks of one CTA's rows)
+// into `out`, and each one's place in that list in `pos` (indexed by column).
+// `stamp` (C entries, set to a value no call uses) marks the columns seen
+// under this call's `tag`; the distinct columns are sorted, or read off in
+// order by one pass over all C columns when that is cheaper.  Replaces a sort
+// of every block's column and a binary search per block.
+inline void distinct_columns(const int32_t* col, int64_t n, int C, int tag,
+                             std::vector<int32_t>& stamp, std::vector<int32_t>& pos,
+                             std::vector<int32_t>& out) {
+  out.clear();
+  for (int64_t k = 0; k < n; ++k) {
+    const int c = col[k];
+    if (stamp[c] != tag) {
+      stamp[c] = tag;
+      out.push_back(c);
+    }
+  }
+  const double m = (double)out.size();
+  if (m * std::log2(std::max(m, 2.0)) > (double)C) {
+    out.clear();
+    for (int c = 0; c < C; ++c)
+      if (stamp[c] == tag) out.push_back(c);
+  } else {
+    std::sort(out.begin(), out.end());
+  }
+  for (size_t k = 0; k < out.size(); ++k) pos[out[k]] = (int32_t)k;
+}
 // Per-CTA column lists of the PCG kernel's shared-memory variant (host copy).
 struct PcgPlan {
   std::vector<int32_t> ucol;  // concatenated sorted column lists of the CTAs

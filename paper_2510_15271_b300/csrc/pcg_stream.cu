@@ -918,15 +918,13 @@ bool plan_pcg_stream(int precision, int device, const std::vector<int32_t>& rowp
   plan.wrow.assign((size_t)G * kSWarps * 2, -1);
   plan.idx.clear();
   int maxu = 0, rmax = 0;
-  std::vector<int32_t> cols;
+  std::vector<int32_t> cols, stamp(C, -1), pos(C, 0);
   for (int g = 0; g < G; ++g) {
     const int r0 = plan.rows[g], r1 = plan.rows[g + 1];
     if (r1 - r0 > 65535) return false;
     rmax = std::max(rmax, r1 - r0);
     const int B0 = rowptr[r0], B1 = rowptr[r1];
-    cols.assign(col.begin() + B0, col.begin() + B1);
-    std::sort(cols.begin(), cols.end());
-    cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+    distinct_columns(col.data() + B0, B1 - B0, C, g, stamp, pos, cols);
     if (cols.size() > 65535) return false;
     maxu = std::max(maxu, (int)cols.size());
     plan.uptr[g] = (int32_t)plan.ucol.size();
@@ -942,8 +940,7 @@ bool plan_pcg_stream(int precision, int device, const std::vector<int32_t>& rowp
       if (s1 <= s0) continue;
       for (int b = B0 + s0; b < B0 + s1; ++b) {
         while (rowptr[row + 1] <= b) ++row;
-        const int lc = (int)(std::lower_bound(cols.begin(), cols.end(), col[b]) - cols.begin());
-        plan.idx.push_back(((uint32_t)(row - r0) << 16) | (uint32_t)lc);
+        plan.idx.push_back(((uint32_t)(row - r0) << 16) | (uint32_t)pos[col[b]]);
         if (b == B0 + s0) plan.wrow[2 * ((size_t)g * kSWarps + w)] = row - r0;
         plan.wrow[2 * ((size_t)g * kSWarps + w) + 1] = row - r0;
       }

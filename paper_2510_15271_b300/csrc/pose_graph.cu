@@ -852,16 +852,19 @@ ba_status ba_pg_set_graph(ba_pose_graph* g, int32_t n_nodes, const double* node_
     ok = keep(g, d.pcg_ucol, std::max<size_t>(plan.ucol.size(), 1) * sizeof(int32_t)) &&
          keep(g, d.pcg_uptr, plan.uptr.size() * sizeof(int32_t)) &&
          keep(g, d.pcg_lcol, std::max<size_t>(plan.lcol.size(), 1) * sizeof(int32_t)) &&
-         keep(g, d.pcg_lown, plan.lown.size() * sizeof(int32_t));
+         keep(g, d.pcg_lown, std::max<size_t>(plan.lown.size(), 1) * sizeof(int32_t));
     if (!ok) {
       g->err = "ba_pg_set_graph: out of device memory (PCG plan)";
       pg_free(g);
       return BA_ERR_OOM;
     }
-    PG_CK(cudaMemcpy(d.pcg_ucol, plan.ucol.data(), plan.ucol.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    if (!plan.ucol.empty())
+      PG_CK(cudaMemcpy(d.pcg_ucol, plan.ucol.data(), plan.ucol.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     PG_CK(cudaMemcpy(d.pcg_uptr, plan.uptr.data(), plan.uptr.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    PG_CK(cudaMemcpy(d.pcg_lcol, plan.lcol.data(), plan.lcol.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    PG_CK(cudaMemcpy(d.pcg_lown, plan.lown.data(), plan.lown.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    if (!plan.lcol.empty())
+      PG_CK(cudaMemcpy(d.pcg_lcol, plan.lcol.data(), plan.lcol.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    if (!plan.lown.empty())
+      PG_CK(cudaMemcpy(d.pcg_lown, plan.lown.data(), plan.lown.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   }
   PG_CK(cudaEventRecord(g->ev1, s));
   PG_CK(cudaEventSynchronize(g->ev1));

@@ -797,16 +797,19 @@ ba_status ba_rig_set_problem(ba_rig* r, int32_t F, int32_t R, int32_t P, int64_t
     ok = planned && rkeep(r, dr.pcg_ucol, std::max<size_t>(plan.ucol.size(), 1) * sizeof(int32_t)) &&
          rkeep(r, dr.pcg_uptr, plan.uptr.size() * sizeof(int32_t)) &&
          rkeep(r, dr.pcg_lcol, std::max<size_t>(plan.lcol.size(), 1) * sizeof(int32_t)) &&
-         rkeep(r, dr.pcg_lown, plan.lown.size() * sizeof(int32_t));
+         rkeep(r, dr.pcg_lown, std::max<size_t>(plan.lown.size(), 1) * sizeof(int32_t));
     if (!ok) {
       r->err = "ba_rig_set_problem: PCG plan or its buffers failed";
       rig_free(r);
       return BA_ERR_OOM;
     }
-    RG_CK(cudaMemcpy(dr.pcg_ucol, plan.ucol.data(), plan.ucol.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    if (!plan.ucol.empty())
+      RG_CK(cudaMemcpy(dr.pcg_ucol, plan.ucol.data(), plan.ucol.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     RG_CK(cudaMemcpy(dr.pcg_uptr, plan.uptr.data(), plan.uptr.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    RG_CK(cudaMemcpy(dr.pcg_lcol, plan.lcol.data(), plan.lcol.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    RG_CK(cudaMemcpy(dr.pcg_lown, plan.lown.data(), plan.lown.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    if (!plan.lcol.empty())
+      RG_CK(cudaMemcpy(dr.pcg_lcol, plan.lcol.data(), plan.lcol.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    if (!plan.lown.empty())
+      RG_CK(cudaMemcpy(dr.pcg_lown, plan.lown.data(), plan.lown.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   }
   RG_CK(cudaStreamSynchronize(s));
   r->loaded = true;

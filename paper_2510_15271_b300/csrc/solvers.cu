@@ -1013,20 +1013,19 @@ static void pcg_lists(int G, int R, const std::vector<int32_t>& rowptr,
   plan.lown.assign(C, 0);
   maxnnz = 0;
   maxu = 0;
-  std::vector<int32_t> cols;
+  std::vector<int32_t> cols, stamp(C, -1), pos(C, 0);
   for (int b = 0; b < G; ++b) {
     const int r0 = std::min(C, b * R), r1 = std::min(C, r0 + R);
     maxnnz = std::max(maxnnz, rowptr[r1] - rowptr[r0]);
-    cols.assign(col.begin() + rowptr[r0], col.begin() + rowptr[r1]);
-    std::sort(cols.begin(), cols.end());
-    cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+    distinct_columns(col.data() + rowptr[r0], rowptr[r1] - rowptr[r0], C, b, stamp, pos, cols);
     plan.uptr[b] = (int32_t)plan.ucol.size();
     plan.ucol.insert(plan.ucol.end(), cols.begin(), cols.end());
     maxu = std::max(maxu, (int)cols.size());
-    for (int k = rowptr[r0]; k < rowptr[r1]; ++k)
-      plan.lcol[k] = (int32_t)(std::lower_bound(cols.begin(), cols.end(), col[k]) - cols.begin());
+    for (int k = rowptr[r0]; k < rowptr[r1]; ++k) plan.lcol[k] = pos[col[k]];
     for (int i = r0; i < r1; ++i)
-      plan.lown[i] = (int32_t)(std::lower_bound(cols.begin(), cols.end(), i) - cols.begin());
+      plan.lown[i] = stamp[i] == b
+                         ? pos[i]
+                         : (int32_t)(std::lower_bound(cols.begin(), cols.end(), i) - cols.begin());
   }
   plan.uptr[G] = (int32_t)plan.ucol.size();
 }
@@ -1034,6 +1033,20 @@ static void pcg_lists(int G, int R, const std::vector<int32_t>& rowptr,
 static size_t pcg_smem_need(int precision, int maxnnz, int R, int maxu) {
   return precision == BA_FP32 ? pcg_smem_bytes<float>(maxnnz, R, maxu)
                               : pcg_smem_bytes<double>(maxnnz, R, maxu);
+}
+
+// Lower bound of a split's shared-memory need without its lists: the most
+// blocks of one CTA of R contiguous rows is exact, and a CTA's distinct
+// columns are at least as many as its longest row holds.
+static size_t pcg_smem_bound(int precision, int G, int R, const std::vector<int32_t>& rowptr,
+                             int longest_row, int& maxnnz) {
+  const int C = (int)rowptr.size() - 1;
+  maxnnz = 0;
+  for (int b = 0; b < G; ++b) {
+    const int r0 = std::min(C, b * R), r1 = std::min(C, r0 + R);
+    maxnnz = std::max(maxnnz, rowptr[r1] - rowptr[r0]);
+  }
+  return pcg_smem_need(precision, maxnnz, R, longest_row);
 }
 
 // Static shared memory of a kernel variant (the pipelined recurrence's row
@@ -1054,7 +1067,14 @@ bool plan_pcg(int precision, int device, const std::vector<int32_t>& rowptr,
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   const bool pipe = cfg.pcg_pipelined != 0;
-  int maxnnz = 0, maxu = 0;
+  int maxnnz = 0, maxu = 0, longest = 0;
+  for (int i = 0; i < C; ++i) longest = std::max(longest, rowptr[i + 1] - rowptr[i]);
+  // The column lists cost a pass over every block of S: they are built only
+  // for splits whose lower bound of the need still fits.
+  auto may_fit = [&](int G, int R, const void* fs) {
+    int mn = 0;
+    return pcg_smem_bound(precision, G, R, rowptr, longest, mn) + static_smem(fs) <= smem_limit;
+  };
   // Many short rows (a pose graph: about 7 blocks per row): one warp per row
   // would launch a CTA per 8 rows, and every iteration's grid barrier takes
   // one arrival per CTA while every CTA reads every CTA's partial sums (G^2
@@ -1068,7 +1088,7 @@ bool plan_pcg(int precision, int device, const std::vector<int32_t>& rowptr,
       int rw = 1;
       while (rw * kPcgWarps < R) rw *= 2;
       const void* fs = pcg_fn_prec(precision, true, rw, pipe);
-      if (!fs) continue;
+      if (!fs || !may_fit(G, R, fs)) continue;
       pcg_lists(G, R, rowptr, col, plan, maxnnz, maxu);
       const size_t need = pcg_smem_need(precision, maxnnz, R, maxu);
       if (need + static_smem(fs) > smem_limit) continue;
@@ -1103,13 +1123,16 @@ bool plan_pcg(int precision, int device, const std::vector<int32_t>& rowptr,
     if (occ < 1 || attempt >= 8) return false;
     G = occ * sms;
   }
-  pcg_lists(G, R, rowptr, col, plan, maxnnz, maxu);
-  size_t need = pcg_smem_need(precision, maxnnz, R, maxu);
+  size_t need = 0;
   bool smem = false;
   const void* fs = pcg_fn_prec(precision, true, rw, pipe);
-  if (fs && need + static_smem(fs) <= smem_limit) {
-    cudaFuncSetAttribute(fs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
-    smem = pcg_occupancy(fs, need) * sms >= G;
+  if (fs && may_fit(G, R, fs)) {
+    pcg_lists(G, R, rowptr, col, plan, maxnnz, maxu);
+    need = pcg_smem_need(precision, maxnnz, R, maxu);
+    if (need + static_smem(fs) <= smem_limit) {
+      cudaFuncSetAttribute(fs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+      smem = pcg_occupancy(fs, need) * sms >= G;
+    }
   }
   // Long rows that do not fit: fewer rows per CTA (more CTAs, still within
   // the co-resident grid) can keep S in shared memory (the dense 103-block-row
@@ -1120,7 +1143,7 @@ bool plan_pcg(int precision, int device, const std::vector<int32_t>& rowptr,
     int rw2 = 1;
     while (rw2 * kPcgWarps < R2) rw2 *= 2;
     const void* f2 = pcg_fn_prec(precision, true, rw2, pipe);
-    if (!f2) continue;
+    if (!f2 || !may_fit(G2, R2, f2)) continue;
     PcgPlan p2;
     int mn2 = 0, mu2 = 0;
     pcg_lists(G2, R2, rowptr, col, p2, mn2, mu2);
@@ -1136,6 +1159,15 @@ bool plan_pcg(int precision, int device, const std::vector<int32_t>& rowptr,
     maxu = mu2;
     need = need2;
     smem = true;
+  }
+  if (!smem) {
+    // the variant that reads S from global memory uses no column lists
+    plan.ucol.clear();
+    plan.uptr.assign(G + 1, 0);
+    plan.lcol.clear();
+    plan.lown.clear();
+    pcg_smem_bound(precision, G, R, rowptr, longest, maxnnz);
+    maxu = 0;
   }
   cfg.pcg_blocks = G;
   cfg.pcg_rows = R;
