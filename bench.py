@@ -128,9 +128,20 @@ def whole_job_value(work_per_step, steps, world, ms_max):
 
 # --------------------------------------------------------------------------- workload
 
-def make_workload(name, seed):
+# Full sizes of the scaled workloads (cameras, points, route length in m).
+_FULL_SIZE = {"driving": dict(n_cams=1000, n_pts=200_000, length_m=2000.0),
+              "city": dict(n_cams=5000, n_pts=1_000_000)}
+
+
+def make_workload(name, seed, scale=1.0):
+    """The seeded workload; scale < 1 shrinks cameras, points (and the
+    driving route) in proportion, for counter captures of a smaller case."""
     from paper_2510_15271_b300 import scenes
-    return scenes.make_scene(name, seed=seed)
+    kw = {}
+    if scale != 1.0 and name in _FULL_SIZE:
+        for k, v in _FULL_SIZE[name].items():
+            kw[k] = v * scale if isinstance(v, float) else max(2, int(round(v * scale)))
+    return scenes.make_scene(name, seed=seed, **kw)
 
 
 def camera_pairs(s):
@@ -186,7 +197,8 @@ def run_ours(args, rank, world, local_rank, workload=None):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    s = make_workload(workload or args.workload, replica_seed(args.seed, rank))
+    s = make_workload(workload or args.workload, replica_seed(args.seed, rank),
+                      args.scale if workload is None else 1.0)
     iters = s.lm_iters
     work = s.n_obs * iters  # obs*iters per step
 
@@ -1007,6 +1019,9 @@ def main():
     ap.add_argument("--no-driving", action="store_true",
                     help="skip the driving leg (run beside a city headline)")
     ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="shrink the headline workload's cameras and points (counter "
+                         "captures of a smaller case; the config line states the sizes run)")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-fp64", action="store_true")

@@ -368,6 +368,16 @@ ba_status ba_set_problem(ba_handle* h, int32_t n_cams, int32_t n_pts, int64_t n_
   }
   launch_scan_i32(cam_cnt, d.cam_ptr, C, scan_tmp, d.cam_ptr + C, s);
   launch_scan_i32(pt_cnt, d.pt_ptr, P, scan_tmp, d.pt_ptr + P, s);
+  {
+    int per_warp = 0;
+    d.nwpt = point_pass_warps(N, per_warp);
+    if (!keep(h, d.wpt, ((size_t)d.nwpt + 1) * sizeof(int32_t))) {
+      h->err = "ba_set_problem: out of device memory (point passes)";
+      free_problem(h);
+      return BA_ERR_OOM;
+    }
+    launch_warp_points(d.nwpt, per_warp, P, d.pt_ptr, d.wpt, s);
+  }
 
   // ---- sorts by (camera, point) and (point, camera)
   uint64_t* k0 = (uint64_t*)tmp.get(N * sizeof(uint64_t));

@@ -26,6 +26,15 @@ struct Intrinsics {
   double fx, fy, cx, cy;
 };
 
+// The intrinsics rounded to T once (per thread): the per-observation code then
+// converts nothing (a double-to-float conversion issues on the FP64 pipe).
+template <typename T>
+struct IntrinsicsT {
+  T fx, fy, cx, cy;
+  __device__ explicit IntrinsicsT(const Intrinsics& K)
+      : fx(T(K.fx)), fy(T(K.fy)), cx(T(K.cx)), cy(T(K.cy)) {}
+};
+
 // --------------------------------------------------------------------------- scalar ops
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
@@ -91,9 +100,8 @@ __device__ __forceinline__ void to_camera32(const float* __restrict__ cam,
 // --------------------------------------------------------------------------- residual
 // r = pi(K x_c) - p_obs with pi(x) = (fx x/z + cx, fy y/z + cy).  valid is
 // false (and r = 0) when the depth is below kZMin.
-template <typename T>
-__device__ __forceinline__ bool residual(const T xc[3], T u, T v, const Intrinsics& K, T& r0,
-                                         T& r1) {
+template <typename T, typename KI>
+__device__ __forceinline__ bool residual(const T xc[3], T u, T v, const KI& K, T& r0, T& r1) {
   const bool valid = xc[2] >= T(kZMin);
   if (!valid) {
     r0 = T(0);
@@ -132,9 +140,9 @@ __device__ __forceinline__ T huber_rho(T s, T delta) {
 //       = [[a, 0, c0, c0 y, a z - c0 x, -a y],
 //          [0, b, c1, c1 y - b z, -c1 x, b x]]
 // Point: J_p = dr/dx_c R.
-template <typename T>
-__device__ __forceinline__ void jacobians(const T xc[3], const T* __restrict__ R,
-                                          const Intrinsics& K, T Jc[2][6], T Jp[2][3]) {
+template <typename T, typename KI>
+__device__ __forceinline__ void jacobians(const T xc[3], const T* __restrict__ R, const KI& K,
+                                          T Jc[2][6], T Jp[2][3]) {
   const T x = xc[0], y = xc[1], z = xc[2];
   const T iz = T(1) / z;
   const T a = T(K.fx) * iz;
@@ -347,6 +355,35 @@ __device__ __forceinline__ bool spd6_inverse(const T* __restrict__ Ain, T* __res
 }
 
 // --------------------------------------------------------------------------- reductions
+// Per-thread running sums of the cost terms.  FP32 terms go into two floats
+// (hi + lo): Knuth's TwoSum of hi and the term is exact, its rounding error is
+// added into lo and the pair renormalised by Dekker's Fast2Sum (the terms are
+// non-negative, so |hi + term| >= |lo + error|).  About 2^-48 relative per
+// term against 2^-53 for an FP64 accumulator, at the FP32 rate (on this part
+// FP64 arithmetic, conversions included, bounds a per-observation FP64 sum).
+// FP64 terms go into a double.
+template <typename T>
+struct CostSum;
+template <>
+struct CostSum<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float t) {
+    const float s = __fadd_rn(hi, t);
+    const float bp = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(t, bp));
+    const float l = __fadd_rn(lo, e);
+    hi = __fadd_rn(s, l);
+    lo = __fsub_rn(l, __fsub_rn(hi, s));
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+template <>
+struct CostSum<double> {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double t) { v += t; }
+  __device__ __forceinline__ double value() const { return v; }
+};
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

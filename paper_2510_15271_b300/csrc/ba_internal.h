@@ -91,6 +91,10 @@ struct DevProblem {
   int32_t* po_k = nullptr;    // [N] index into the camera-sorted order
   int32_t* po_cam = nullptr;  // [N]
   void* po_uv = nullptr;      // [N][2] T
+  // per-point passes: warp w takes the points [wpt[w], wpt[w + 1]), about
+  // the same number of observations each
+  int32_t* wpt = nullptr;  // [nwpt + 1]
+  int nwpt = 0;
   // block pattern of S (BSR, 6x6 blocks, full rows)
   int32_t* s_rowptr = nullptr;  // [C+1]
   int32_t* s_col = nullptr;     // [nnzb]

@@ -390,27 +390,29 @@ template <typename T>
 __device__ void cost_pass(const BProb& p, bool trial, T delta, int mode) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const PV<T> view(p, trial);
+  const IntrinsicsT<T> Kt(p.K);
   const T* uv = (const T*)p.oc_uv;
   for (int i = warp; i < p.C; i += nw) {
     typename PV<T>::Cam cam;
     view.cam(i, cam);
-    double acc = 0.0, nv = 0.0;
+    CostSum<T> sum;
+    int nvalid = 0;
     for (int k = p.cam_ptr[i] + lane; k < p.cam_ptr[i + 1]; k += 32) {
       const int j = p.oc_pt[k];
       T xc[3];
       view.xc(cam, j, xc);
       T r0, r1;
-      if (!residual<T>(xc, uv[2 * (int64_t)k], uv[2 * (int64_t)k + 1], p.K, r0, r1)) continue;
+      if (!residual<T>(xc, uv[2 * (int64_t)k], uv[2 * (int64_t)k + 1], Kt, r0, r1)) continue;
       const T s = fma_rn(r0, r0, mul_rn(r1, r1));
       if (mode == 0) {
-        acc += 0.5 * (double)huber_rho<T>(s, delta);
+        sum.add(T(0.5) * huber_rho<T>(s, delta));  // the halving is exact in T
       } else {
-        acc += (double)s;
-        nv += 1.0;
+        sum.add(s);
+        ++nvalid;
       }
     }
-    acc = warp_sum(acc);
-    nv = warp_sum(nv);
+    const double acc = warp_sum(sum.value());
+    const double nv = warp_sum((double)nvalid);
     if (lane == 0) {
       p.cpart[i] = acc;
       if (mode == 1) p.cpart[p.C + i] = nv;
@@ -423,6 +425,7 @@ template <typename T>
 __device__ void lin_cams(const BProb& p, T delta) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const PV<T> view(p, false);
+  const IntrinsicsT<T> Kt(p.K);
   const T* uv = (const T*)p.oc_uv;
   for (int i = warp; i < p.C; i += nw) {
     T acc[27];
@@ -436,11 +439,11 @@ __device__ void lin_cams(const BProb& p, T delta) {
         T xc[3];
         view.xc(cam, j, xc);
         T r0, r1;
-        if (!residual<T>(xc, uv[2 * (int64_t)k], uv[2 * (int64_t)k + 1], p.K, r0, r1)) continue;
+        if (!residual<T>(xc, uv[2 * (int64_t)k], uv[2 * (int64_t)k + 1], Kt, r0, r1)) continue;
         const T s = fma_rn(r0, r0, mul_rn(r1, r1));
         const T w = huber_weight<T>(s, delta);
         T Jc[2][6], Jp[2][3];
-        jacobians<T>(xc, PV<T>::rot(cam), p.K, Jc, Jp);
+        jacobians<T>(xc, PV<T>::rot(cam), Kt, Jc, Jp);
         int u_idx = 0;
 #pragma unroll
         for (int a = 0; a < 6; ++a) {
@@ -478,6 +481,7 @@ __device__ void lin_cams(const BProb& p, T delta) {
 template <typename T>
 __device__ void lin_pts(const BProb& p, T delta) {
   const PV<T> view(p, false);
+  const IntrinsicsT<T> Kt(p.K);
   const T* uv = (const T*)p.po_uv;
   T* Wg = (T*)p.W;
   for (int j = threadIdx.x; j < p.P; j += blockDim.x) {
@@ -493,11 +497,11 @@ __device__ void lin_pts(const BProb& p, T delta) {
       T Wk[18];
 #pragma unroll
       for (int a = 0; a < 18; ++a) Wk[a] = T(0);
-      if (residual<T>(xc, uv[2 * (int64_t)q], uv[2 * (int64_t)q + 1], p.K, r0, r1)) {
+      if (residual<T>(xc, uv[2 * (int64_t)q], uv[2 * (int64_t)q + 1], Kt, r0, r1)) {
         const T s = fma_rn(r0, r0, mul_rn(r1, r1));
         const T w = huber_weight<T>(s, delta);
         T Jc[2][6], Jp[2][3];
-        jacobians<T>(xc, PV<T>::rot(cam), p.K, Jc, Jp);
+        jacobians<T>(xc, PV<T>::rot(cam), Kt, Jc, Jp);
         const T a0 = w * Jp[0][0], a1 = w * Jp[0][1], a2 = w * Jp[0][2];
         const T b0 = w * Jp[1][0], b1 = w * Jp[1][1], b2 = w * Jp[1][2];
         V[0] += a0 * Jp[0][0] + b0 * Jp[1][0];

@@ -698,6 +698,29 @@ void launch_stage_base(int nchunks, const int32_t* chunk_seg, const int32_t* seg
                                                                  sub_len, base);
 }
 
+__global__ void k_warp_points(int nwpt, int per_warp, int P, const int32_t* __restrict__ pt_ptr,
+                              int32_t* __restrict__ wpt) {
+  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w <= nwpt; w += gridDim.x * blockDim.x) {
+    if (w == nwpt) {
+      wpt[w] = P;
+      continue;
+    }
+    const int64_t target = (int64_t)w * per_warp;
+    int lo = 0, hi = P;  // first j in [0, P] with pt_ptr[j] >= target
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (pt_ptr[mid] < target) lo = mid + 1;
+      else hi = mid;
+    }
+    wpt[w] = lo;
+  }
+}
+
+void launch_warp_points(int nwpt, int per_warp, int P, const int32_t* pt_ptr, int32_t* wpt,
+                        cudaStream_t s) {
+  k_warp_points<<<grid_for((int64_t)nwpt + 1, 256), 256, 0, s>>>(nwpt, per_warp, P, pt_ptr, wpt);
+}
+
 void launch_pair_counts(const DevProblem& d, int32_t* cnt, int32_t* nch, cudaStream_t s) {
   k_pair_counts<<<grid_for(d.N, 256), 256, 0, s>>>(d.N, d.oc_cam, d.oc_pt, d.pt_ptr, d.po_cam, cnt);
   k_chunk_counts<<<grid_for(d.C, 256), 256, 0, s>>>(d.C, d.cam_ptr, nch);

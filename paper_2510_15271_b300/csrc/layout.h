@@ -53,6 +53,11 @@ void launch_stage_counts(int nchunks, const int32_t* chunk_seg, const int32_t* s
 // (split segments numbered in segment order) for the given length.
 void launch_stage_base(int nchunks, const int32_t* chunk_seg, const int32_t* seg_begin,
                        int sub_len, int32_t* base, cudaStream_t s);
+// Warps of the per-point passes: nwpt warps of about per_warp observations,
+// each starting at a point boundary (wpt[w] = first point whose observations
+// start at or after w * per_warp; wpt[nwpt] = P).
+void launch_warp_points(int nwpt, int per_warp, int P, const int32_t* pt_ptr, int32_t* wpt,
+                        cudaStream_t s);
 // d.s_mirror from the pattern (d.s_rowptr, d.s_col)
 void launch_mirror(const DevProblem& d, cudaStream_t s);
 void launch_gen_pairs(const DevProblem& d, const int32_t* chunk_ptr, const int32_t* pair_ptr,

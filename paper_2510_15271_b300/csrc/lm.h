@@ -128,6 +128,15 @@ inline void distinct_columns(const int32_t* col, int64_t n, int C, int tag,
   }
   for (size_t k = 0; k < out.size(); ++k) pos[out[k]] = (int32_t)k;
 }
+// Warps of the per-point passes (k_lin_pt, k_backsub): about 148 x 6 CTAs
+// of 8 warps on large problems, at least 64 observations a warp; the count
+// stays within the model-decrease partials (one per CTA of k_backsub).
+constexpr int kPointPassThreads = 256;
+inline int point_pass_warps(int64_t N, int& per_warp) {
+  const int64_t target = 148 * 6 * (kPointPassThreads / 32);
+  per_warp = (int)std::max<int64_t>(64, (N + target - 1) / target);
+  return (int)std::max<int64_t>(1, (N + per_warp - 1) / per_warp);
+}
 // Per-CTA column lists of the PCG kernel's shared-memory variant (host copy).
 struct PcgPlan {
   std::vector<int32_t> ucol;  // concatenated sorted column lists of the CTAs

@@ -22,6 +22,7 @@
 // (Sec. 4.3, 6.1); LM with Marquardt scaling and Nielsen's damping update
 // after Madsen, Nielsen & Tingleff 2004 (Sec. 3.2).
 #include <cuda_runtime.h>
+#include <limits.h>
 #include <math.h>
 #include <stdint.h>
 
@@ -191,6 +192,7 @@ __global__ void __launch_bounds__(NT) k_lin_cam(DevProblem d, T delta) {
   const int k0 = d.cam_ptr[i], k1 = d.cam_ptr[i + 1];
   const bool fixed = d.fixed[i] != 0;
   const View<T> view(d, false);
+  const IntrinsicsT<T> Kt(d.K);
   typename View<T>::Cam cam;
   view.cam(i, cam);
   T acc[27];
@@ -205,7 +207,7 @@ __global__ void __launch_bounds__(NT) k_lin_cam(DevProblem d, T delta) {
     T xc[3];
     view.xc(cam, j, xc);
     T r0, r1;
-    const bool valid = residual<T>(xc, u, v, d.K, r0, r1);
+    const bool valid = residual<T>(xc, u, v, Kt, r0, r1);
     T Wk[18];
 #pragma unroll
     for (int a = 0; a < 18; ++a) Wk[a] = T(0);
@@ -213,7 +215,7 @@ __global__ void __launch_bounds__(NT) k_lin_cam(DevProblem d, T delta) {
       const T s = fma_rn(r0, r0, mul_rn(r1, r1));
       const T w = huber_weight<T>(s, delta);
       T Jc[2][6], Jp[2][3];
-      jacobians<T>(xc, View<T>::rot(cam), d.K, Jc, Jp);
+      jacobians<T>(xc, View<T>::rot(cam), Kt, Jc, Jp);
       int u_idx = 0;
 #pragma unroll
       for (int a = 0; a < 6; ++a) {
@@ -242,47 +244,116 @@ __global__ void __launch_bounds__(NT) k_lin_cam(DevProblem d, T delta) {
   }
 }
 
+// Warp-cooperative pass over the point-major observations of whole points.
+// Warp w of the launch takes the points [d.wpt[w], d.wpt[w + 1]) (set-up cuts
+// the observations into ranges of about the same size at point boundaries),
+// 32 observations a round, lane l the l-th.  contrib(q, j, v) gives the NV
+// terms of observation q (of point j); a segmented shuffle scan sums them per
+// point in a fixed shape (a point that continues into the next round carries
+// its partial sum into that round's first lane), and fin(j, v) receives every
+// point's total in the lane holding the point's last observation.  Every
+// point has at least two observations (set-up refuses fewer), so the ends of
+// the points a round touches are distinct.
+template <typename T, int NV, typename Contrib, typename Fin>
+__device__ __forceinline__ void point_pass(const DevProblem& d, int w, Contrib contrib, Fin fin) {
+  constexpr unsigned kAll = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int jb = d.wpt[w], je = d.wpt[w + 1];
+  const int qe = d.pt_ptr[je];
+  int j0 = jb;  // point of the round's first observation
+  T carry[NV];
+#pragma unroll
+  for (int e = 0; e < NV; ++e) carry[e] = T(0);
+  for (int q0 = d.pt_ptr[jb]; q0 < qe; q0 += 32) {
+    // end of point j0 + lane; the round position where the next one starts
+    const int end_l = j0 + lane < je ? d.pt_ptr[j0 + lane + 1] : INT_MAX;
+    const int64_t pos = (int64_t)end_l - q0;  // >= 1
+    const unsigned starts = __reduce_or_sync(kAll, pos < 32 ? 1u << (int)pos : 0u);
+    const unsigned upto = lane == 31 ? kAll : ((2u << lane) - 1u);
+    const int j = j0 + __popc(starts & upto);
+    const int q = q0 + lane;
+    T v[NV];
+    if (q < qe) {
+      contrib(q, j, v);
+    } else {
+#pragma unroll
+      for (int e = 0; e < NV; ++e) v[e] = T(0);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int e = 0; e < NV; ++e) v[e] += carry[e];
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int js = __shfl_up_sync(kAll, j, o);
+      const bool take = lane >= o && js == j;
+#pragma unroll
+      for (int e = 0; e < NV; ++e) {
+        const T t = __shfl_up_sync(kAll, v[e], o);
+        if (take) v[e] += t;
+      }
+    }
+    const int jend = __shfl_sync(kAll, end_l, j - j0);  // j - j0 <= 31
+    if (q < qe && q + 1 == jend) fin(j, v);
+    const int j31 = __shfl_sync(kAll, j, 31);
+    const bool open = __shfl_sync(kAll, (q < qe && q + 1 != jend) ? 1 : 0, 31) != 0;
+#pragma unroll
+    for (int e = 0; e < NV; ++e) {
+      const T t = __shfl_sync(kAll, v[e], 31);
+      carry[e] = open ? t : T(0);
+    }
+    j0 = open ? j31 : j31 + 1;
+  }
+}
+
+// One warp per range of points (point_pass): V_j = sum w Jp^T Jp and
+// g_p,j = sum w Jp^T r over the point's observations.
 template <typename T>
-__global__ void k_lin_pt(DevProblem d, T delta) {
+__global__ void __launch_bounds__(kPointPassThreads) k_lin_pt(DevProblem d, T delta) {
   if (!d.lm->need_lin) return;
+  const int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  if (w >= d.nwpt) return;
   const T* uv = (const T*)d.po_uv;
   const View<T> view(d, false);
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.P; j += gridDim.x * blockDim.x) {
-    T V[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-    T g[3] = {T(0), T(0), T(0)};
-    for (int q = d.pt_ptr[j]; q < d.pt_ptr[j + 1]; ++q) {
-      const int c = d.po_cam[q];
-      T u, v;
-      load_uv<T>(uv, q, u, v);
-      typename View<T>::Cam cam;
-      view.cam(c, cam);
-      T xc[3];
-      view.xc(cam, j, xc);
-      T r0, r1;
-      if (!residual<T>(xc, u, v, d.K, r0, r1)) continue;
-      const T s = fma_rn(r0, r0, mul_rn(r1, r1));
-      const T w = huber_weight<T>(s, delta);
-      T Jc[2][6], Jp[2][3];
-      jacobians<T>(xc, View<T>::rot(cam), d.K, Jc, Jp);
-      const T a0 = w * Jp[0][0], a1 = w * Jp[0][1], a2 = w * Jp[0][2];
-      const T b0 = w * Jp[1][0], b1 = w * Jp[1][1], b2 = w * Jp[1][2];
-      V[0] += a0 * Jp[0][0] + b0 * Jp[1][0];
-      V[1] += a0 * Jp[0][1] + b0 * Jp[1][1];
-      V[2] += a0 * Jp[0][2] + b0 * Jp[1][2];
-      V[3] += a1 * Jp[0][1] + b1 * Jp[1][1];
-      V[4] += a1 * Jp[0][2] + b1 * Jp[1][2];
-      V[5] += a2 * Jp[0][2] + b2 * Jp[1][2];
-      g[0] += a0 * r0 + b0 * r1;
-      g[1] += a1 * r0 + b1 * r1;
-      g[2] += a2 * r0 + b2 * r1;
-    }
-    T* Vo = (T*)d.V + 6 * (int64_t)j;
+  const IntrinsicsT<T> Kt(d.K);
+  point_pass<T, 9>(
+      d, w,
+      [&](int q, int j, T(&v)[9]) {
 #pragma unroll
-    for (int a = 0; a < 6; ++a) Vo[a] = V[a];
-    T* go = (T*)d.gp + 3 * (int64_t)j;
+        for (int e = 0; e < 9; ++e) v[e] = T(0);
+        const int c = d.po_cam[q];
+        T u, vv;
+        load_uv<T>(uv, q, u, vv);
+        typename View<T>::Cam cam;
+        view.cam(c, cam);
+        T xc[3];
+        view.xc(cam, j, xc);
+        T r0, r1;
+        if (!residual<T>(xc, u, vv, Kt, r0, r1)) return;
+        const T s = fma_rn(r0, r0, mul_rn(r1, r1));
+        const T wt = huber_weight<T>(s, delta);
+        T Jc[2][6], Jp[2][3];
+        jacobians<T>(xc, View<T>::rot(cam), Kt, Jc, Jp);
+        const T a0 = wt * Jp[0][0], a1 = wt * Jp[0][1], a2 = wt * Jp[0][2];
+        const T b0 = wt * Jp[1][0], b1 = wt * Jp[1][1], b2 = wt * Jp[1][2];
+        v[0] = a0 * Jp[0][0] + b0 * Jp[1][0];
+        v[1] = a0 * Jp[0][1] + b0 * Jp[1][1];
+        v[2] = a0 * Jp[0][2] + b0 * Jp[1][2];
+        v[3] = a1 * Jp[0][1] + b1 * Jp[1][1];
+        v[4] = a1 * Jp[0][2] + b1 * Jp[1][2];
+        v[5] = a2 * Jp[0][2] + b2 * Jp[1][2];
+        v[6] = a0 * r0 + b0 * r1;
+        v[7] = a1 * r0 + b1 * r1;
+        v[8] = a2 * r0 + b2 * r1;
+      },
+      [&](int j, const T(&v)[9]) {
+        T* Vo = (T*)d.V + 6 * (int64_t)j;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) go[a] = g[a];
-  }
+        for (int a = 0; a < 6; ++a) Vo[a] = v[a];
+        T* go = (T*)d.gp + 3 * (int64_t)j;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) go[a] = v[6 + a];
+      });
 }
 
 template <typename T>
@@ -508,57 +579,75 @@ __global__ void __launch_bounds__(NT, 2) k_schur(DevProblem d, int colcap) {
 
 // --------------------------------------------------------------------------- back-substitution
 
+// One warp per range of points (point_pass): the terms W_k^T dc_i(k) of a
+// point's observations summed per point (parked in dp), then, one lane per
+// point over the warp's points, the point's step, trial point and its part of
+// the model decrease (FP64 work at full lane width); one partial sum per CTA.
 template <typename T>
-__global__ void k_backsub(DevProblem d) {
-  __shared__ double red[32];
+__global__ void __launch_bounds__(kPointPassThreads) k_backsub(DevProblem d) {
+  __shared__ double red[kPointPassThreads / 32];
   const double mu = fmax(d.lm->mu, d.mu_min);  // damping of the linear system
   const T* Wg = (const T*)d.W;
   const T* dc = (const T*)d.dc;
+  T* dpo = (T*)d.dp;
   double part = 0.0;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.P; j += gridDim.x * blockDim.x) {
-    const T* gp = (const T*)d.gp + 3 * (int64_t)j;
-    T rhs0 = -gp[0], rhs1 = -gp[1], rhs2 = -gp[2];
-    for (int q = d.pt_ptr[j]; q < d.pt_ptr[j + 1]; ++q) {
-      const int c = d.po_cam[q];
-      if (d.fixed[c]) continue;
-      T Wk[18];
-      load_w<T>(Wg, d.po_k[q], Wk);
-      const T* x = dc + 6 * c;
+  const int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  if (w < d.nwpt) {
+    point_pass<T, 3>(
+        d, w,
+        [&](int q, int, T(&v)[3]) {
+          v[0] = v[1] = v[2] = T(0);
+          const int c = d.po_cam[q];
+          if (d.fixed[c]) return;
+          T Wk[18];
+          load_w<T>(Wg, d.po_k[q], Wk);
+          const T* x = dc + 6 * c;
 #pragma unroll
-      for (int a = 0; a < 6; ++a) {
-        const T xa = x[a];
-        rhs0 -= Wk[3 * a] * xa;
-        rhs1 -= Wk[3 * a + 1] * xa;
-        rhs2 -= Wk[3 * a + 2] * xa;
-      }
+          for (int a = 0; a < 6; ++a) {
+            const T xa = x[a];
+            v[0] += Wk[3 * a] * xa;
+            v[1] += Wk[3 * a + 1] * xa;
+            v[2] += Wk[3 * a + 2] * xa;
+          }
+        },
+        [&](int j, const T(&v)[3]) {
+          T* o = dpo + 3 * (int64_t)j;
+          o[0] = v[0];
+          o[1] = v[1];
+          o[2] = v[2];
+        });
+    __syncwarp();  // the warp's sums are visible to all its lanes
+    for (int j = d.wpt[w] + (int)(threadIdx.x & 31); j < d.wpt[w + 1]; j += 32) {
+      T* dp = dpo + 3 * (int64_t)j;
+      const T* gp = (const T*)d.gp + 3 * (int64_t)j;
+      const double r0 = (double)(-gp[0] - dp[0]), r1 = (double)(-gp[1] - dp[1]),
+                   r2 = (double)(-gp[2] - dp[2]);
+      const double* vi = d.Vinv + 6 * (int64_t)j;
+      const double p0 = vi[0] * r0 + vi[1] * r1 + vi[2] * r2;
+      const double p1 = vi[1] * r0 + vi[3] * r1 + vi[4] * r2;
+      const double p2 = vi[2] * r0 + vi[4] * r1 + vi[5] * r2;
+      dp[0] = (T)p0;
+      dp[1] = (T)p1;
+      dp[2] = (T)p2;
+      const double n0 = d.X[3 * j] + p0, n1 = d.X[3 * j + 1] + p1, n2 = d.X[3 * j + 2] + p2;
+      d.X2[3 * j] = n0;
+      d.X2[3 * j + 1] = n1;
+      d.X2[3 * j + 2] = n2;
+      if (d.X32b) write_pt32(n0, n1, n2, d.X32b + kPt32 * (int64_t)j);
+      // model decrease, point part: h (mu D h - g)
+      const T* V = (const T*)d.V + 6 * (int64_t)j;
+      const double D0 = fmax((double)V[0], kDiagMin), D1 = fmax((double)V[3], kDiagMin),
+                   D2 = fmax((double)V[5], kDiagMin);
+      part += p0 * (mu * D0 * p0 - (double)gp[0]) + p1 * (mu * D1 * p1 - (double)gp[1]) +
+              p2 * (mu * D2 * p2 - (double)gp[2]);
     }
-    const double* vi = d.Vinv + 6 * (int64_t)j;
-    const double r0 = rhs0, r1 = rhs1, r2 = rhs2;
-    const double p0 = vi[0] * r0 + vi[1] * r1 + vi[2] * r2;
-    const double p1 = vi[1] * r0 + vi[3] * r1 + vi[4] * r2;
-    const double p2 = vi[2] * r0 + vi[4] * r1 + vi[5] * r2;
-    T* dp = (T*)d.dp + 3 * (int64_t)j;
-    dp[0] = (T)p0;
-    dp[1] = (T)p1;
-    dp[2] = (T)p2;
-    const double n0 = d.X[3 * j] + p0, n1 = d.X[3 * j + 1] + p1, n2 = d.X[3 * j + 2] + p2;
-    d.X2[3 * j] = n0;
-    d.X2[3 * j + 1] = n1;
-    d.X2[3 * j + 2] = n2;
-    if (d.X32b) write_pt32(n0, n1, n2, d.X32b + kPt32 * (int64_t)j);
-    // model decrease, point part: h (mu D h - g)
-    const T* V = (const T*)d.V + 6 * (int64_t)j;
-    const double D0 = fmax((double)V[0], kDiagMin), D1 = fmax((double)V[3], kDiagMin),
-                 D2 = fmax((double)V[5], kDiagMin);
-    part += p0 * (mu * D0 * p0 - (double)gp[0]) + p1 * (mu * D1 * p1 - (double)gp[1]) +
-            p2 * (mu * D2 * p2 - (double)gp[2]);
   }
   part = warp_sum(part);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
   __syncthreads();
   if (threadIdx.x == 0) {
     double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
     d.part[kPartDl + blockIdx.x] = s;
   }
 }
@@ -615,7 +704,9 @@ __global__ void k_cost(DevProblem d, int trial, T delta, int mode) {
   __shared__ double red[64];
   const T* uv = (const T*)d.oc_uv;
   const View<T> view(d, trial != 0);
-  double acc = 0.0, nv = 0.0;
+  const IntrinsicsT<T> Kt(d.K);
+  CostSum<T> sum;
+  int nvalid = 0;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < d.N;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int c = d.oc_cam[k], j = d.oc_pt[k];
@@ -626,17 +717,17 @@ __global__ void k_cost(DevProblem d, int trial, T delta, int mode) {
     T xc[3];
     view.xc(cam, j, xc);
     T r0, r1;
-    if (!residual<T>(xc, u, v, d.K, r0, r1)) continue;
+    if (!residual<T>(xc, u, v, Kt, r0, r1)) continue;
     const T s = fma_rn(r0, r0, mul_rn(r1, r1));
     if (mode == 0) {
-      acc += 0.5 * (double)huber_rho<T>(s, delta);
+      sum.add(T(0.5) * huber_rho<T>(s, delta));  // the halving is exact in T
     } else {
-      acc += (double)s;
-      nv += 1.0;
+      sum.add(s);
+      ++nvalid;
     }
   }
-  acc = warp_sum(acc);
-  nv = warp_sum(nv);
+  double acc = warp_sum(sum.value());
+  double nv = warp_sum((double)nvalid);
   if ((threadIdx.x & 31) == 0) {
     red[threadIdx.x >> 5] = acc;
     red[32 + (threadIdx.x >> 5)] = nv;
@@ -778,7 +869,11 @@ static unsigned grid_cap(int64_t n, int threads, int cap) {
 }
 
 int cost_blocks(const DevProblem& d) { return (int)grid_cap(d.N, 256, kCostParts / 2); }
-int backsub_blocks(const DevProblem& d) { return (int)grid_cap(d.P, 256, kDlParts / 2); }
+static_assert(148 * 6 <= kDlParts / 2, "one model-decrease partial per CTA of k_backsub");
+int backsub_blocks(const DevProblem& d) {
+  return (d.nwpt + kPointPassThreads / 32 - 1) / (kPointPassThreads / 32);
+}
+static unsigned point_blocks(const DevProblem& d) { return (unsigned)backsub_blocks(d); }
 int retract_blocks(const DevProblem& d) { return (int)grid_cap(d.C, 128, kDlParts / 2); }
 
 size_t schur_smem(int precision, int colcap, int max_rs) {
@@ -819,7 +914,7 @@ static void lm_iteration_t(const DevProblem& d, const SolveConfig& cfg, cudaStre
   k_lin_cam<T, 256><<<d.C, 256, 0, s>>>(d, delta);
   launch_prior_lin(d, s);  // pose priors into U and g_c (none when off)
   mark(cfg, kKLinCam, s);
-  k_lin_pt<T><<<gp, 256, 0, s>>>(d, delta);
+  k_lin_pt<T><<<point_blocks(d), kPointPassThreads, 0, s>>>(d, delta);
   mark(cfg, kKLinPt, s);
   k_damp_pt<T><<<gp, 256, 0, s>>>(d);
   mark(cfg, kKDampPt, s);
@@ -829,7 +924,7 @@ static void lm_iteration_t(const DevProblem& d, const SolveConfig& cfg, cudaStre
   mark(cfg, kKSchur, s);
   launch_linear_solve(d, cfg, s);
   mark(cfg, kKSolve, s);
-  k_backsub<T><<<backsub_blocks(d), 256, 0, s>>>(d);
+  k_backsub<T><<<backsub_blocks(d), kPointPassThreads, 0, s>>>(d);
   mark(cfg, kKBacksub, s);
   k_retract<T><<<retract_blocks(d), 128, 0, s>>>(d);
   mark(cfg, kKRetract, s);
@@ -879,7 +974,7 @@ static void steps_t(const DevProblem& d, const SolveConfig& cfg, int step, int a
   switch (step) {
     case 0:  // linearisation (a new state only)
       k_lin_cam<T, 256><<<d.C, 256, 0, s>>>(d, delta);
-      k_lin_pt<T><<<gp, 256, 0, s>>>(d, delta);
+      k_lin_pt<T><<<point_blocks(d), kPointPassThreads, 0, s>>>(d, delta);
       break;
     case 1:
       k_damp_pt<T><<<gp, 256, 0, s>>>(d);
@@ -889,7 +984,7 @@ static void steps_t(const DevProblem& d, const SolveConfig& cfg, int step, int a
           d, cfg.schur_colcap);
       break;
     case 3:
-      k_backsub<T><<<backsub_blocks(d), 256, 0, s>>>(d);
+      k_backsub<T><<<backsub_blocks(d), kPointPassThreads, 0, s>>>(d);
       break;
     case 4:  // arg: trial (bit 0), mode (bit 1)
       k_cost<T><<<cost_blocks(d), 256, 0, s>>>(d, arg & 1, delta, (arg >> 1) & 1);
