@@ -71,6 +71,47 @@ __device__ __forceinline__ void load_w<double>(const double* __restrict__ W, int
   }
 }
 
+// Rows 3h .. 3h+2 of the W block of one observation (9 values, row-major).
+template <typename T>
+__device__ __forceinline__ void load_w_half(const T* __restrict__ W, int64_t k, int h, T w[9]);
+template <>
+__device__ __forceinline__ void load_w_half<float>(const float* __restrict__ W, int64_t k, int h,
+                                                   float w[9]) {
+  // h = 0: floats 0..11 (0..8 used); h = 1: floats 8..19 (9..17 used); the
+  // record is padded to 20 floats
+  const float4* p = reinterpret_cast<const float4*>(W + k * kWStrideF32) + 2 * h;
+  const float4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
+  w[0] = h ? a.y : a.x;
+  w[1] = h ? a.z : a.y;
+  w[2] = h ? a.w : a.z;
+  w[3] = h ? b.x : a.w;
+  w[4] = h ? b.y : b.x;
+  w[5] = h ? b.z : b.y;
+  w[6] = h ? b.w : b.z;
+  w[7] = h ? c.x : b.w;
+  w[8] = h ? c.y : c.x;
+}
+template <>
+__device__ __forceinline__ void load_w_half<double>(const double* __restrict__ W, int64_t k, int h,
+                                                    double w[9]) {
+  // h = 0: pairs at 0, 2, 4, 6 and the single 8; h = 1: the single 9 and
+  // pairs at 10, 12, 14, 16
+  const double* r = W + k * kWStrideF64;
+  const double2* p = reinterpret_cast<const double2*>(r + (h ? 10 : 0));
+  const double one = __ldg(r + (h ? 9 : 8));
+  double v[8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const double2 t = __ldg(p + i);
+    v[2 * i] = t.x;
+    v[2 * i + 1] = t.y;
+  }
+  w[0] = h ? one : v[0];
+#pragma unroll
+  for (int i = 1; i < 8; ++i) w[i] = h ? v[i - 1] : v[i];
+  w[8] = h ? v[7] : one;
+}
+
 template <typename T>
 __device__ __forceinline__ void store_w(T* __restrict__ W, int64_t k, const T w[18]);
 template <>
@@ -464,60 +505,84 @@ __global__ void __launch_bounds__(NT, 2) k_schur(DevProblem d, int colcap) {
           }
         }
         __syncthreads();
-        // each thread accumulates whole sub-segments (<= sub_len pairs)
+        // each thread pair accumulates whole sub-segments (<= sub_len pairs)
         const int sg0 = d.chunk_seg[ch], sg1 = d.chunk_seg[ch + 1];
         const int u0 = d.seg_sub[sg0], u1 = d.seg_sub[sg1];
-        // a thread pair per sub-segment: thread h = tid & 1 owns output rows
-        // 3h .. 3h+2; both read the same W gathers (one request)
+        // thread h = tid & 1 of a pair owns output columns 3h .. 3h+2 (all six
+        // rows): it gathers only rows 3h .. 3h+2 of the partner's W and reads
+        // the whole Y_k1 from shared memory
         const int h = threadIdx.x & 1;
-        for (int u = u0 + (int)(threadIdx.x >> 1); u < u1; u += NT / 2) {
-          const int slot = d.sub_slot[u];
-          if (slot < lo || slot >= hi) continue;
-          const int pb = d.sub_begin[u], pe = d.sub_begin[u + 1];
-          T sum[18];
+        int u = u0 + (int)(threadIdx.x >> 1);
+        // the sub-segment's metadata, loaded one sub-segment ahead
+        int slot = 0, pb = 0, pe = 0, rs = 0;
+        if (u < u1) {
+          slot = d.sub_slot[u];
+          pb = d.sub_begin[u];
+          pe = d.sub_begin[u + 1];
+          rs = d.sub_rs[u];
+        }
+        for (; u < u1; u += NT / 2) {
+          const int un = u + NT / 2;
+          int nslot = 0, npb = 0, npe = 0, nrs = 0;
+          if (un < u1) {
+            nslot = d.sub_slot[un];
+            npb = d.sub_begin[un];
+            npe = d.sub_begin[un + 1];
+            nrs = d.sub_rs[un];
+          }
+          if (slot >= lo && slot < hi) {
+            T sum[18];  // sum[3a + c]: output row a, column 3h + c
 #pragma unroll
-          for (int e = 0; e < 18; ++e) sum[e] = T(0);
-          // groups of up to 4 pairs: the indices are loaded first, so the W
-          // gathers of the (unrolled) group can be issued together
-          for (int p0 = pb; p0 < pe; p0 += 4) {
-            // all four gathers are issued before any arithmetic: past the end
-            // of the sub-segment the last pair is re-read and weighted by 0
-            int tq[4], kq[4];
-            T wq[4];
+            for (int e = 0; e < 18; ++e) sum[e] = T(0);
+            // groups of kG pairs: the indices are loaded first, so the W
+            // gathers of the (unrolled) group are issued together; past the
+            // end of the sub-segment the last pair is re-read and weighted by 0
+            constexpr int kG = sizeof(T) == 4 ? 8 : 4;
+            for (int p0 = pb; p0 < pe; p0 += kG) {
+              int tq[kG], kq[kG];
+              T wq[kG];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const int p = min(p0 + q, pe - 1);
-              tq[q] = (int)d.pair_t[p];
-              kq[q] = d.pair_k2[p];
-              wq[q] = (p0 + q < pe) ? T(1) : T(0);
-            }
-            T W2[4][18];
+              for (int q = 0; q < kG; ++q) {
+                const int pp = min(p0 + q, pe - 1);
+                tq[q] = (int)d.pair_t[pp];
+                kq[q] = d.pair_k2[pp];
+                wq[q] = (p0 + q < pe) ? T(1) : T(0);
+              }
+              T W2[kG][9];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) load_w<T>(Wg, kq[q], W2[q]);
+              for (int q = 0; q < kG; ++q) load_w_half<T>(Wg, kq[q], h, W2[q]);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const T* Y = Ys + 18 * tq[q] + 9 * h;
+              for (int q = 0; q < kG; ++q) {
+                const T* Y = Ys + 18 * tq[q];
 #pragma unroll
-              for (int a = 0; a < 3; ++a) {
-                const T y0 = wq[q] * Y[3 * a], y1 = wq[q] * Y[3 * a + 1], y2 = wq[q] * Y[3 * a + 2];
+                for (int a = 0; a < 6; ++a) {
+                  const T y0 = wq[q] * Y[3 * a], y1 = wq[q] * Y[3 * a + 1], y2 = wq[q] * Y[3 * a + 2];
 #pragma unroll
-                for (int bb = 0; bb < 6; ++bb)
-                  sum[6 * a + bb] +=
-                      y0 * W2[q][3 * bb] + y1 * W2[q][3 * bb + 1] + y2 * W2[q][3 * bb + 2];
+                  for (int c = 0; c < 3; ++c)
+                    sum[3 * a + c] +=
+                        y0 * W2[q][3 * c] + y1 * W2[q][3 * c + 1] + y2 * W2[q][3 * c + 2];
+                }
               }
             }
-          }
-          const int rs = d.sub_rs[u];
-          if (rs < 0) {
-            // the segment's only sub-segment: straight into its block
-            T* A = acc + 36 * (slot - lo) + 18 * h;
+            if (rs < 0) {
+              // the segment's only sub-segment: straight into its block
+              T* A = acc + 36 * (slot - lo) + 3 * h;
 #pragma unroll
-            for (int e = 0; e < 18; ++e) A[e] += sum[e];
-          } else {
-            T* res = Rs + (size_t)rs * kResStride + 18 * h;
+              for (int a = 0; a < 6; ++a)
 #pragma unroll
-            for (int e = 0; e < 18; ++e) res[e] = sum[e];
+                for (int c = 0; c < 3; ++c) A[6 * a + c] += sum[3 * a + c];
+            } else {
+              T* res = Rs + (size_t)rs * kResStride + 3 * h;
+#pragma unroll
+              for (int a = 0; a < 6; ++a)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) res[6 * a + c] = sum[3 * a + c];
+            }
           }
+          slot = nslot;
+          pb = npb;
+          pe = npe;
+          rs = nrs;
         }
         __syncthreads();
         // the split segments: their sub-segments added in order
@@ -707,23 +772,41 @@ __global__ void k_cost(DevProblem d, int trial, T delta, int mode) {
   const IntrinsicsT<T> Kt(d.K);
   CostSum<T> sum;
   int nvalid = 0;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < d.N;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const int c = d.oc_cam[k], j = d.oc_pt[k];
-    T u, v;
-    load_uv<T>(uv, k, u, v);
-    typename View<T>::Cam cam;
-    view.cam(c, cam);
-    T xc[3];
-    view.xc(cam, j, xc);
-    T r0, r1;
-    if (!residual<T>(xc, u, v, Kt, r0, r1)) continue;
-    const T s = fma_rn(r0, r0, mul_rn(r1, r1));
-    if (mode == 0) {
-      sum.add(T(0.5) * huber_rho<T>(s, delta));  // the halving is exact in T
-    } else {
-      sum.add(s);
-      ++nvalid;
+  // the thread's observations k0, k0 + stride, ... in that order, four at a
+  // time: their indices, then their camera and point gathers, are issued
+  // together before any arithmetic (the gathers are what the pass waits on)
+  constexpr int kU = 4;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k0 < d.N; k0 += kU * stride) {
+    int cq[kU], jq[kU];
+    T uq[kU], vq[kU];
+#pragma unroll
+    for (int q = 0; q < kU; ++q) {
+      const int64_t k = k0 + q * stride;
+      const int64_t kk = k < d.N ? k : k0;
+      cq[q] = d.oc_cam[kk];
+      jq[q] = d.oc_pt[kk];
+      load_uv<T>(uv, kk, uq[q], vq[q]);
+    }
+    T xq[kU][3];
+#pragma unroll
+    for (int q = 0; q < kU; ++q) {
+      typename View<T>::Cam cam;
+      view.cam(cq[q], cam);
+      view.xc(cam, jq[q], xq[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < kU; ++q) {
+      if (k0 + q * stride >= d.N) break;
+      T r0, r1;
+      if (!residual<T>(xq[q], uq[q], vq[q], Kt, r0, r1)) continue;
+      const T s = fma_rn(r0, r0, mul_rn(r1, r1));
+      if (mode == 0) {
+        sum.add(T(0.5) * huber_rho<T>(s, delta));  // the halving is exact in T
+      } else {
+        sum.add(s);
+        ++nvalid;
+      }
     }
   }
   double acc = warp_sum(sum.value());
