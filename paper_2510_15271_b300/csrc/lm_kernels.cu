@@ -192,6 +192,15 @@ struct View<double> {
   __device__ __forceinline__ void xc(const Cam& c, int j, double out[3]) const {
     to_camera64(c.R, c.t, X[3 * (int64_t)j], X[3 * (int64_t)j + 1], X[3 * (int64_t)j + 2], out);
   }
+  // the same in two steps: the point's load, then the transform
+  static constexpr int kPtN = 3;
+  __device__ __forceinline__ void pt(int j, double out[kPtN]) const {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) out[a] = X[3 * (int64_t)j + a];
+  }
+  __device__ __forceinline__ static void xc_pt(const Cam& c, const double P[kPtN], double out[3]) {
+    to_camera64(c.R, c.t, P[0], P[1], P[2], out);
+  }
   __device__ __forceinline__ static const double* rot(const Cam& c) { return c.R; }
 };
 
@@ -220,6 +229,21 @@ struct View<float> {
     const float pt[6] = {a.x, a.y, b.x, b.y, e.x, e.y};
     to_camera32(c.v, pt, out);
   }
+  // the same in two steps: the point's load, then the transform
+  static constexpr int kPtN = kPt32;
+  __device__ __forceinline__ void pt(int j, float out[kPtN]) const {
+    const float2* p = reinterpret_cast<const float2*>(X + kPt32 * (int64_t)j);
+    const float2 a = __ldg(p), b = __ldg(p + 1), e = __ldg(p + 2);
+    out[0] = a.x;
+    out[1] = a.y;
+    out[2] = b.x;
+    out[3] = b.y;
+    out[4] = e.x;
+    out[5] = e.y;
+  }
+  __device__ __forceinline__ static void xc_pt(const Cam& c, const float P[kPtN], float out[3]) {
+    to_camera32(c.v, P, out);
+  }
   __device__ __forceinline__ static const float* rot(const Cam& c) { return c.v; }
 };
 
@@ -241,12 +265,27 @@ __global__ void __launch_bounds__(NT) k_lin_cam(DevProblem d, T delta) {
   for (int a = 0; a < 27; ++a) acc[a] = T(0);
   const T* uv = (const T*)d.oc_uv;
   T* Wout = (T*)d.W;
+  // software pipeline over the camera's observations: the point index two
+  // rounds ahead and the point one round ahead are loaded before the current
+  // observation is evaluated (the point gather is what the pass waits on)
+  constexpr int kPN = View<T>::kPtN;
+  T Pn[kPN];
+  int jnn = 0;
+  {
+    const int k = k0 + threadIdx.x;
+    if (k < k1) view.pt(d.oc_pt[k], Pn);
+    if (k + NT < k1) jnn = d.oc_pt[k + NT];
+  }
   for (int k = k0 + threadIdx.x; k < k1; k += NT) {
-    const int j = d.oc_pt[k];
+    T Pc[kPN];
+#pragma unroll
+    for (int a = 0; a < kPN; ++a) Pc[a] = Pn[a];
+    if (k + NT < k1) view.pt(jnn, Pn);
+    if (k + 2 * NT < k1) jnn = d.oc_pt[k + 2 * NT];
     T u, v;
     load_uv<T>(uv, k, u, v);
     T xc[3];
-    view.xc(cam, j, xc);
+    View<T>::xc_pt(cam, Pc, xc);
     T r0, r1;
     const bool valid = residual<T>(xc, u, v, Kt, r0, r1);
     T Wk[18];

@@ -397,6 +397,66 @@ __device__ __forceinline__ void grid_total(const double* slot, double* bcast, do
   consumers_sync();
 }
 
+// cta_sum, grid_sync and grid_total in one pass with one closing consumer
+// barrier: each warp's shuffle sum, then warp 0 alone: lane 0 sums the warps
+// in order into this CTA's slot, arrives (release) and waits (acquire,
+// bounded) for every CTA; the warp sums all CTAs' slots (lane-strided, then a
+// shuffle tree: the order of grid_total) and lane 0 runs fin(totals), whose
+// shared writes the consumers read after the barrier.  out[] holds the totals
+// in every consumer on return.  Bit-identical to the three-call sequence.
+template <int NV, typename Fin>
+__device__ __forceinline__ void grid_reduce(double (&v)[NV], double* red, double* slot,
+                                            double* bcast, unsigned* bar, unsigned& epoch,
+                                            int* err, double (&out)[NV], Fin fin) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) red[w * NV + k] = v[k];
+  consumers_sync();
+  if (w == 0) {
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        double s = 0.0;
+        for (int ww = 0; ww < kSWarps; ++ww) s += red[ww * NV + k];
+        slot[blockIdx.x * NV + k] = s;
+      }
+      const unsigned target = (++epoch) * gridDim.x;
+      asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(bar), "r"(1u) : "memory");
+      const unsigned long long t0 = s_now();
+      for (unsigned n = 1; (int)(ld_acq(bar) - target) < 0; ++n) {
+        if ((n & 63u) == 0) {
+          if (ld_vol(err) != 0) break;
+          if (s_now() - t0 > kSWaitLimitNs) {
+            atomicOr(err, kErrBarrierTimeout);
+            break;
+          }
+        }
+      }
+      asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    }
+    __syncwarp();
+    double acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) acc[k] += __ldcg(slot + b * NV + k);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = warp_sum(acc[k]);
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) bcast[k] = acc[k];
+      fin(acc);
+    }
+  }
+  consumers_sync();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) out[k] = bcast[k];
+}
+
 struct StreamArgs {
   double tol;
   int max_iters;
@@ -546,19 +606,16 @@ __global__ void __launch_bounds__(kSThreads, 1) k_pcg_stream(DevProblem d, Strea
     }
     double l2[2] = {0.0, 0.0};
     precondition(rr, zr, l2[0], l2[1]);
-    cta_sum<2>(l2, red, partB);
-    grid_sync(d.barrier, epoch, err);
     double tot[2];
-    grid_total<2>(partB, bcast, tot);
+    grid_reduce<2>(l2, red, partB, bcast, d.barrier, epoch, err, tot, [&](const double(&t)[2]) {
+      const double bn = sqrt(t[1]);
+      s_bt = T(0);
+      s_go = (max_iters > 0 && t[1] > (tol * bn) * (tol * bn) && !bad()) ? 1 : 0;
+    });
     double rz = tot[0], r2 = tot[1];
     const double bnorm = sqrt(r2);
     const double thr2 = (tol * bnorm) * (tol * bnorm);
     int k = 0;
-    if (tid == 0) {
-      s_bt = T(0);
-      s_go = (max_iters > 0 && r2 > thr2 && !bad()) ? 1 : 0;
-    }
-    consumers_sync();
     while (s_go) {
       const T bt = s_bt;
       T* pn = pb[k & 1];
@@ -589,15 +646,12 @@ __global__ void __launch_bounds__(kSThreads, 1) k_pcg_stream(DevProblem d, Strea
           pq[0] += (double)pr[j] * (double)qr[j];
         }
       }
-      cta_sum<1>(pq, red, partA);
-      grid_sync(d.barrier, epoch, err);
       double pqt[1];
-      grid_total<1>(partA, bcast, pqt);
-      if (tid == 0) {
-        s_go = (pqt[0] > 0.0 && !bad()) ? 1 : 0;  // S positive definite along p
-        s_al = (T)(rz / pqt[0]);
-      }
-      consumers_sync();
+      grid_reduce<1>(pq, red, partA, bcast, d.barrier, epoch, err, pqt,
+                     [&](const double(&t)[1]) {
+                       s_go = (t[0] > 0.0 && !bad()) ? 1 : 0;  // S positive definite along p
+                       s_al = (T)(rz / t[0]);
+                     });
       if (!s_go) break;
       const T al = s_al;
 #pragma unroll
@@ -607,18 +661,15 @@ __global__ void __launch_bounds__(kSThreads, 1) k_pcg_stream(DevProblem d, Strea
       }
       double lz[2] = {0.0, 0.0};
       precondition(rr, zr, lz[0], lz[1]);
-      cta_sum<2>(lz, red, partB);
-      grid_sync(d.barrier, epoch, err);
-      const bool e_now = tid == 0 ? bad() : false;
-      grid_total<2>(partB, bcast, tot);
       ++k;
-      if (tid == 0) {
-        s_bt = (T)(tot[0] / rz);
-        rz = tot[0];
-        r2 = tot[1];
-        s_go = (k < max_iters && r2 > thr2 && !e_now) ? 1 : 0;
-      }
-      consumers_sync();
+      grid_reduce<2>(lz, red, partB, bcast, d.barrier, epoch, err, tot,
+                     [&](const double(&t)[2]) {
+                       const bool e_now = bad();
+                       s_bt = (T)(t[0] / rz);
+                       rz = t[0];
+                       r2 = t[1];
+                       s_go = (k < max_iters && r2 > thr2 && !e_now) ? 1 : 0;
+                     });
     }
 #pragma unroll
     for (int j = 0; j < ND; ++j) {
