@@ -463,7 +463,10 @@ def measured_traffic(s, name):
     for line in text.splitlines():
         cells = [c.strip() for c in line.strip().strip("|").split("|")]
         if len(cells) > 4 and cells[0] in _PROFILE_NAMES[name]:
-            return int(cells[4])
+            try:
+                return int(cells[4])
+            except ValueError:  # no full-size figure for this kernel
+                return None
     return None
 
 
