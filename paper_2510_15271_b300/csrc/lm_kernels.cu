@@ -26,6 +26,9 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <atomic>
+
 #include "lm.h"
 
 namespace ba {
@@ -387,9 +390,12 @@ __device__ __forceinline__ void point_pass(const DevProblem& d, int w, Contrib c
 }
 
 // One warp per range of points (point_pass): V_j = sum w Jp^T Jp and
-// g_p,j = sum w Jp^T r over the point's observations.
+// g_p,j = sum w Jp^T r over the point's observations.  In FP32 six CTAs fit
+// on an SM (at most 42 registers), so the point ranges set-up cuts (six CTAs'
+// worth per SM) run in one wave.
 template <typename T>
-__global__ void __launch_bounds__(kPointPassThreads) k_lin_pt(DevProblem d, T delta) {
+__global__ void __launch_bounds__(kPointPassThreads, sizeof(T) == 4 ? 6 : 1)
+    k_lin_pt(DevProblem d, T delta) {
   if (!d.lm->need_lin) return;
   const int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   if (w >= d.nwpt) return;
@@ -990,7 +996,24 @@ static unsigned grid_cap(int64_t n, int threads, int cap) {
   return (unsigned)g;
 }
 
-int cost_blocks(const DevProblem& d) { return (int)grid_cap(d.N, 256, kCostParts / 2); }
+// CTAs of the cost pass: one wave of resident CTAs at most (the pass strides
+// over the observations, so a second, partial wave would only leave SMs idle
+// at its end), and no more than there are partial-sum slots.
+int cost_blocks(const DevProblem& d) {
+  static std::atomic<int> wave[2];  // per precision, on the device of the first call
+  const int pi = d.precision == BA_FP32 ? 0 : 1;
+  int cap = wave[pi].load(std::memory_order_relaxed);
+  if (cap == 0) {
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (pi == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cost<float>, 256, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cost<double>, 256, 0);
+    cap = std::max(1, sms * std::max(1, occ));
+    wave[pi].store(cap, std::memory_order_relaxed);
+  }
+  return (int)grid_cap(d.N, 256, std::min(kCostParts / 2, cap));
+}
 static_assert(148 * 6 <= kDlParts / 2, "one model-decrease partial per CTA of k_backsub");
 int backsub_blocks(const DevProblem& d) {
   return (d.nwpt + kPointPassThreads / 32 - 1) / (kPointPassThreads / 32);
