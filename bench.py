@@ -273,13 +273,19 @@ def run_ours(args, rank, world, local_rank, workload=None):
         q64, _ = ba.ba_get_state(h64, s.n_cams, s.n_pts)
         h64.close()
         rot, pos = pose_errors_qt(q32, q64)
+        rot_a, pos_a = pose_errors_qt(q32, q64, align=True)
         fp64 = {"value": work * args.fp64_steps * world / (ms64 / 1e3), "unit": UNIT,
                 "ms_per_step": ms64 / args.fp64_steps,
                 "final_cost": float(reps64[-1]["costs"][-1]),
                 "rmse_px": float(reps64[-1]["rmse_px"]),
                 "pcg_iters": int(np.sum(reps64[-1]["pcg_iters"])),
                 "pose_diff_fp32_vs_fp64": {"max_rad": float(rot.max()), "mean_rad": float(rot.mean()),
-                                           "max_m": float(pos.max()), "mean_m": float(pos.mean())}}
+                                           "max_m": float(pos.max()), "mean_m": float(pos.mean()),
+                                           "sim3_aligned": {
+                                               "max_rad": float(rot_a.max()),
+                                               "mean_rad": float(rot_a.mean()),
+                                               "max_m": float(pos_a.max()),
+                                               "mean_m": float(pos_a.mean())}}}
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
@@ -472,15 +478,29 @@ def measured_traffic(s, name):
 
 # --------------------------------------------------------------------------- batched / served
 
-def pose_errors_qt(qa, qb):
+def pose_errors_qt(qa, qb, align=False):
     """Per-camera rotation angle of R_a R_b^T (rad) and centre distance (m)
-    between two pose arrays (qw, qx, qy, qz, tx, ty, tz), world to camera."""
+    between two pose arrays (qw, qx, qy, qz, tx, ty, tz), world to camera.
+    align: first move result a onto b by the similarity that best maps a's
+    camera centres onto b's (least squares, Umeyama 1991), since the scale
+    of the reconstruction is left to the damping."""
     from scipy.spatial.transform import Rotation
     Ra = Rotation.from_quat(qa[:, [1, 2, 3, 0]])
     Rb = Rotation.from_quat(qb[:, [1, 2, 3, 0]])
-    rot = (Ra * Rb.inv()).magnitude()
     Ca = -Ra.inv().apply(qa[:, 4:])
     Cb = -Rb.inv().apply(qb[:, 4:])
+    if align:
+        # centred point sets, their cross-covariance, its SVD with a
+        # reflection guard; scale from the singular values
+        ma, mb = Ca.mean(0), Cb.mean(0)
+        xa, xb = Ca - ma, Cb - mb
+        u, sv, vt = np.linalg.svd(xb.T @ xa / len(Ca))
+        fix = np.diag([1.0, 1.0, np.sign(np.linalg.det(u) * np.linalg.det(vt))])
+        G = u @ fix @ vt
+        scale = float(np.sum(sv * np.diag(fix)) / (np.sum(xa * xa) / len(Ca)))
+        Ca = scale * (xa @ G.T) + mb
+        Ra = Ra * Rotation.from_matrix(G).inv()  # world-to-camera after the move
+    rot = (Ra * Rb.inv()).magnitude()
     return rot, np.linalg.norm(Ca - Cb, axis=1)
 
 

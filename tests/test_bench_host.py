@@ -52,3 +52,29 @@ def test_replicas_take_the_slowest_rank_and_sum_the_work():
 def test_single_rank_needs_no_process_group():
     assert bench.max_over_ranks(12.5, 1, "cpu") == 12.5
     assert bench.whole_job_value(100, 2, 1, 50.0) == pytest.approx(4000.0)
+
+
+def test_pose_difference_after_similarity_alignment():
+    """Two pose sets that differ by a similarity of the world (rotation,
+    scale, translation) differ by zero after the alignment, and not before;
+    a perturbation of one camera shows up after it."""
+    import numpy as np
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(3)
+    n = 40
+    Ra = Rotation.random(n, random_state=4)
+    ta = rng.normal(size=(n, 3))
+    qa = np.concatenate([Ra.as_quat()[:, [3, 0, 1, 2]], ta], 1)
+    G = Rotation.from_rotvec([0.2, -0.4, 0.1])
+    scale, shift = 1.7, np.array([3.0, -1.0, 0.5])
+    Rb = Ra * G.inv()
+    Cb = scale * G.apply(-Ra.inv().apply(ta)) + shift
+    qb = np.concatenate([Rb.as_quat()[:, [3, 0, 1, 2]], -Rb.apply(Cb)], 1)
+    rot, pos = bench.pose_errors_qt(qa, qb)
+    assert rot.max() > 0.1 and pos.max() > 0.1
+    rot, pos = bench.pose_errors_qt(qa, qb, align=True)
+    assert rot.max() < 1e-12 and pos.max() < 1e-12
+    qc = qb.copy()
+    qc[7, 4] += 0.01  # move camera 7 by 1 cm (it also tilts the fitted similarity a little)
+    rot, pos = bench.pose_errors_qt(qa, qc, align=True)
+    assert int(np.argmax(pos)) == 7 and 0.005 < pos[7] < 0.011 and rot.max() < 1e-3
