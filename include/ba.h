@@ -403,7 +403,11 @@ typedef struct {
  * problem, max_lm_iters each) in one persistent launch: every CTA takes the
  * next problem from a device work queue and runs its whole LM loop.
  * results[n] receives each problem's costs.  Problems of the batch share
- * nothing, so a result does not depend on the rest of the batch.
+ * nothing, so a result does not depend on the rest of the batch.  The
+ * inputs are copied to the device in a compact form: each observation's
+ * camera and point in one 32-bit word and, with precision BA_FP32, its
+ * pixels rounded to FP32 (the kernels compute in FP32 on that path anyway),
+ * so pixel coordinates beyond the FP32 range are refused as non-finite.
  * Errors: INVALID_ARG (a problem fails validation; results[i].status says
  * which), OOM, TIMEOUT, CUDA. */
 ba_status ba_solve_batch(ba_handle* h, int32_t n, const ba_problem* problems,

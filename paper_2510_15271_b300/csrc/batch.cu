@@ -51,19 +51,17 @@ struct Carve {
 struct InPtrs {
   double* cam_qt;
   double* pts;
-  double* uv;
-  int32_t* cam;
-  int32_t* pt;
+  void* uv;       // [N][2] in the batch's precision
+  uint32_t* idx;  // [N] pack_obs_index(camera, point)
   uint8_t* fixed;
 };
 
-InPtrs carve_in(Carve& c, int C, int P, int64_t N) {
+InPtrs carve_in(Carve& c, int precision, int C, int P, int64_t N) {
   InPtrs r;
   r.cam_qt = c.take<double>((size_t)C * 7);
   r.pts = c.take<double>((size_t)P * 3);
-  r.uv = c.take<double>((size_t)N * 2);
-  r.cam = c.take<int32_t>((size_t)N);
-  r.pt = c.take<int32_t>((size_t)N);
+  r.uv = c.take_bytes((size_t)N * 2 * (precision == BA_FP32 ? sizeof(float) : sizeof(double)));
+  r.idx = c.take<uint32_t>((size_t)N);
   r.fixed = c.take<uint8_t>((size_t)C);
   return r;
 }
@@ -148,23 +146,10 @@ int64_t count_pairs(const ba_problem& q) {
   return s;
 }
 
-// The same count from a point index array (used on the packed copy, which
-// is in cache right after packing).
-int64_t count_pairs_raw(const int32_t* pt, int64_t N, int P) {
-  std::vector<int32_t> L((size_t)P, 0);
-  for (int64_t k = 0; k < N; ++k) {
-    const int j = pt[k];
-    if (j >= 0 && j < P) ++L[j];
-  }
-  int64_t s = 0;
-  for (int32_t l : L) s += (int64_t)l * (l + 1) / 2;
-  return s;
-}
-
 ProbBytes prob_bytes(int precision, int C, int P, int64_t N, int64_t npairs) {
   ProbBytes b;
   Carve ci(nullptr), co(nullptr), cw(nullptr);
-  carve_in(ci, C, P, N);
+  carve_in(ci, precision, C, P, N);
   BProb tmp{};
   carve_out(co, tmp, C, P);
   carve_work(cw, tmp, precision, C, P, N, npairs);
@@ -176,33 +161,45 @@ ProbBytes prob_bytes(int precision, int C, int P, int64_t N, int64_t npairs) {
 
 void assign_prob(int precision, BProb& p, char* in, char* out, char* work) {
   Carve ci(in), co(out), cw(work);
-  const InPtrs r = carve_in(ci, p.C, p.P, p.N);
+  const InPtrs r = carve_in(ci, precision, p.C, p.P, p.N);
   p.cam_qt = r.cam_qt;
   p.pts = r.pts;
   p.raw_uv = r.uv;
-  p.raw_cam = r.cam;
-  p.raw_pt = r.pt;
+  p.raw_idx = r.idx;
   p.fixed = r.fixed;
   carve_out(co, p, p.C, p.P);
   carve_work(cw, p, precision, p.C, p.P, p.N, p.npairs);
 }
 
-void pack_inputs(int /*precision*/, const ba_problem& src, char* host_in) {
+int64_t pack_inputs(int precision, const ba_problem& src, char* host_in) {
   Carve c(host_in);
   const int C = src.n_cams, P = src.n_pts;
   const int64_t N = src.n_obs;
-  const InPtrs r = carve_in(c, C, P, N);
+  const InPtrs r = carve_in(c, precision, C, P, N);
   memcpy(r.cam_qt, src.cam_qt, sizeof(double) * 7 * (size_t)C);
   memcpy(r.pts, src.pts, sizeof(double) * 3 * (size_t)P);
-  memcpy(r.uv, src.obs_uv, sizeof(double) * 2 * (size_t)N);
-  memcpy(r.cam, src.obs_cam, sizeof(int32_t) * (size_t)N);
-  memcpy(r.pt, src.obs_pt, sizeof(int32_t) * (size_t)N);
+  if (precision == BA_FP32) {
+    float* uv = static_cast<float*>(r.uv);
+    for (int64_t k = 0; k < 2 * N; ++k) uv[k] = (float)src.obs_uv[k];
+  } else {
+    memcpy(r.uv, src.obs_uv, sizeof(double) * 2 * (size_t)N);
+  }
+  // the packed indices and the track lengths (for the pair count) in one pass
+  std::vector<int32_t> L((size_t)P, 0);
+  for (int64_t k = 0; k < N; ++k) {
+    const int32_t j = src.obs_pt[k];
+    r.idx[k] = pack_obs_index(src.obs_cam[k], j, C, P);
+    if (j >= 0 && j < P) ++L[j];
+  }
   if (src.cam_fixed) {
     memcpy(r.fixed, src.cam_fixed, (size_t)C);
   } else {
     memset(r.fixed, 0, (size_t)C);
     r.fixed[0] = 1;
   }
+  int64_t pairs = 0;
+  for (int32_t l : L) pairs += (int64_t)l * (l + 1) / 2;
+  return pairs;
 }
 
 // Host-side checks of one problem's arguments (the device checks values).
@@ -510,10 +507,7 @@ ba_status pack_and_copy(ba_handle* h, ba_batch* b, int32_t n, const ba_problem* 
   const int prec = h->opts.precision;
   auto pack_one = [&](int i) {
     char* dst = b->h_in + b->in_off[i];
-    pack_inputs(prec, pr[i], dst);
-    Carve c(dst);
-    const InPtrs r = carve_in(c, pr[i].n_cams, pr[i].n_pts, pr[i].n_obs);
-    npairs[i] = count_pairs_raw(r.pt, pr[i].n_obs, pr[i].n_pts);
+    npairs[i] = pack_inputs(prec, pr[i], dst);
   };
   const int nth = (total > (32u << 20) && n >= 16) ? host_threads() : 1;
   // groups of about total / (4 threads) bytes, at least 8 MB
@@ -573,7 +567,7 @@ ba_status prepare_inputs(ba_handle* h, ba_batch* b, int32_t n, const ba_problem*
   int max_cams = 1;
   for (int i = 0; i < n; ++i) {
     Carve ci(nullptr);
-    carve_in(ci, pr[i].n_cams, pr[i].n_pts, pr[i].n_obs);
+    carve_in(ci, h->opts.precision, pr[i].n_cams, pr[i].n_pts, pr[i].n_obs);
     b->in_off[i] = in;
     in += ci.off;
     max_cams = std::max(max_cams, (int)pr[i].n_cams);

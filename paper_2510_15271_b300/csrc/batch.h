@@ -26,6 +26,23 @@ constexpr int kPanel = 32;                // Cholesky panel width
 constexpr int kPairItem = 32;             // pairs per Schur work item
 constexpr int kBatchMaxThreads = 512;
 
+// The input block holds each observation's camera and point in one 32-bit
+// word: camera in the low kIdxCamBits bits, point above.  An index out of
+// range is stored as the field's largest value, which is at least the
+// problem's count, so the device still reports it as out of range.
+constexpr int kIdxCamBits = 10;
+constexpr uint32_t kIdxCamMask = (1u << kIdxCamBits) - 1u;
+constexpr uint32_t kIdxPtMax = (1u << (32 - kIdxCamBits)) - 1u;
+static_assert(kBatchMaxCams <= (int)kIdxCamMask, "camera field holds every valid camera");
+static_assert(kBatchMaxPts <= (int)kIdxPtMax, "point field holds every valid point");
+__host__ __device__ inline uint32_t pack_obs_index(int32_t cam, int32_t pt, int C, int P) {
+  const uint32_t c = (cam >= 0 && cam < C) ? (uint32_t)cam : kIdxCamMask;
+  const uint32_t j = (pt >= 0 && pt < P) ? (uint32_t)pt : kIdxPtMax;
+  return (j << kIdxCamBits) | c;
+}
+__host__ __device__ inline int obs_cam(uint32_t w) { return (int)(w & kIdxCamMask); }
+__host__ __device__ inline int obs_pt(uint32_t w) { return (int)(w >> kIdxCamBits); }
+
 // One problem, device-resident.  Pointers address the engine's arena.
 struct BProb {
   int C, P, N, iters;
@@ -37,9 +54,8 @@ struct BProb {
   int need_lin, step_ok, iter, n_accepted;
   double rmse_s, rmse_n;
   // inputs (copied in) and outputs
-  const int32_t* raw_cam;
-  const int32_t* raw_pt;
-  const double* raw_uv;
+  const uint32_t* raw_idx;  // [N] packed (point, camera) of each observation (pack_obs_index)
+  const void* raw_uv;       // [N][2] pixels in T (FP32 on the FP32 path)
   const double* cam_qt;
   const double* pts;
   const uint8_t* fixed;
@@ -145,8 +161,14 @@ int64_t count_pairs(const ba_problem& q);
 void assign_prob(int precision, BProb& p, char* in, char* out, char* work);
 
 // Host image of a problem's input block (what assign_prob puts there), so a
-// packed host buffer can be copied with one transfer.
-void pack_inputs(int precision, const ba_problem& src, char* host_in);
+// packed host buffer can be copied with one transfer: poses and points in
+// FP64, the observations' pixels in the batch's precision (FP32 pixels are
+// the FP64 ones rounded to nearest, as the kernels would round them; pixels
+// beyond the FP32 range become infinite and are refused as non-finite) and
+// their (point, camera) packed by pack_obs_index.  Returns the problem's
+// Schur pair count (sum over points of L (L + 1) / 2, indices out of range
+// skipped).
+int64_t pack_inputs(int precision, const ba_problem& src, char* host_in);
 
 // Dynamic shared memory the kernel needs for problems of at most max_cams
 // cameras, and what it can use (the Cholesky panel in shared memory).

@@ -245,8 +245,10 @@ __device__ void setup_problem(BProb& p, Smem& sm, int* wsm) {
   __syncthreads();
   int bad = 0;
   for (int k = tid; k < N; k += NT) {
-    const int c = p.raw_cam[k], j = p.raw_pt[k];
-    const double u = p.raw_uv[2 * (int64_t)k], v = p.raw_uv[2 * (int64_t)k + 1];
+    const uint32_t w = p.raw_idx[k];
+    const int c = obs_cam(w), j = obs_pt(w);
+    const T* uvk = (const T*)p.raw_uv + 2 * (int64_t)k;
+    const T u = uvk[0], v = uvk[1];
     const bool okc = c >= 0 && c < C, okp = j >= 0 && j < P;
     if (!okc) bad |= kBadCamIndex;
     if (!okp) bad |= kBadPtIndex;
@@ -288,7 +290,7 @@ __device__ void setup_problem(BProb& p, Smem& sm, int* wsm) {
   int32_t* tcnt = po_orig + N;
   for (int j = tid; j < P; j += NT) pt_cur[j] = p.pt_ptr[j];
   __syncthreads();
-  for (int k = tid; k < N; k += NT) po_orig[atomicAdd(&pt_cur[p.raw_pt[k]], 1)] = k;
+  for (int k = tid; k < N; k += NT) po_orig[atomicAdd(&pt_cur[obs_pt(p.raw_idx[k])], 1)] = k;
   __syncthreads();
   // each bucket by (camera, original index): insertion sort, one thread per point
   bad = 0;
@@ -296,11 +298,11 @@ __device__ void setup_problem(BProb& p, Smem& sm, int* wsm) {
     const int q0 = p.pt_ptr[j], q1 = p.pt_ptr[j + 1];
     for (int a = q0 + 1; a < q1; ++a) {
       const int k = po_orig[a];
-      const int ck = p.raw_cam[k];
+      const int ck = obs_cam(p.raw_idx[k]);
       int b = a - 1;
       while (b >= q0) {
         const int kb = po_orig[b];
-        const int cb = p.raw_cam[kb];
+        const int cb = obs_cam(p.raw_idx[kb]);
         if (cb < ck || (cb == ck && kb < k)) break;
         po_orig[b + 1] = kb;
         --b;
@@ -308,7 +310,8 @@ __device__ void setup_problem(BProb& p, Smem& sm, int* wsm) {
       po_orig[b + 1] = k;
     }
     for (int a = q0 + 1; a < q1; ++a)
-      if (p.raw_cam[po_orig[a]] == p.raw_cam[po_orig[a - 1]]) bad |= kDuplicateObs;
+      if (obs_cam(p.raw_idx[po_orig[a]]) == obs_cam(p.raw_idx[po_orig[a - 1]]))
+        bad |= kDuplicateObs;
   }
   if (bad) atomicOr(&sm.flag, bad);
   __syncthreads();
@@ -324,7 +327,7 @@ __device__ void setup_problem(BProb& p, Smem& sm, int* wsm) {
   __syncthreads();
   {
     const int q0 = tid * tile, q1 = min(N, q0 + tile);
-    for (int q = q0; q < q1; ++q) tcnt[tid * C + p.raw_cam[po_orig[q]]] += 1;
+    for (int q = q0; q < q1; ++q) tcnt[tid * C + obs_cam(p.raw_idx[po_orig[q]])] += 1;
   }
   __syncthreads();
   for (int c = tid; c < C; c += NT) {
@@ -342,10 +345,12 @@ __device__ void setup_problem(BProb& p, Smem& sm, int* wsm) {
     const int q0 = tid * tile, q1 = min(N, q0 + tile);
     for (int q = q0; q < q1; ++q) {
       const int k = po_orig[q];
-      const int c = p.raw_cam[k];
+      const uint32_t w = p.raw_idx[k];
+      const int c = obs_cam(w);
       const int r = tcnt[tid * C + c]++;
-      const T u = (T)p.raw_uv[2 * (int64_t)k], v = (T)p.raw_uv[2 * (int64_t)k + 1];
-      p.oc_pt[r] = p.raw_pt[k];
+      const T* uvk = (const T*)p.raw_uv + 2 * (int64_t)k;
+    const T u = uvk[0], v = uvk[1];
+      p.oc_pt[r] = obs_pt(w);
       p.q_of[r] = q;
       p.po_cam[q] = c;
       p.po_k[q] = r;
