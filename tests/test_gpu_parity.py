@@ -263,8 +263,8 @@ def test_fp32_final_rmse_within_one_percent(name, kw, iters, solver):
           f"rad {pos:.2e} m")
 
 
-# The untrimmed gate (every generator inlier, reading C12 as the survey set
-# it) against the plain FP64 oracle.  It holds for the FP64 path and for the
+# The untrimmed gate (RMSE over every generator inlier, reading C12) against
+# the plain FP64 oracle.  It holds for the FP64 path and for the
 # dense FP32 ring, and fails for the FP32 PCG workloads: their RMSE over all
 # inliers is dominated by a few hundred weakly determined points pulled by
 # wrong matches, whose end point after a fixed number of iterations follows
