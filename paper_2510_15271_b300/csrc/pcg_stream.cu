@@ -599,11 +599,9 @@ __global__ void __launch_bounds__(kSThreads, 1) k_pcg_stream(DevProblem d, Strea
     for (int j = 0; j < ND; ++j) {
       const int t = tid + j * kSConsumers;
       xr[j] = rr[j] = pr[j] = T(0);
-      if (t < nel) {
-        rr[j] = rhs[e0 + t];
-        pb[1][e0 + t] = T(0);  // p_{-1} = 0
-      }
+      if (t < nel) rr[j] = rhs[e0 + t];
     }
+    for (int i = tid; i < 6 * nu; i += kSConsumers) sv[i] = T(0);  // p_{-1} = 0
     double l2[2] = {0.0, 0.0};
     precondition(rr, zr, l2[0], l2[1]);
     double tot[2];
@@ -618,19 +616,14 @@ __global__ void __launch_bounds__(kSThreads, 1) k_pcg_stream(DevProblem d, Strea
     int k = 0;
     while (s_go) {
       const T bt = s_bt;
-      T* pn = pb[k & 1];
-      const T* po = pb[(k & 1) ^ 1];
-      // p_k = z + beta p_{k-1}: own rows in registers and global (for the
-      // other CTAs' staging next time), referenced columns into sv
+      // p_k = z + beta p_{k-1}: own rows in registers; the referenced
+      // columns in sv, from the owners' z and this CTA's own staged p_{k-1}
+      // (the same arithmetic as the owners', so the same values)
 #pragma unroll
-      for (int j = 0; j < ND; ++j) {
-        const int t = tid + j * kSConsumers;
-        pr[j] = zr[j] + bt * pr[j];
-        if (t < nel) pn[e0 + t] = pr[j];
-      }
+      for (int j = 0; j < ND; ++j) pr[j] = zr[j] + bt * pr[j];
       for (int i = tid; i < 6 * nu; i += kSConsumers) {
         const int gi = 6 * __ldg(ucol + i / 6) + i % 6;
-        sv[i] = __ldcg(z + gi) + bt * __ldcg(po + gi);
+        sv[i] = __ldcg(z + gi) + bt * sv[i];
       }
       consumers_sync();
       spmv_stream<T, T, T, NS>(d, wp, nrow, sfirst, slast, full, fail, ring, ridx, sv, sq, fl, g,
