@@ -135,13 +135,34 @@ _FULL_SIZE = {"driving": dict(n_cams=1000, n_pts=200_000, length_m=2000.0),
 
 def make_workload(name, seed, scale=1.0):
     """The seeded workload; scale < 1 shrinks cameras, points (and the
-    driving route) in proportion, for counter captures of a smaller case."""
+    driving route) in proportion, for counter captures of a smaller case.
+    Generated once per (name, seed, scale, generator source) and cached on
+    local disk, outside any timed region (the city scene takes about 90 s
+    of host time to generate)."""
+    import pickle
     from paper_2510_15271_b300 import scenes
     kw = {}
     if scale != 1.0 and name in _FULL_SIZE:
         for k, v in _FULL_SIZE[name].items():
             kw[k] = v * scale if isinstance(v, float) else max(2, int(round(v * scale)))
-    return scenes.make_scene(name, seed=seed, **kw)
+    with open(scenes.__file__, "rb") as f:
+        src = hashlib.sha256(f.read()).hexdigest()[:12]
+    path = os.path.join(tempfile.gettempdir(), f"ba_workload_{name}_{seed}_{scale:g}_{src}.pkl")
+    if os.path.exists(path):
+        try:
+            with open(path, "rb") as f:
+                return pickle.load(f)
+        except Exception:
+            pass
+    s = scenes.make_scene(name, seed=seed, **kw)
+    try:
+        tmp = f"{path}.{os.getpid()}"
+        with open(tmp, "wb") as f:
+            pickle.dump(s, f, protocol=pickle.HIGHEST_PROTOCOL)
+        os.replace(tmp, path)
+    except Exception:
+        pass
+    return s
 
 
 def camera_pairs(s):
