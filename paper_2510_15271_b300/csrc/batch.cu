@@ -510,8 +510,9 @@ ba_status pack_and_copy(ba_handle* h, ba_batch* b, int32_t n, const ba_problem* 
     npairs[i] = pack_inputs(prec, pr[i], dst);
   };
   const int nth = (total > (32u << 20) && n >= 16) ? host_threads() : 1;
-  // groups of about total / (4 threads) bytes, at least 8 MB
-  const size_t target = std::max<size_t>((size_t)8 << 20, total / (4 * (size_t)nth));
+  // groups of about total / (16 threads) bytes, at least 1 MB: many small groups keep every
+  // host thread busy to the end and start the copies early
+  const size_t target = std::max<size_t>((size_t)1 << 20, total / (16 * (size_t)nth));
   std::vector<int> gbeg{0};
   for (int i = 0; i + 1 < n; ++i)
     if (b->in_off[i + 1] - b->in_off[gbeg.back()] >= target) gbeg.push_back(i + 1);
