@@ -78,3 +78,28 @@ def test_pose_difference_after_similarity_alignment():
     qc[7, 4] += 0.01  # move camera 7 by 1 cm (it also tilts the fitted similarity a little)
     rot, pos = bench.pose_errors_qt(qa, qc, align=True)
     assert int(np.argmax(pos)) == 7 and 0.005 < pos[7] < 0.011 and rot.max() < 1e-3
+
+
+def test_measured_traffic_reads_the_matching_row_of_a_current_profile(tmp_path, monkeypatch):
+    """The bench takes a kernel's DRAM traffic from the committed ncu summary
+    only while the summary's source digest matches the sources, only from
+    the row named exactly after the kernel, and reports none for a row
+    without a full-size figure."""
+    import types
+    prof = tmp_path / "city_fp32_kernels.md"
+    digest = bench.source_digest()
+    prof.write_text(
+        f"Source digest of the driving path's sources at capture: `{digest}`\n\n"
+        "| kernel | a | b | c | traffic / launch (B) | rest |\n|---|---|---|---|---|---|\n"
+        "| k_pcg_stream (0.4 scale) | 1 | 2 | 3 | 999 | x |\n"
+        "| k_pcg_stream | 1 | 2 | 3 | 123456 | x |\n"
+        "| k_schur | 1 | 2 | 3 | 777 | x |\n"
+        "| k_backsub | 1 | 2 | 3 | — | x |\n")
+    monkeypatch.setattr(bench, "profile_path", lambda name: str(prof))
+    s = types.SimpleNamespace(name="city")
+    assert bench.measured_traffic(s, "pcg") == 123456
+    assert bench.measured_traffic(s, "schur") == 777
+    assert bench.measured_traffic(s, "backsub") is None
+    assert bench.measured_traffic(s, "lin_pt") is None
+    prof.write_text(prof.read_text().replace(digest, "0" * 16))
+    assert bench.measured_traffic(s, "pcg") is None
